@@ -1,0 +1,303 @@
+/*
+ * FP64 CPU oracle for the exact two-dimensional DCT (test infrastructure).
+ *
+ * This file is test infrastructure only.  The tests, the package's smoke()
+ * check and the benchmark's CPU-baseline leg may call it; the CUDA library
+ * never does, and the two share no code, tables or constants.
+ *
+ * What it computes (BRiDCT paper, Section 2.1):
+ *   Eq. 1   (Q_n)_{kj} = alpha_k cos[(pi/n)(j + 1/2) k],
+ *           alpha_0 = n^{-1/2}, alpha_k = (2/n)^{1/2} for k > 0.
+ *   Eq. 2   C(X) = Q_h X Q_w^T   (forward, DCT-II),
+ *           C^{-1}(Y) = Q_h^T Y Q_w   (inverse, DCT-III, the adjoint).
+ *   Section 7.1 gives the rectangular operator Q_h X Q_w^T for X in R^{h x w}.
+ *   The round trip C^{-1}(C(X)) has exact result X (Section 2.1).
+ *
+ * The unnormalized convention (Section 2.1 names FFTW's REDFT10/REDFT01 pair,
+ * pair factor 2n per axis) is read as
+ *   forward  y_k = 2 sum_j x_j cos(pi (2j+1) k / (2n))
+ *   inverse  x_j = y_0 + 2 sum_{k>=1} y_k cos(pi (2j+1) k / (2n)).
+ *
+ * Everything is a plain double-precision sum, applied separably (first along
+ * rows, then along columns), exactly as Eq. 2 is written.  A second, brute-force
+ * O(h^2 w^2) evaluation of the same double sum, with the cosine taken straight
+ * from libm, serves as an independent check of the separable form.
+ *
+ * A planted-fault switch (oracle_set_fault) lets the CPU tests show that their
+ * pins catch a dropped term, a wrong scale, a wrong index or a transposed
+ * operand.  It is off (0) unless a test turns it on.
+ */
+#define _GNU_SOURCE
+#include <math.h>
+#include <pthread.h>
+#include <sched.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <unistd.h>
+
+#define ORACLE_NORM_ORTHO 0
+#define ORACLE_NORM_NONE 1
+
+#define ORACLE_DIR_FORWARD 1
+#define ORACLE_DIR_INVERSE 2
+
+static int g_fault = 0;
+
+/* Planted faults, for the tests of the pins only:
+ *   1  alpha_0 taken as (2/n)^{1/2}                     (wrong scale)
+ *   2  last term of every 1D sum dropped                (dropped term)
+ *   3  cos argument uses (2j-1) instead of (2j+1)        (wrong index)
+ *   4  inverse uses M instead of M^T                     (transposed operand)
+ *   5  row axis uses the column-axis matrix              (swapped axes)    */
+void oracle_set_fault(int f) { g_fault = f; }
+int oracle_get_fault(void) { return g_fault; }
+
+/* cos(pi * m / d) for integers m >= 0 and d > 0, with the argument reduced
+ * exactly in integers so that the zeros and the +-1 values come out exact and
+ * the remaining argument lies in [0, pi/4]. */
+double oracle_cospi_frac(int64_t m, int64_t d)
+{
+    int64_t r = m % (2 * d);
+    if (r < 0) r += 2 * d;
+    if (r > d) r = 2 * d - r;            /* cos(2pi - t) = cos t, r in [0, d] */
+    double sign = 1.0;
+    if (2 * r > d) { r = d - r; sign = -1.0; } /* cos(pi - t) = -cos t, r in [0, d/2] */
+    if (r == 0) return sign;
+    if (2 * r == d) return 0.0;
+    if (4 * r > d) /* cos t = sin(pi/2 - t) with pi/2 - t = pi (d - 2r) / (2d) */
+        return sign * sin(M_PI * (double)(d - 2 * r) / (double)(2 * d));
+    return sign * cos(M_PI * (double)r / (double)d);
+}
+
+/* Unscaled DCT-II kernel G_n[k][j] = cos(pi (2j+1) k / (2n)), row-major n x n. */
+static void basis(int n, double *G)
+{
+    for (int k = 0; k < n; ++k)
+        for (int j = 0; j < n; ++j) {
+            int64_t odd = (g_fault == 3) ? (2 * (int64_t)j - 1) : (2 * (int64_t)j + 1);
+            G[(size_t)k * n + j] = oracle_cospi_frac(odd * k, 2 * (int64_t)n);
+        }
+}
+
+/* Per-coefficient factor applied to G_n in the requested direction/norm.
+ * forward ORTHO: alpha_k (Eq. 1);  forward NONE: 2;
+ * inverse ORTHO: alpha_k;          inverse NONE: 1 for k = 0, else 2. */
+static double coef_scale(int n, int k, int dir, int norm)
+{
+    if (norm == ORACLE_NORM_ORTHO) {
+        if (k == 0 && g_fault != 1) return sqrt(1.0 / n);
+        return sqrt(2.0 / n);
+    }
+    if (dir == ORACLE_DIR_FORWARD) return 2.0;
+    return (k == 0) ? 1.0 : 2.0;
+}
+
+/* The 1D operator matrix M (n x n, row-major) so that the 2D result is
+ * M_h X M_w^T:
+ *   forward: M[k][j] = s_k G[k][j]      (ORTHO: M = Q_n)
+ *   inverse: M[j][k] = s_k G[k][j]      (ORTHO: M = Q_n^T)                 */
+void oracle_matrix(int n, int dir, int norm, double *M)
+{
+    double *G = (double *)malloc(sizeof(double) * (size_t)n * n);
+    basis(n, G);
+    for (int k = 0; k < n; ++k) {
+        double s = coef_scale(n, k, dir, norm);
+        for (int j = 0; j < n; ++j) {
+            double v = s * G[(size_t)k * n + j];
+            int transpose = (dir == ORACLE_DIR_INVERSE) && (g_fault != 4);
+            if (transpose) M[(size_t)j * n + k] = v;
+            else M[(size_t)k * n + j] = v;
+        }
+    }
+    free(G);
+}
+
+/* One array: out = Mh * X * Mw^T, X is h x w (float), out is h x w (double).
+ * First T = X Mw^T (every row transformed), then out = Mh T (every column). */
+static void sandwich_one(int h, int w, const double *Mh, const double *Mw,
+                         const float *X, double *out, double *T)
+{
+    int last_w = (g_fault == 2) ? w - 1 : w;
+    int last_h = (g_fault == 2) ? h - 1 : h;
+    for (int i = 0; i < h; ++i)
+        for (int l = 0; l < w; ++l) {
+            double acc = 0.0;
+            for (int j = 0; j < last_w; ++j)
+                acc += (double)X[(size_t)i * w + j] * Mw[(size_t)l * w + j];
+            T[(size_t)i * w + l] = acc;
+        }
+    for (int k = 0; k < h; ++k)
+        for (int l = 0; l < w; ++l) {
+            double acc = 0.0;
+            for (int i = 0; i < last_h; ++i)
+                acc += Mh[(size_t)k * h + i] * T[(size_t)i * w + l];
+            out[(size_t)k * w + l] = acc;
+        }
+}
+
+/* Same as sandwich_one for a double input (used by the round-trip composition). */
+static void sandwich_one_d(int h, int w, const double *Mh, const double *Mw,
+                           const double *X, double *out, double *T)
+{
+    for (int i = 0; i < h; ++i)
+        for (int l = 0; l < w; ++l) {
+            double acc = 0.0;
+            for (int j = 0; j < w; ++j)
+                acc += X[(size_t)i * w + j] * Mw[(size_t)l * w + j];
+            T[(size_t)i * w + l] = acc;
+        }
+    for (int k = 0; k < h; ++k)
+        for (int l = 0; l < w; ++l) {
+            double acc = 0.0;
+            for (int i = 0; i < h; ++i)
+                acc += Mh[(size_t)k * h + i] * T[(size_t)i * w + l];
+            out[(size_t)k * w + l] = acc;
+        }
+}
+
+typedef struct {
+    int h, w, dir, norm;
+    const double *Mh, *Mw, *Mh2, *Mw2;
+    const float *in;
+    double *out;
+    int64_t first, last;
+    int roundtrip;
+} job_t;
+
+static void *worker(void *arg)
+{
+    job_t *jb = (job_t *)arg;
+    size_t hw = (size_t)jb->h * jb->w;
+    double *T = (double *)malloc(sizeof(double) * hw);
+    double *F = jb->roundtrip ? (double *)malloc(sizeof(double) * hw) : NULL;
+    for (int64_t b = jb->first; b < jb->last; ++b) {
+        const float *x = jb->in + (size_t)b * hw;
+        double *y = jb->out + (size_t)b * hw;
+        if (!jb->roundtrip) {
+            sandwich_one(jb->h, jb->w, jb->Mh, jb->Mw, x, y, T);
+        } else {
+            sandwich_one(jb->h, jb->w, jb->Mh, jb->Mw, x, F, T);
+            sandwich_one_d(jb->h, jb->w, jb->Mh2, jb->Mw2, F, y, T);
+        }
+    }
+    free(T);
+    free(F);
+    return NULL;
+}
+
+int oracle_default_threads(void)
+{
+    cpu_set_t set;
+    if (sched_getaffinity(0, sizeof(set), &set) == 0) {
+        int c = CPU_COUNT(&set);
+        if (c > 0) return c;
+    }
+    long n = sysconf(_SC_NPROCESSORS_ONLN);
+    return n > 0 ? (int)n : 1;
+}
+
+static int run_jobs(int h, int w, int dir, int norm, const float *in, double *out,
+                    int64_t batch, int threads, int roundtrip)
+{
+    if (h < 1 || w < 1 || batch < 0) return -1;
+    if (batch == 0) return 0;
+    if (threads <= 0) threads = oracle_default_threads();
+    if (threads > batch) threads = (int)batch;
+    if (threads > 512) threads = 512;
+
+    double *Mh = (double *)malloc(sizeof(double) * (size_t)h * h);
+    double *Mw = (double *)malloc(sizeof(double) * (size_t)w * w);
+    double *Mh2 = NULL, *Mw2 = NULL;
+    int d1 = roundtrip ? ORACLE_DIR_FORWARD : dir;
+    oracle_matrix(h, d1, norm, Mh);
+    oracle_matrix(w, d1, norm, Mw);
+    if (g_fault == 5 && h != w) { /* planted fault: row axis uses the column matrix */
+        free(Mw);
+        Mw = (double *)malloc(sizeof(double) * (size_t)w * w);
+        for (int a = 0; a < w; ++a)
+            for (int b = 0; b < w; ++b)
+                Mw[(size_t)a * w + b] = (a < h && b < h) ? Mh[(size_t)a * h + b] : 0.0;
+    }
+    if (roundtrip) {
+        Mh2 = (double *)malloc(sizeof(double) * (size_t)h * h);
+        Mw2 = (double *)malloc(sizeof(double) * (size_t)w * w);
+        oracle_matrix(h, ORACLE_DIR_INVERSE, norm, Mh2);
+        oracle_matrix(w, ORACLE_DIR_INVERSE, norm, Mw2);
+        if (norm == ORACLE_NORM_NONE) { /* normalized round trip: divide by 4hw */
+            double s = 1.0 / (4.0 * (double)h * (double)w);
+            for (size_t q = 0; q < (size_t)h * h; ++q) Mh2[q] *= s;
+        }
+    }
+
+    pthread_t *tid = (pthread_t *)malloc(sizeof(pthread_t) * threads);
+    job_t *jobs = (job_t *)malloc(sizeof(job_t) * threads);
+    int64_t per = batch / threads, rem = batch % threads, start = 0;
+    for (int t = 0; t < threads; ++t) {
+        int64_t cnt = per + (t < rem ? 1 : 0);
+        jobs[t] = (job_t){h, w, dir, norm, Mh, Mw, Mh2, Mw2, in, out, start, start + cnt, roundtrip};
+        start += cnt;
+    }
+    for (int t = 1; t < threads; ++t) pthread_create(&tid[t], NULL, worker, &jobs[t]);
+    worker(&jobs[0]);
+    for (int t = 1; t < threads; ++t) pthread_join(tid[t], NULL);
+    free(tid);
+    free(jobs);
+    free(Mh);
+    free(Mw);
+    free(Mh2);
+    free(Mw2);
+    return 0;
+}
+
+/* Forward 2D DCT-II of `batch` contiguous h x w float arrays into double. */
+int oracle_forward(int h, int w, int norm, const float *in, double *out, int64_t batch, int threads)
+{
+    return run_jobs(h, w, ORACLE_DIR_FORWARD, norm, in, out, batch, threads, 0);
+}
+
+/* Inverse 2D DCT-III of `batch` contiguous h x w float arrays into double. */
+int oracle_inverse(int h, int w, int norm, const float *in, double *out, int64_t batch, int threads)
+{
+    return run_jobs(h, w, ORACLE_DIR_INVERSE, norm, in, out, batch, threads, 0);
+}
+
+/* FP64 composition C^{-1}(C(X)) (normalized); its exact result is X. */
+int oracle_roundtrip(int h, int w, int norm, const float *in, double *out, int64_t batch, int threads)
+{
+    return run_jobs(h, w, ORACLE_DIR_FORWARD, norm, in, out, batch, threads, 1);
+}
+
+/* Brute-force O(h^2 w^2) double sum of Eq. 2 for one array, with every cosine
+ * taken directly from libm (no table, no separable factoring). */
+int oracle_bruteforce(int h, int w, int dir, int norm, const float *in, double *out)
+{
+    if (h < 1 || w < 1) return -1;
+    for (int p = 0; p < h; ++p)
+        for (int q = 0; q < w; ++q) {
+            double acc = 0.0;
+            for (int a = 0; a < h; ++a)
+                for (int b = 0; b < w; ++b) {
+                    /* forward: out[k=p][l=q] += s_k s_l x[i=a][j=b] cos(..a..p) cos(..b..q)
+                     * inverse: out[i=p][j=q] += s_k s_l y[k=a][l=b] cos(..p..a) cos(..q..b) */
+                    int k, i, l, j;
+                    if (dir == ORACLE_DIR_FORWARD) { k = p; i = a; l = q; j = b; }
+                    else { k = a; i = p; l = b; j = q; }
+                    double sk, sl;
+                    if (norm == ORACLE_NORM_ORTHO) {
+                        sk = (k == 0) ? 1.0 / sqrt((double)h) : sqrt(2.0 / h);
+                        sl = (l == 0) ? 1.0 / sqrt((double)w) : sqrt(2.0 / w);
+                    } else if (dir == ORACLE_DIR_FORWARD) {
+                        sk = 2.0; sl = 2.0;
+                    } else {
+                        sk = (k == 0) ? 1.0 : 2.0;
+                        sl = (l == 0) ? 1.0 : 2.0;
+                    }
+                    double ch = cos(M_PI * (2.0 * i + 1.0) * k / (2.0 * h));
+                    double cw = cos(M_PI * (2.0 * j + 1.0) * l / (2.0 * w));
+                    acc += sk * sl * (double)in[(size_t)a * w + b] * ch * cw;
+                }
+            out[(size_t)p * w + q] = acc;
+        }
+    return 0;
+}
