@@ -1,0 +1,373 @@
+"""Benchmark of the batched exact 2D DCT on one GB300.
+
+Workload (one step): a 2048 x 2048 float32 image (N(0,1) + 0.01 (i + j))
+cut into 16384 independent 16 x 16 blocks, forward DCT-II then inverse
+DCT-III on every block through the tiled-image entry point -- the
+phase-unwrapping-shaped workload that motivates the paper (Section 1.1).
+Algorithmic traffic: 8 bytes per element per transform (read + write), so
+16 bytes per element per step.  Steps rotate over a pool of images whose
+inputs, spectra and outputs together exceed twice the L2 cache, so every
+step streams from HBM.
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle (the
+only reference this method has) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "batched 2D DCT GB/s & % HBM roofline, split-BF16 TC vs FP32, at ≤1e-6 rel err"
+IMG = 2048
+BLK = 16
+BYTES_PER_ELEM_STEP = 16  # forward (4 read + 4 write) + inverse (4 read + 4 write)
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled while the timed region runs."""
+
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_oracle_sample(target_s: float = 1.5):
+    """Time the FP64 oracle on forward-then-inverse of a bounded slice of the
+    image workload; returns (GB/s on the metric's algorithmic bytes, threads,
+    description)."""
+    import oracle
+    from paper_2609_28519_gb300 import inputs
+    threads = oracle.default_threads()
+    img = inputs.ramp_image(2)
+    blocks = inputs.image_to_blocks(img, BLK, BLK)
+    # whole image per repeat; repeat until the sample has run target_s of wall time
+    reps = 0
+    t0 = time.perf_counter()
+    while True:
+        spec = oracle.forward(blocks, 0, threads=threads)
+        oracle.inverse(spec.astype(np.float32), 0, threads=threads)
+        reps += 1
+        dt = time.perf_counter() - t0
+        if dt >= target_s:
+            break
+    gbs = reps * len(blocks) * BLK * BLK * BYTES_PER_ELEM_STEP / dt / 1e9
+    return gbs, threads, dt, (f"{reps} passes over the 16384 16x16 blocks of the 2048x2048 image, "
+                              f"F then I, {dt:.2f} s wall on {threads} threads")
+
+
+def run_reference(args):
+    rank, world, _ = _dist_env()
+    if rank != 0:
+        return 0
+    # each step: a bounded sample of the workload through the FP64 oracle
+    import oracle
+    from paper_2609_28519_gb300 import inputs
+    threads = oracle.default_threads()
+    blocks = inputs.image_to_blocks(inputs.ramp_image(2), BLK, BLK)
+    n = 2048
+    sub = blocks[:n]
+    for _ in range(args.warmup):
+        oracle.inverse(oracle.forward(sub, 0, threads=threads).astype(np.float32), 0, threads=threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.inverse(oracle.forward(sub, 0, threads=threads).astype(np.float32), 0, threads=threads)
+    dt = time.perf_counter() - t0
+    gbs = args.steps * n * BLK * BLK * BYTES_PER_ELEM_STEP / dt / 1e9
+    sample = f"{n} of 16384 16x16 blocks per step, forward then inverse, FP64 oracle"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "2048x2048 image as 16384 16x16 blocks, forward then inverse",
+                   "global_batch": 16384, "seq_len": None, "parallelism": "none",
+                   "l2": "oracle on host cores"},
+        "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def traffic_from_profiles(kernel_key: str):
+    """DRAM bytes per launch recorded by an ncu capture, if the kernel source
+    has not changed since (the summary stores the source hash)."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "traffic_per_launch.txt")
+    if not os.path.exists(p):
+        return None
+    src = os.path.join(ROOT, "paper_2609_28519_gb300", "csrc", "fp32_fused.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    for ln in open(p):
+        parts = ln.split()
+        if len(parts) >= 3 and parts[0] == kernel_key and not ln.startswith("#"):
+            if parts[2] == h:
+                return float(parts[1])
+    return None
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = _dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2609_28519_gb300 import Plan, inputs, native
+    from paper_2609_28519_gb300 import build as B
+    if not os.path.exists(native.LIB_PATH):
+        B.build()
+    plan = Plan(BLK, BLK, kind=native.FORWARD | native.INVERSE | native.ROUNDTRIP, norm="ortho",
+                path=args.path)
+    info = plan.info()
+    L = native.lib()
+
+    # pool of images: inputs + spectra + outputs > 2 x L2
+    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+    img_bytes = IMG * IMG * 4
+    pool = max(4, int(np.ceil(2.5 * l2 / (3 * img_bytes))))
+    base = torch.from_numpy(inputs.ramp_image(2 + rank)).to(dev)
+    imgs = [base.clone() for _ in range(pool)]
+    for i in range(1, pool):
+        imgs[i].add_(float(i) * 1e-3)
+    specs = [torch.empty_like(base) for _ in range(pool)]
+    outs = [torch.empty_like(base) for _ in range(pool)]
+    stream = torch.cuda.current_stream(dev)
+    s_ptr = __import__("ctypes").c_void_p(stream.cuda_stream)
+    c_void_p = __import__("ctypes").c_void_p
+    ptr_in = [c_void_p(t.data_ptr()) for t in imgs]
+    ptr_sp = [c_void_p(t.data_ptr()) for t in specs]
+    ptr_out = [c_void_p(t.data_ptr()) for t in outs]
+    h = plan.handle
+    ex = L.bdct_execute_tiled
+
+    def step(i, evs=None):
+        k = i % pool
+        if evs is not None:
+            evs[0].record(stream)
+        st = ex(h, native.FORWARD, ptr_in[k], ptr_sp[k], IMG, IMG, IMG, IMG, s_ptr)
+        if evs is not None:
+            evs[1].record(stream)
+        st |= ex(h, native.INVERSE, ptr_sp[k], ptr_out[k], IMG, IMG, IMG, IMG, s_ptr)
+        if evs is not None:
+            evs[2].record(stream)
+        if st:
+            raise RuntimeError(f"bdct_execute_tiled failed: {st}")
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, per-launch CUDA events on the launch stream
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t_start.record(stream)
+    for i in range(args.steps):
+        step(i, evs[i])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    ms_total = t_start.elapsed_time(t_end)
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    fwd_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    inv_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    elems = IMG * IMG
+    step_bytes = elems * BYTES_PER_ELEM_STEP
+    value = world * args.steps * step_bytes / (ms_total * 1e-3) / 1e9
+
+    # ---- dominant kernel roofline (forward fused kernel; 8 B/element/launch)
+    fwd_avg = sum(fwd_ms) / len(fwd_ms)
+    inv_avg = sum(inv_ms) / len(inv_ms)
+    dom_key, dom_avg = ("k_fused_small<16,16,FWD,tiled>", fwd_avg) if fwd_avg >= inv_avg else \
+        ("k_fused_small<16,16,INV,tiled>", inv_avg)
+    peak, peak_kind = _peaks()
+    achieved = elems * 8 / (dom_avg * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic_from_profiles(dom_key),
+                "kernel": dom_key, "peak_source": f"{peak_kind} hbm_gbs",
+                "avg_launch_us": {"forward": fwd_avg * 1e3, "inverse": inv_avg * 1e3}}
+
+    # ---- end to end through host buffers (pinned), copies inside the timed region
+    e2e = None
+    if rank == 0 or world > 1:
+        host_in = torch.from_numpy(inputs.ramp_image(2 + rank)).pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        d_in, d_sp, d_out = imgs[0], specs[0], outs[0]
+        pin, psp, pout = c_void_p(d_in.data_ptr()), c_void_p(d_sp.data_ptr()), c_void_p(d_out.data_ptr())
+        k_e2e = max(10, args.steps // 4)
+
+        def e2e_step():
+            d_in.copy_(host_in, non_blocking=True)
+            ex(h, native.FORWARD, pin, psp, IMG, IMG, IMG, IMG, s_ptr)
+            ex(h, native.INVERSE, psp, pout, IMG, IMG, IMG, IMG, s_ptr)
+            host_out.copy_(d_out, non_blocking=True)
+
+        for _ in range(3):
+            e2e_step()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k_e2e):
+            e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = a.elapsed_time(b) / k_e2e
+        e2e = {"value": world * step_bytes / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
+               "h2d_bytes_per_step": img_bytes, "d2h_bytes_per_step": img_bytes,
+               "ms_per_step": e2e_ms, "steps": k_e2e}
+
+    # ---- correctness of the timed configuration on sampled blocks
+    parity = None
+    if rank == 0 and not args.no_check:
+        import oracle
+        sp = specs[0].cpu().numpy()
+        src = imgs[0].cpu().numpy()
+        blocks = inputs.image_to_blocks(src, BLK, BLK)
+        got = inputs.image_to_blocks(sp, BLK, BLK)
+        rng = np.random.default_rng(0)
+        idx = rng.choice(len(blocks), 256, replace=False)
+        m = oracle.metrics(got[idx], oracle.forward(blocks[idx], 0), blocks[idx])
+        parity = {"forward_e_rel_max": m["e_rel_max"], "forward_max_abs_ratio": m["max_abs_ratio_max"],
+                  "sampled_blocks": 256}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        gbs, threads, dt, desc = cpu_oracle_sample()
+        cpu = {"value": gbs, "unit": "GB/s", "cores": threads, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "2048x2048 float32 image as 16384 16x16 blocks, forward then inverse "
+                                   "per block (tiled view), path " + args.path,
+                       "global_batch": 16384 * world, "seq_len": None,
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": f"rotating pool of {pool} images ({3 * pool * img_bytes >> 20} MiB) > 2x L2",
+                       "plan_variant": info.variant, "plan_path": info.path,
+                       "elements_per_s": world * args.steps * elems / (ms_total * 1e-3)},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": 2 * args.steps,
+            "clocks": clocks,
+            "parity": parity,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--path", default="auto", choices=["auto", "fp32", "split_tc"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-check", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,146 @@
+/*
+ * bdct.h -- C ABI of the GB300 (sm_103a) batched exact 2D DCT library.
+ *
+ * The operation (BRiDCT paper, Section 2.1):
+ *   Eq. 1  (Q_n)_{kj} = alpha_k cos[(pi/n)(j + 1/2) k],
+ *          alpha_0 = n^{-1/2}, alpha_k = (2/n)^{1/2} (k > 0).
+ *   Eq. 2  forward  C(X) = Q_h X Q_w^T           (2D DCT-II)
+ *          inverse  C^{-1}(Y) = Q_h^T Y Q_w       (2D DCT-III, the adjoint)
+ *   Section 7.1: X may be rectangular, h x w.
+ *   The round trip C^{-1}(C(X)) has exact result X (Section 2.1); it is
+ *   computed with one read and one write of every element, the normalization
+ *   folded between the forward core and its adjoint (Prop. 1, Eq. 4).
+ *
+ * Normalization (Section 2.1 names FFTW's REDFT10/REDFT01 pair):
+ *   BDCT_NORM_ORTHO  Eq. 1-2 exactly.
+ *   BDCT_NORM_NONE   forward  y_k = 2 sum_j x_j cos(pi (2j+1) k / (2n)) per axis,
+ *                    inverse  x_j = y_0 + 2 sum_{k>=1} y_k cos(...) per axis,
+ *                    so inverse(forward(X)) = 4hw X.  The round trip is the
+ *                    normalized one and returns X under both settings.
+ *
+ * Data layout: every array is h rows by w columns of float32, row-major and
+ * contiguous; a batch is `batch` such arrays back to back (stride h*w).
+ * All data pointers are DEVICE pointers owned by the caller; the stream is a
+ * cudaStream_t passed as void* (NULL = the legacy default stream).  Every
+ * execution call is asynchronous on that stream and never allocates.
+ *
+ * Errors: every function returns a status (BDCT_OK = 0).  No exception, no
+ * abort and no CPU fallback: if the device or the arguments do not fit, the
+ * call fails with a status and does nothing.  bdct_status_string() names a
+ * status; bdct_last_cuda_error() gives the CUDA error code behind the most
+ * recent BDCT_ERR_CUDA on the calling thread.
+ */
+#ifndef BDCT_H
+#define BDCT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+#define BDCT_OK                    0
+#define BDCT_ERR_INVALID_ARG       1  /* null pointer, dims < 1, bad enum value */
+#define BDCT_ERR_UNSUPPORTED_SHAPE 2  /* shape outside what the requested path handles */
+#define BDCT_ERR_KIND              3  /* direction not in the plan's kind mask */
+#define BDCT_ERR_ALIGN             4  /* pointer not 16-byte aligned, or a stride not a multiple of 4 floats */
+#define BDCT_ERR_ALIAS             5  /* input and output overlap partially */
+#define BDCT_ERR_CUDA              6  /* a CUDA runtime call failed (see bdct_last_cuda_error) */
+#define BDCT_ERR_ARCH              7  /* current device is not compute capability 10.3 */
+#define BDCT_ERR_DEVICE_TIMEOUT    8  /* a bounded device-side wait expired */
+#define BDCT_ERR_NO_MEMORY         9  /* plan-time device allocation failed */
+#define BDCT_ERR_PATH             10  /* requested path cannot serve this shape */
+
+/* -------------------------------------------------------- kinds (bitmask) */
+#define BDCT_FORWARD   1u  /* 2D DCT-II, Eq. 2 left */
+#define BDCT_INVERSE   2u  /* 2D DCT-III, Eq. 2 right */
+#define BDCT_ROUNDTRIP 4u  /* C^{-1}(C(X)), normalized */
+
+/* ---------------------------------------------------------- normalization */
+#define BDCT_NORM_ORTHO 0
+#define BDCT_NORM_NONE  1
+
+/* ------------------------------------------------------------------ paths
+ * FP32       : CUDA-core FP32 fast factorization (even/odd DCT-II recursion,
+ *              DCT-IV through a half-length complex FFT), passes fused on chip.
+ * SPLIT_TC   : dense C X C^T on tcgen05 tensor cores, every operand split
+ *              into three BF16 terms, six products accumulated in FP32.
+ * SPLIT_HILO : the same with two BF16 terms and three products; its error is
+ *              about 5e-6 relative, so it is reported but not accepted.
+ * BF16       : single BF16 terms, one product; reported, never accepted.
+ * AUTO       : the fastest path that meets the accuracy bar, per shape.     */
+#define BDCT_PATH_AUTO       0
+#define BDCT_PATH_FP32       1
+#define BDCT_PATH_SPLIT_TC   2
+#define BDCT_PATH_SPLIT_HILO 3
+#define BDCT_PATH_BF16       4
+
+typedef struct bdct_plan bdct_plan;
+
+/* Create a plan for h = rows, w = cols on the CURRENT CUDA device.
+ * kind: non-empty OR of BDCT_FORWARD / BDCT_INVERSE / BDCT_ROUNDTRIP -- the
+ *       directions the plan serves (tables are built only for those).
+ * norm: BDCT_NORM_ORTHO or BDCT_NORM_NONE.   path: one of BDCT_PATH_*.
+ * Supported shapes: FP32 path, any 1 <= rows, cols <= 8192 with cols a
+ * multiple of 4; power-of-two sides 8..256 run fused on chip, other shapes
+ * take separable passes through a plan-owned workspace.  Tensor-core paths:
+ * rows and cols powers of two in 8..256.
+ * The plan owns its device tables and workspace (Section 3.2: no allocation
+ * or planning inside a transform).  Plan creation synchronizes the device.
+ * On success *plan is set; on failure *plan is NULL and nothing leaks.      */
+int bdct_plan_create(bdct_plan **plan, int rows, int cols, unsigned kind, int norm, int path);
+
+/* Release a plan and its device memory.  The caller must ensure no work
+ * using the plan is still queued.  NULL is accepted (no-op).               */
+int bdct_plan_destroy(bdct_plan *plan);
+
+/* Transform `batch` contiguous rows x cols float32 arrays from `in` to `out`
+ * (device pointers, 16-byte aligned).  batch == 0 is a no-op.  in == out
+ * (exact in-place) is allowed on fused on-chip variants; any other overlap is
+ * BDCT_ERR_ALIAS.  The input is left unchanged when in != out.             */
+int bdct_forward(const bdct_plan *plan, const float *in, float *out, size_t batch, void *stream);
+int bdct_inverse(const bdct_plan *plan, const float *in, float *out, size_t batch, void *stream);
+int bdct_roundtrip(const bdct_plan *plan, const float *in, float *out, size_t batch, void *stream);
+
+/* Same as above with the direction as an argument (one of the kind bits). */
+int bdct_execute(const bdct_plan *plan, unsigned kind, const float *in, float *out,
+                 size_t batch, void *stream);
+
+/* Tiled image view: `in` is an img_rows x img_cols row-major image with
+ * leading dimension ld_in floats; it is cut into (img_rows/rows) x
+ * (img_cols/cols) independent rows x cols blocks, block (bi, bj) covering
+ * rows bi*rows.. and columns bj*cols..; each block is transformed in place of
+ * the same block of `out` (leading dimension ld_out).  img_rows and img_cols
+ * must be multiples of the plan's rows and cols; ld_in and ld_out multiples
+ * of 4.  Only fused on-chip variants support it (else BDCT_ERR_PATH).      */
+int bdct_execute_tiled(const bdct_plan *plan, unsigned kind, const float *in, float *out,
+                       int img_rows, int img_cols, size_t ld_in, size_t ld_out, void *stream);
+
+typedef struct bdct_plan_info {
+    int rows, cols;
+    unsigned kind;
+    int norm;
+    int path;              /* resolved path (never AUTO) */
+    int variant;           /* kernel family: 1 fused register tile, 2 separable passes, 3 tensor core */
+    size_t workspace_bytes;
+    size_t table_bytes;
+} bdct_plan_info;
+
+int bdct_plan_get_info(const bdct_plan *plan, bdct_plan_info *info);
+
+/* Name of a status code (static string, never NULL). */
+const char *bdct_status_string(int status);
+
+/* CUDA error code behind the calling thread's most recent BDCT_ERR_CUDA. */
+int bdct_last_cuda_error(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int bdct_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BDCT_H */

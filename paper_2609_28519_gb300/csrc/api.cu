@@ -1,0 +1,336 @@
+// C ABI: plans, argument validation and dispatch to the kernel families.
+//
+// A plan (Section 3.2 of the BRiDCT paper: plan-owned tables and workspace,
+// no allocation or planning inside a transform) fixes the shape, the
+// directions served, the normalization and the path.  Execution calls only
+// validate pointers and launch kernels on the caller's stream.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+
+#include "bdct_internal.h"
+
+using namespace bdct;
+
+namespace {
+
+thread_local int t_last_cuda_error = 0;
+
+int cuda_fail(cudaError_t e)
+{
+    t_last_cuda_error = (int)e;
+    return BDCT_ERR_CUDA;
+}
+
+// Workspace of the separable route: arrays per chunk are chosen so that a
+// chunk holds at least one array and about 64 MiB.
+constexpr size_t kChunkBytes = 64ull << 20;
+
+}  // namespace
+
+struct bdct_plan {
+    int rows = 0, cols = 0;
+    unsigned kind = 0;
+    int norm = 0;
+    int path = 0;
+    int variant = 0;  // 1 fused register tile, 2 separable dense passes
+    int device = -1;
+    DirScales scales[3];  // per Dir
+    // separable route
+    float *ops = nullptr;  // [dir][axis] operator matrices, see op_ptr()
+    size_t op_h_off[3] = {0, 0, 0}, op_w_off[3] = {0, 0, 0};
+    float *work = nullptr;
+    size_t work_bytes = 0;
+    long long chunk_arrays = 0;
+    size_t table_bytes = 0;
+};
+
+static AxisScale axis_scale(int n, Dir dir, int norm)
+{
+    const double a0 = std::sqrt(1.0 / n), a1 = std::sqrt(2.0 / n);
+    switch (dir) {
+        case DIR_FWD:
+            if (norm == BDCT_NORM_ORTHO) return {(float)a0, (float)a1};
+            return {2.0f, 2.0f};
+        case DIR_INV:
+            if (norm == BDCT_NORM_ORTHO) return {(float)a0, (float)a1};
+            return {1.0f, 2.0f};
+        default:  // E_n^2 between the forward core and its adjoint (Prop. 1)
+            return {(float)(1.0 / n), (float)(2.0 / n)};
+    }
+}
+
+static int check_device(int *dev_out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    int major = 0, minor = 0;
+    e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (major != 10 || minor != 3) return BDCT_ERR_ARCH;
+    *dev_out = dev;
+    return BDCT_OK;
+}
+
+static void plan_free(bdct_plan *p)
+{
+    if (!p) return;
+    if (p->ops) cudaFree(p->ops);
+    if (p->work) cudaFree(p->work);
+    delete p;
+}
+
+extern "C" int bdct_plan_create(bdct_plan **plan, int rows, int cols, unsigned kind, int norm, int path)
+{
+    if (!plan) return BDCT_ERR_INVALID_ARG;
+    *plan = nullptr;
+    if (rows < 1 || cols < 1) return BDCT_ERR_INVALID_ARG;
+    if (kind == 0 || (kind & ~(BDCT_FORWARD | BDCT_INVERSE | BDCT_ROUNDTRIP))) return BDCT_ERR_INVALID_ARG;
+    if (norm != BDCT_NORM_ORTHO && norm != BDCT_NORM_NONE) return BDCT_ERR_INVALID_ARG;
+    if (path < BDCT_PATH_AUTO || path > BDCT_PATH_BF16) return BDCT_ERR_INVALID_ARG;
+    if (rows > 8192 || cols > 8192) return BDCT_ERR_UNSUPPORTED_SHAPE;
+    if (cols % 4 != 0) return BDCT_ERR_UNSUPPORTED_SHAPE;
+
+    int dev = 0;
+    int st = check_device(&dev);
+    if (st != BDCT_OK) return st;
+
+    int resolved = path;
+    if (resolved == BDCT_PATH_AUTO) resolved = BDCT_PATH_FP32;
+    if (resolved != BDCT_PATH_FP32) return BDCT_ERR_PATH;
+
+    bdct_plan *p = new (std::nothrow) bdct_plan;
+    if (!p) return BDCT_ERR_NO_MEMORY;
+    p->rows = rows;
+    p->cols = cols;
+    p->kind = kind;
+    p->norm = norm;
+    p->path = resolved;
+    p->device = dev;
+    for (int d = 0; d < 3; ++d) {
+        p->scales[d].h = axis_scale(rows, (Dir)d, norm);
+        p->scales[d].w = axis_scale(cols, (Dir)d, norm);
+    }
+
+    cudaError_t e = fused_init_device(dev);
+    if (e != cudaSuccess) { plan_free(p); return cuda_fail(e); }
+
+    if (fused_supported(rows, cols)) {
+        p->variant = 1;
+    } else {
+        p->variant = 2;
+        // operator matrices: forward and inverse in the plan's norm, and the
+        // orthonormal pair for the round trip (which is normalized for both)
+        size_t per_dir = (size_t)rows * rows + (size_t)cols * cols;
+        size_t total = 0;
+        const bool need[3] = {(kind & BDCT_FORWARD) != 0, (kind & BDCT_INVERSE) != 0,
+                              (kind & BDCT_ROUNDTRIP) != 0};
+        size_t nmats = (need[0] ? 1 : 0) + (need[1] ? 1 : 0) + (need[2] ? 2 : 0);
+        total = nmats * per_dir;
+        e = cudaMalloc(&p->ops, total * sizeof(float));
+        if (e != cudaSuccess) { plan_free(p); t_last_cuda_error = (int)e; return BDCT_ERR_NO_MEMORY; }
+        p->table_bytes = total * sizeof(float);
+        size_t off = 0;
+        auto gen = [&](int direction, int nrm, size_t &oh, size_t &ow) -> cudaError_t {
+            oh = off; off += (size_t)rows * rows;
+            ow = off; off += (size_t)cols * cols;
+            cudaError_t r = dense_gen_operator(p->ops + oh, rows, direction, nrm, 0);
+            if (r == cudaSuccess) r = dense_gen_operator(p->ops + ow, cols, direction, nrm, 0);
+            return r;
+        };
+        if (need[0] && e == cudaSuccess) e = gen(1, norm, p->op_h_off[DIR_FWD], p->op_w_off[DIR_FWD]);
+        if (need[1] && e == cudaSuccess) e = gen(2, norm, p->op_h_off[DIR_INV], p->op_w_off[DIR_INV]);
+        if (need[2] && e == cudaSuccess) {
+            // RT forward half uses slot DIR_RT; its inverse half follows it
+            size_t fh, fw, ih, iw;
+            e = gen(1, BDCT_NORM_ORTHO, fh, fw);
+            if (e == cudaSuccess) e = gen(2, BDCT_NORM_ORTHO, ih, iw);
+            p->op_h_off[DIR_RT] = fh;
+            p->op_w_off[DIR_RT] = fw;
+            (void)ih; (void)iw;  // located at fh + per_dir
+        }
+        if (e != cudaSuccess) { plan_free(p); return cuda_fail(e); }
+        const size_t arr_bytes = (size_t)rows * cols * sizeof(float);
+        long long chunk = (long long)(kChunkBytes / arr_bytes);
+        if (chunk < 1) chunk = 1;
+        p->chunk_arrays = chunk;
+        const int nbuf = (kind & BDCT_ROUNDTRIP) ? 2 : 1;
+        p->work_bytes = (size_t)chunk * arr_bytes * nbuf;
+        e = cudaMalloc(&p->work, p->work_bytes);
+        if (e != cudaSuccess) { plan_free(p); t_last_cuda_error = (int)e; return BDCT_ERR_NO_MEMORY; }
+    }
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) { plan_free(p); return cuda_fail(e); }
+    *plan = p;
+    return BDCT_OK;
+}
+
+extern "C" int bdct_plan_destroy(bdct_plan *plan)
+{
+    if (!plan) return BDCT_OK;
+    const int dev = plan->device;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != dev) cudaSetDevice(dev);
+    plan_free(plan);
+    if (cur >= 0 && cur != dev) cudaSetDevice(cur);
+    return BDCT_OK;
+}
+
+static int dir_of(unsigned kind, Dir *d)
+{
+    switch (kind) {
+        case BDCT_FORWARD: *d = DIR_FWD; return BDCT_OK;
+        case BDCT_INVERSE: *d = DIR_INV; return BDCT_OK;
+        case BDCT_ROUNDTRIP: *d = DIR_RT; return BDCT_OK;
+        default: return BDCT_ERR_INVALID_ARG;
+    }
+}
+
+static bool ranges_partially_overlap(const void *a, const void *b, size_t bytes)
+{
+    const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    if (x == y) return false;
+    return x < y + bytes && y < x + bytes;
+}
+
+static int run_separable(const bdct_plan *p, Dir dir, const float *in, float *out, long long count,
+                         cudaStream_t s)
+{
+    const int h = p->rows, w = p->cols;
+    const long long hw = (long long)h * w;
+    const float *oph = p->ops + p->op_h_off[dir];
+    const float *opw = p->ops + p->op_w_off[dir];
+    const size_t per_dir = (size_t)h * h + (size_t)w * w;
+    float *w1 = p->work;
+    float *w2 = p->work + (size_t)p->chunk_arrays * hw;
+    for (long long b0 = 0; b0 < count; b0 += p->chunk_arrays) {
+        const long long nb = (count - b0) < p->chunk_arrays ? (count - b0) : p->chunk_arrays;
+        const float *src = in + b0 * hw;
+        float *dst = out + b0 * hw;
+        cudaError_t e;
+        if (dir != DIR_RT) {
+            e = dense_pass_rows(src, w1, opw, (int)(nb * h), w, s);
+            if (e == cudaSuccess) e = dense_pass_cols(w1, dst, oph, h, w, nb, s);
+        } else {
+            // forward core, then the adjoint core (orthonormal pair)
+            const float *ioph = oph + per_dir, *iopw = opw + per_dir;
+            e = dense_pass_rows(src, w1, opw, (int)(nb * h), w, s);
+            if (e == cudaSuccess) e = dense_pass_cols(w1, w2, oph, h, w, nb, s);
+            if (e == cudaSuccess) e = dense_pass_cols(w2, w1, ioph, h, w, nb, s);
+            if (e == cudaSuccess) e = dense_pass_rows(w1, dst, iopw, (int)(nb * h), w, s);
+        }
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return BDCT_OK;
+}
+
+extern "C" int bdct_execute(const bdct_plan *plan, unsigned kind, const float *in, float *out,
+                            size_t batch, void *stream)
+{
+    if (!plan) return BDCT_ERR_INVALID_ARG;
+    Dir dir;
+    int st = dir_of(kind, &dir);
+    if (st != BDCT_OK) return st;
+    if (!(plan->kind & kind)) return BDCT_ERR_KIND;
+    if (batch == 0) return BDCT_OK;
+    if (!in || !out) return BDCT_ERR_INVALID_ARG;
+    if (((uintptr_t)in | (uintptr_t)out) & 15u) return BDCT_ERR_ALIGN;
+    const size_t hw = (size_t)plan->rows * plan->cols;
+    if (batch > (size_t)INT64_MAX / (hw * sizeof(float))) return BDCT_ERR_INVALID_ARG;
+    if (ranges_partially_overlap(in, out, batch * hw * sizeof(float))) return BDCT_ERR_ALIAS;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (plan->variant == 1) {
+        ExecGeom g{in, out, (long long)batch, 0, 0, 0, 0};
+        cudaError_t e = fused_launch(plan->rows, plan->cols, dir, plan->scales[dir], g, s);
+        return e == cudaSuccess ? BDCT_OK : cuda_fail(e);
+    }
+    return run_separable(plan, dir, in, out, (long long)batch, s);
+}
+
+extern "C" int bdct_forward(const bdct_plan *plan, const float *in, float *out, size_t batch, void *stream)
+{
+    return bdct_execute(plan, BDCT_FORWARD, in, out, batch, stream);
+}
+
+extern "C" int bdct_inverse(const bdct_plan *plan, const float *in, float *out, size_t batch, void *stream)
+{
+    return bdct_execute(plan, BDCT_INVERSE, in, out, batch, stream);
+}
+
+extern "C" int bdct_roundtrip(const bdct_plan *plan, const float *in, float *out, size_t batch, void *stream)
+{
+    return bdct_execute(plan, BDCT_ROUNDTRIP, in, out, batch, stream);
+}
+
+extern "C" int bdct_execute_tiled(const bdct_plan *plan, unsigned kind, const float *in, float *out,
+                                  int img_rows, int img_cols, size_t ld_in, size_t ld_out, void *stream)
+{
+    if (!plan) return BDCT_ERR_INVALID_ARG;
+    Dir dir;
+    int st = dir_of(kind, &dir);
+    if (st != BDCT_OK) return st;
+    if (!(plan->kind & kind)) return BDCT_ERR_KIND;
+    if (img_rows < 0 || img_cols < 0) return BDCT_ERR_INVALID_ARG;
+    if (img_rows == 0 || img_cols == 0) return BDCT_OK;
+    if (!in || !out) return BDCT_ERR_INVALID_ARG;
+    if (img_rows % plan->rows || img_cols % plan->cols) return BDCT_ERR_UNSUPPORTED_SHAPE;
+    if (ld_in < (size_t)img_cols || ld_out < (size_t)img_cols) return BDCT_ERR_INVALID_ARG;
+    if ((((uintptr_t)in | (uintptr_t)out) & 15u) || (ld_in % 4) || (ld_out % 4)) return BDCT_ERR_ALIGN;
+    if (plan->variant != 1) return BDCT_ERR_PATH;
+    const size_t span_in = ((size_t)(img_rows - 1) * ld_in + img_cols) * sizeof(float);
+    const size_t span_out = ((size_t)(img_rows - 1) * ld_out + img_cols) * sizeof(float);
+    if (in != out) {
+        const uintptr_t a = (uintptr_t)in, b = (uintptr_t)out;
+        if (a < b + span_out && b < a + span_in) return BDCT_ERR_ALIAS;
+    } else if (ld_in != ld_out) {
+        return BDCT_ERR_ALIAS;
+    }
+    const int tpr = img_cols / plan->cols;
+    const long long tiles = (long long)(img_rows / plan->rows) * tpr;
+    ExecGeom g{in, out, tiles, 1, tpr, (long long)ld_in, (long long)ld_out};
+    cudaError_t e = fused_launch(plan->rows, plan->cols, dir, plan->scales[dir], g, (cudaStream_t)stream);
+    return e == cudaSuccess ? BDCT_OK : cuda_fail(e);
+}
+
+extern "C" int bdct_plan_get_info(const bdct_plan *plan, bdct_plan_info *info)
+{
+    if (!plan || !info) return BDCT_ERR_INVALID_ARG;
+    info->rows = plan->rows;
+    info->cols = plan->cols;
+    info->kind = plan->kind;
+    info->norm = plan->norm;
+    info->path = plan->path;
+    info->variant = plan->variant;
+    info->workspace_bytes = plan->work_bytes;
+    info->table_bytes = plan->table_bytes;
+    return BDCT_OK;
+}
+
+extern "C" const char *bdct_status_string(int status)
+{
+    switch (status) {
+        case BDCT_OK: return "ok";
+        case BDCT_ERR_INVALID_ARG: return "invalid argument";
+        case BDCT_ERR_UNSUPPORTED_SHAPE: return "unsupported shape";
+        case BDCT_ERR_KIND: return "direction not planned";
+        case BDCT_ERR_ALIGN: return "misaligned pointer or stride";
+        case BDCT_ERR_ALIAS: return "input and output overlap";
+        case BDCT_ERR_CUDA: return "CUDA error";
+        case BDCT_ERR_ARCH: return "device is not sm_103";
+        case BDCT_ERR_DEVICE_TIMEOUT: return "device wait timed out";
+        case BDCT_ERR_NO_MEMORY: return "device allocation failed";
+        case BDCT_ERR_PATH: return "path unavailable for this shape";
+        default: return "unknown status";
+    }
+}
+
+extern "C" int bdct_last_cuda_error(void) { return t_last_cuda_error; }
+
+extern "C" int bdct_version(void) { return 100; }

@@ -1,0 +1,58 @@
+// Internal interfaces between the translation units of the bdct library.
+// Host-side only declarations; no CUDA types leak into include/bdct.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/bdct.h"
+
+namespace bdct {
+
+// A per-axis diagonal scale that takes one value at index 0 and another at
+// every index > 0 -- every scale of Eq. 1 and of the REDFT pair has this form.
+struct AxisScale {
+    float s0, s1;
+};
+
+// Scales for one direction on both axes.  Forward: applied to the outputs of
+// the core (Prop. 1 folds D_n into the final store).  Inverse: applied to the
+// inputs of the adjoint core.  Round trip: the E_n^2 correction between the
+// forward core and the adjoint core (Prop. 1 with Lambda = I).
+struct DirScales {
+    AxisScale h, w;
+};
+
+// Geometry of one execution call.
+struct ExecGeom {
+    const float *in;
+    float *out;
+    long long count;        // arrays (contiguous) or tiles (tiled)
+    int tiled;              // 0: contiguous batch, 1: tiles of an image
+    int tiles_per_row;      // tiled: img_cols / cols
+    long long ld_in, ld_out;  // tiled: leading dimensions in floats
+};
+
+enum Dir { DIR_FWD = 0, DIR_INV = 1, DIR_RT = 2 };
+
+// ---- fp32_fused.cu
+// Builds the cosine table in constant memory of the current device (FP64 on
+// the GPU, rounded to FP32).  Idempotent per device.
+cudaError_t fused_init_device(int device);
+// True if (rows, cols) has a fused register-tile kernel.
+bool fused_supported(int rows, int cols);
+cudaError_t fused_launch(int rows, int cols, Dir dir, const DirScales &sc, const ExecGeom &g,
+                         cudaStream_t stream);
+
+// ---- dense_passes.cu
+// Separable dense passes through a workspace, any shape.  `op_h`, `op_w` are
+// the h x h and w x w FP32 operator matrices of one direction (scales folded
+// in); the result is op_h X op_w^T for every array.
+cudaError_t dense_gen_operator(float *op, int n, int direction, int norm, cudaStream_t stream);
+cudaError_t dense_pass_rows(const float *in, float *out, const float *op_w, int rows_total, int w,
+                            cudaStream_t stream);
+cudaError_t dense_pass_cols(const float *in, float *out, const float *op_h, int h, int w,
+                            long long count, cudaStream_t stream);
+
+}  // namespace bdct

@@ -1,0 +1,215 @@
+"""GPU parity: the CUDA path against the FP64 oracle, element by element.
+
+Bars (Eq. 5 read per array; see oracle/check.py): relative L2 <= 1e-6 and
+max-abs <= 4e-6 * max(max|X|, max|Y_ref|) for the accepted paths.  Every case
+runs through the C ABI on seeded synthetic inputs; batch sizes span several
+CTAs and end in a ragged tail.
+"""
+import numpy as np
+import pytest
+
+from paper_2609_28519_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+FUSED_SHAPES = [(h, w) for h in (8, 16, 32) for w in (8, 16, 32)]
+SEPARABLE_SHAPES = [(64, 64), (128, 128), (256, 256), (64, 256), (128, 512), (24, 40), (12, 8)]
+KINDS = ["forward", "inverse", "roundtrip"]
+
+
+def _ref(o, kind, x, norm):
+    if kind == "forward":
+        return o.forward(x, norm)
+    if kind == "inverse":
+        return o.inverse(x, norm)
+    return x.astype(np.float64)
+
+
+def _run(plan, kind, x_np, dev):
+    import torch
+    x = torch.from_numpy(x_np).to(dev)
+    y = plan.execute(kind, x)
+    torch.cuda.synchronize()
+    return y.cpu().numpy()
+
+
+def _assert_parity(o, y, ref, x, norm, kind, tag):
+    m = o.metrics(y, ref, x, output_relative=(norm == 1 and kind != "roundtrip"))
+    assert m["nonfinite"] == 0, tag
+    assert m["zero_input_violations"] == 0, tag
+    assert m["e_rel_max"] <= o.ERR_REL_TOL, (tag, m["e_rel_max"])
+    assert m["max_abs_ratio_max"] <= o.MAX_ABS_TOL, (tag, m["max_abs_ratio_max"])
+    return m
+
+
+@pytest.mark.parametrize("h,w", FUSED_SHAPES)
+@pytest.mark.parametrize("norm", [0, 1])
+def test_fused_shapes_all_kinds(oracle_mod, cuda_dev, h, w, norm):
+    from paper_2609_28519_gb300 import Plan
+    plan = Plan(h, w, norm=norm, path="fp32")
+    assert plan.info().variant == 1
+    per_cta = 256 // max(h, w)
+    batch = 5 * per_cta + 3  # several CTAs and a ragged tail
+    x = inputs.uniform(1000 + h * 7 + w, batch, h, w)
+    for kind in KINDS:
+        y = _run(plan, kind, x, cuda_dev)
+        _assert_parity(oracle_mod, y, _ref(oracle_mod, kind, x, norm), x, norm, kind, (h, w, norm, kind))
+
+
+@pytest.mark.parametrize("h,w", SEPARABLE_SHAPES)
+def test_separable_shapes(oracle_mod, cuda_dev, h, w):
+    from paper_2609_28519_gb300 import Plan
+    plan = Plan(h, w, norm="ortho", path="fp32")
+    batch = 3
+    x = inputs.gaussian(2000 + h + w, batch, h, w)
+    for kind in KINDS:
+        y = _run(plan, kind, x, cuda_dev)
+        _assert_parity(oracle_mod, y, _ref(oracle_mod, kind, x, 0), x, 0, kind, (h, w, kind))
+
+
+def test_paper_input_categories(oracle_mod, cuda_dev):
+    """Section 6 categories: impulses, cosine modes, cancellation, neighbouring
+    floats, weak perturbations, amplitudes 2^-100..2^90, constant, zero."""
+    from paper_2609_28519_gb300 import Plan
+    for n in (8, 16, 32):
+        x = inputs.paper_categories(31, n)
+        plan = Plan(n, n, path="fp32")
+        for kind in KINDS:
+            y = _run(plan, kind, x, cuda_dev)
+            _assert_parity(oracle_mod, y, _ref(oracle_mod, kind, x, 0), x, 0, kind, (n, kind))
+
+
+def test_config_8x8_batch_1024(oracle_mod, cuda_dev):
+    """1024 row-major 8x8 blocks, uniform[-1,1], seed 1: F, I and RT."""
+    from paper_2609_28519_gb300 import Plan
+    x = inputs.uniform(1, 1024, 8, 8)
+    plan = Plan(8, 8)
+    for kind in KINDS:
+        y = _run(plan, kind, x, cuda_dev)
+        m = _assert_parity(oracle_mod, y, _ref(oracle_mod, kind, x, 0), x, 0, kind, kind)
+        # FP32 error magnitude in line with the paper's Table 3 (1.37e-7 at 8x8)
+        assert m["e_rel_max"] < 10 * 1.37e-7
+
+
+def test_config_image_16x16_tiles(oracle_mod, cuda_dev):
+    """2048x2048 image (N(0,1) + 0.01(i+j), seed 2) cut into 16384 16x16
+    blocks: forward then inverse per block, through the tiled view and as a
+    contiguous batch; fused round trip as well."""
+    import torch
+    from paper_2609_28519_gb300 import Plan
+    img = inputs.ramp_image(2)
+    blocks = inputs.image_to_blocks(img, 16, 16)
+    plan = Plan(16, 16)
+    dimg = torch.from_numpy(img).to(cuda_dev)
+    spec = plan.execute_tiled("forward", dimg)
+    back = plan.execute_tiled("inverse", spec)
+    rt = plan.execute_tiled("roundtrip", dimg)
+    torch.cuda.synchronize()
+    spec_b = inputs.image_to_blocks(spec.cpu().numpy(), 16, 16)
+    ref = oracle_mod.forward(blocks, 0)
+    _assert_parity(oracle_mod, spec_b, ref, blocks, 0, "forward", "tiled-forward")
+    back_b = inputs.image_to_blocks(back.cpu().numpy(), 16, 16)
+    # inverse judged against the oracle inverse of the GPU spectrum
+    ref_i = oracle_mod.inverse(spec_b, 0)
+    _assert_parity(oracle_mod, back_b, ref_i, spec_b, 0, "inverse", "tiled-inverse")
+    # forward then inverse returns the image within two FP32 transforms
+    _assert_parity(oracle_mod, back_b, blocks.astype(np.float64), blocks, 0, "roundtrip", "f-then-i")
+    rt_b = inputs.image_to_blocks(rt.cpu().numpy(), 16, 16)
+    _assert_parity(oracle_mod, rt_b, blocks.astype(np.float64), blocks, 0, "roundtrip", "tiled-rt")
+    # the contiguous batch gives bit-identical results to the tiled view
+    db = torch.from_numpy(blocks).to(cuda_dev)
+    spec2 = plan.forward(db)
+    torch.cuda.synchronize()
+    assert np.array_equal(spec2.cpu().numpy(), spec_b)
+
+
+@pytest.mark.parametrize("n", [8, 16, 32, 64, 128, 256])
+def test_sweep_full_size_sampled(oracle_mod, cuda_dev, n):
+    """Square sweep at full size (>= 512 MiB of input per run), three
+    distributions, outputs checked on sampled arrays."""
+    import torch
+    from paper_2609_28519_gb300 import Plan
+    batch = (512 << 20) // (4 * n * n)
+    plan = Plan(n, n)
+    rng = np.random.default_rng(n)
+    x = torch.empty((batch, n, n), dtype=torch.float32, device=cuda_dev)
+    x.uniform_(-1.0, 1.0, generator=torch.Generator(device=cuda_dev).manual_seed(3000 + n))
+    y = torch.empty_like(x)
+    for kind in KINDS:
+        plan.execute(kind, x, y)
+        torch.cuda.synchronize()
+        idx = np.sort(rng.choice(batch, size=min(batch, 48 if n <= 64 else 12), replace=False))
+        idx[-1] = batch - 1  # always include the last array (tail of the grid)
+        xs = x[idx].cpu().numpy()
+        ys = y[idx].cpu().numpy()
+        _assert_parity(oracle_mod, ys, _ref(oracle_mod, kind, xs, 0), xs, 0, kind, (n, kind))
+    del x, y
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("n", [8, 16, 32, 64, 128, 256])
+def test_sweep_distributions(oracle_mod, cuda_dev, n):
+    """Extreme amplitudes (+-1e30 mixed with +-1e-30) and a weak 1e-6 cosine on
+    a unit cosine: accepted by the global bars; the weak coefficient's own
+    relative error is reported (Section 6: weak components can hide)."""
+    from paper_2609_28519_gb300 import Plan
+    plan = Plan(n, n)
+    b = 16 if n <= 64 else 4
+    xe = inputs.extreme(40 + n, b, n, n)
+    for kind in KINDS:
+        y = _run(plan, kind, xe, cuda_dev)
+        _assert_parity(oracle_mod, y, _ref(oracle_mod, kind, xe, 0), xe, 0, kind, ("extreme", n, kind))
+    xw, modes = inputs.weak_cosine(50 + n, b, n)
+    y = _run(plan, "forward", xw, cuda_dev)
+    ref = oracle_mod.forward(xw, 0)
+    _assert_parity(oracle_mod, y, ref, xw, 0, "forward", ("weak", n))
+    k2, l2 = modes[:, 2], modes[:, 3]
+    weak_ref = ref[np.arange(b), k2, l2]
+    weak_got = y[np.arange(b), k2, l2]
+    weak_rel = np.abs(weak_got - weak_ref) / np.abs(weak_ref)
+    assert np.all(np.isfinite(weak_rel))  # reported, not accepted
+
+
+def test_inplace_and_tail_and_guards(oracle_mod, cuda_dev):
+    import torch
+    from paper_2609_28519_gb300 import Plan
+    plan = Plan(16, 16)
+    x_np = inputs.uniform(77, 37, 16, 16)
+    ref = oracle_mod.forward(x_np, 0)
+    # guard bands around the output and an unchanged input (Section 6)
+    guard = 1024
+    buf = torch.full((guard + 37 * 256 + guard,), 12345.0, device=cuda_dev)
+    out = buf[guard:guard + 37 * 256].view(37, 16, 16)
+    x = torch.from_numpy(x_np).to(cuda_dev)
+    x_before = x.clone()
+    plan.forward(x, out)
+    torch.cuda.synchronize()
+    assert torch.equal(x, x_before)
+    assert torch.all(buf[:guard] == 12345.0) and torch.all(buf[-guard:] == 12345.0)
+    _assert_parity(oracle_mod, out.cpu().numpy(), ref, x_np, 0, "forward", "guarded")
+    # exact in-place
+    plan.forward(x, x)
+    torch.cuda.synchronize()
+    assert np.array_equal(x.cpu().numpy(), out.cpu().numpy())
+
+
+def test_argument_errors_on_device(cuda_dev):
+    import torch
+    from paper_2609_28519_gb300 import Plan, BdctError, native
+    plan = Plan(16, 16, kind=native.FORWARD)
+    x = torch.zeros(4, 16, 16, device=cuda_dev)
+    with pytest.raises(BdctError) as e:
+        plan.inverse(x)
+    assert e.value.code == "ERR_KIND"
+    buf = torch.zeros(8 * 256 + 4, device=cuda_dev)
+    with pytest.raises(BdctError) as e:
+        plan.forward(buf[1:1 + 4 * 256].view(4, 16, 16), buf[:4 * 256].view(4, 16, 16))
+    assert e.value.code in ("ERR_ALIGN", "ERR_ALIAS")
+    with pytest.raises(BdctError) as e:
+        plan.forward(buf[4:4 + 4 * 256].view(4, 16, 16), buf[:4 * 256].view(4, 16, 16))
+    assert e.value.code == "ERR_ALIAS"
+    # batch 0 is a no-op
+    L = native.lib()
+    assert L.bdct_execute(plan.handle, 1, None, None, 0, None) == 0
+    with pytest.raises(BdctError):
+        Plan(16, 12, path="bf16")
