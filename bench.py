@@ -238,8 +238,42 @@ def run_ours(args):
         step(i)
     torch.cuda.synchronize()
 
-    # ---- timed region: K steps, per-launch CUDA events on the launch stream
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    # The steps are tiny (16 MiB per launch), so host launch latency would
+    # dominate a Python loop: the K timed steps are captured once into a CUDA
+    # graph and replayed, which feeds the GPU back to back.
+    def capture(fn):
+        g = torch.cuda.CUDAGraph()
+        cs = torch.cuda.Stream(dev)
+        cs.wait_stream(stream)
+        with torch.cuda.graph(g, stream=cs):
+            fn(c_void_p(cs.cuda_stream))
+        torch.cuda.synchronize()
+        return g
+
+    def steps_fn(sp):
+        for i in range(args.steps):
+            k = i % pool
+            st = ex(h, native.FORWARD, ptr_in[k], ptr_sp[k], IMG, IMG, IMG, IMG, sp)
+            st |= ex(h, native.INVERSE, ptr_sp[k], ptr_out[k], IMG, IMG, IMG, IMG, sp)
+            if st:
+                raise RuntimeError(f"bdct_execute_tiled failed: {st}")
+
+    def only_fn(kind, src, dst):
+        def fn(sp):
+            for i in range(args.steps):
+                k = i % pool
+                if ex(h, kind, src[k], dst[k], IMG, IMG, IMG, IMG, sp):
+                    raise RuntimeError("bdct_execute_tiled failed")
+        return fn
+
+    g_steps = capture(steps_fn)
+    g_fwd = capture(only_fn(native.FORWARD, ptr_in, ptr_sp))
+    g_inv = capture(only_fn(native.INVERSE, ptr_sp, ptr_out))
+    for g in (g_steps, g_fwd, g_inv):
+        g.replay()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps (graph replay), CUDA events on the launch stream
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     sampler = ClockSampler(local)
@@ -249,35 +283,41 @@ def run_ours(args):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     t_start.record(stream)
-    for i in range(args.steps):
-        step(i, evs[i])
+    g_steps.replay()
     t_end.record(stream)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
+    # per-kernel averages: the same K launches of one kernel alone, same pool
+    kt = {}
+    for name, g in (("forward", g_fwd), ("inverse", g_inv)):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        g.replay()
+        b.record(stream)
+        torch.cuda.synchronize()
+        kt[name] = a.elapsed_time(b) / args.steps
     clocks = sampler.stop()
     ms_total = t_start.elapsed_time(t_end)
     if world > 1:
         t = torch.tensor([ms_total], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms_total = float(t.item())
-    fwd_ms = [e[0].elapsed_time(e[1]) for e in evs]
-    inv_ms = [e[1].elapsed_time(e[2]) for e in evs]
     elems = IMG * IMG
     step_bytes = elems * BYTES_PER_ELEM_STEP
     value = world * args.steps * step_bytes / (ms_total * 1e-3) / 1e9
 
-    # ---- dominant kernel roofline (forward fused kernel; 8 B/element/launch)
-    fwd_avg = sum(fwd_ms) / len(fwd_ms)
-    inv_avg = sum(inv_ms) / len(inv_ms)
-    dom_key, dom_avg = ("k_fused_small<16,16,FWD,tiled>", fwd_avg) if fwd_avg >= inv_avg else \
-        ("k_fused_small<16,16,INV,tiled>", inv_avg)
+    # ---- dominant kernel roofline (8 B/element/launch)
+    fwd_avg, inv_avg = kt["forward"], kt["inverse"]
+    dom_key, dom_avg = ("k_fused<16,16,FWD,tiled>", fwd_avg) if fwd_avg >= inv_avg else \
+        ("k_fused<16,16,INV,tiled>", inv_avg)
     peak, peak_kind = _peaks()
     achieved = elems * 8 / (dom_avg * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic_from_profiles(dom_key),
-                "kernel": dom_key, "peak_source": f"{peak_kind} hbm_gbs",
-                "avg_launch_us": {"forward": fwd_avg * 1e3, "inverse": inv_avg * 1e3}}
+                "kernel": dom_key, "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
+                "avg_launch_us": {"forward": fwd_avg * 1e3, "inverse": inv_avg * 1e3},
+                "timing": "K back-to-back launches of the kernel alone (CUDA graph), same rotating pool"}
 
     # ---- end to end through host buffers (pinned), copies inside the timed region
     e2e = None
@@ -343,12 +383,49 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": 2 * args.steps,
+            "launch": "CUDA graph of the K steps (2 kernels per step)",
             "clocks": clocks,
             "parity": parity,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_sweep(args):
+    """Square-size sweep: n in {8..256}, batch so each run moves >= 512 MiB,
+    forward / inverse / round trip, GB/s on 8 B per element per call.  One
+    JSON line per (size, kind); not the headline line."""
+    import torch
+    from paper_2609_28519_gb300 import Plan
+    dev = torch.device("cuda", 0)
+    peak, _ = _peaks()
+    sizes = [int(v) for v in args.sizes.split(",")]
+    for n in sizes:
+        batch = (512 << 20) // (4 * n * n)
+        x = torch.empty((batch, n, n), dtype=torch.float32, device=dev).uniform_(-1, 1)
+        y = torch.empty_like(x)
+        plan = Plan(n, n, path=args.path)
+        for kind in ("forward", "inverse", "roundtrip"):
+            for _ in range(3):
+                plan.execute(kind, x, y)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 10
+            a.record()
+            for _ in range(reps):
+                plan.execute(kind, x, y)
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / reps
+            gbs = batch * n * n * 8 / (ms * 1e-3) / 1e9
+            print(json.dumps({"sweep": True, "n": n, "batch": batch, "kind": kind, "path": args.path,
+                              "variant": plan.info().variant, "ms": ms, "GB/s": gbs,
+                              "frac_of_measured_hbm": gbs / peak}), flush=True)
+        plan.close()
+        del x, y
+        torch.cuda.empty_cache()
     return 0
 
 
@@ -361,11 +438,15 @@ def main():
     ap.add_argument("--path", default="auto", choices=["auto", "fp32", "split_tc"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--sweep", action="store_true", help="square-size sweep instead of the headline")
+    ap.add_argument("--sizes", default="8,16,32,64,128,256")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.sweep:
+        return run_sweep(args)
     return run_ours(args)
 
 

@@ -130,6 +130,20 @@ typedef struct bdct_plan_info {
 
 int bdct_plan_get_info(const bdct_plan *plan, bdct_plan_info *info);
 
+/* Synchronize the device and return the plan's device-side status: BDCT_OK,
+ * or BDCT_ERR_DEVICE_TIMEOUT if a bounded wait inside one of the plan's
+ * kernels gave up since the last clear (the kernel then stopped early and its
+ * output is incomplete).  clear != 0 resets the word.  Host errors are
+ * returned as usual.                                                         */
+int bdct_plan_device_status(const bdct_plan *plan, int clear);
+
+/* Self-test of the bounded device-side wait: launches one thread that waits
+ * on a barrier nothing completes, with a limit of limit_us microseconds
+ * (1..2000000), and returns the status it recorded -- BDCT_ERR_DEVICE_TIMEOUT
+ * when the bounded wait behaves, with the CUDA context still usable.  No
+ * counterpart in the paper: it tests the library's failure detection.       */
+int bdct_selftest_wait_timeout(unsigned int limit_us);
+
 /* Name of a status code (static string, never NULL). */
 const char *bdct_status_string(int status);
 

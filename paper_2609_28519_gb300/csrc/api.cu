@@ -46,6 +46,7 @@ struct bdct_plan {
     size_t work_bytes = 0;
     long long chunk_arrays = 0;
     size_t table_bytes = 0;
+    unsigned int *status = nullptr;  // device status word written by bounded waits
 };
 
 static AxisScale axis_scale(int n, Dir dir, int norm)
@@ -82,6 +83,7 @@ static void plan_free(bdct_plan *p)
 {
     if (!p) return;
     if (p->ops) cudaFree(p->ops);
+    if (p->status) cudaFree(p->status);
     if (p->work) cudaFree(p->work);
     delete p;
 }
@@ -119,6 +121,10 @@ extern "C" int bdct_plan_create(bdct_plan **plan, int rows, int cols, unsigned k
     }
 
     cudaError_t e = fused_init_device(dev);
+    if (e != cudaSuccess) { plan_free(p); return cuda_fail(e); }
+    e = cudaMalloc(&p->status, sizeof(unsigned int));
+    if (e != cudaSuccess) { plan_free(p); t_last_cuda_error = (int)e; return BDCT_ERR_NO_MEMORY; }
+    e = cudaMemset(p->status, 0, sizeof(unsigned int));
     if (e != cudaSuccess) { plan_free(p); return cuda_fail(e); }
 
     if (fused_supported(rows, cols)) {
@@ -248,7 +254,7 @@ extern "C" int bdct_execute(const bdct_plan *plan, unsigned kind, const float *i
     cudaStream_t s = (cudaStream_t)stream;
     if (plan->variant == 1) {
         ExecGeom g{in, out, (long long)batch, 0, 0, 0, 0};
-        cudaError_t e = fused_launch(plan->rows, plan->cols, dir, plan->scales[dir], g, s);
+        cudaError_t e = fused_launch(plan->rows, plan->cols, dir, plan->scales[dir], g, plan->status, s);
         return e == cudaSuccess ? BDCT_OK : cuda_fail(e);
     }
     return run_separable(plan, dir, in, out, (long long)batch, s);
@@ -295,7 +301,8 @@ extern "C" int bdct_execute_tiled(const bdct_plan *plan, unsigned kind, const fl
     const int tpr = img_cols / plan->cols;
     const long long tiles = (long long)(img_rows / plan->rows) * tpr;
     ExecGeom g{in, out, tiles, 1, tpr, (long long)ld_in, (long long)ld_out};
-    cudaError_t e = fused_launch(plan->rows, plan->cols, dir, plan->scales[dir], g, (cudaStream_t)stream);
+    cudaError_t e = fused_launch(plan->rows, plan->cols, dir, plan->scales[dir], g, plan->status,
+                                 (cudaStream_t)stream);
     return e == cudaSuccess ? BDCT_OK : cuda_fail(e);
 }
 
@@ -311,6 +318,21 @@ extern "C" int bdct_plan_get_info(const bdct_plan *plan, bdct_plan_info *info)
     info->workspace_bytes = plan->work_bytes;
     info->table_bytes = plan->table_bytes;
     return BDCT_OK;
+}
+
+extern "C" int bdct_plan_device_status(const bdct_plan *plan, int clear)
+{
+    if (!plan) return BDCT_ERR_INVALID_ARG;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e);
+    unsigned int v = 0;
+    e = cudaMemcpy(&v, plan->status, sizeof(v), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (clear && v) {
+        e = cudaMemset(plan->status, 0, sizeof(v));
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return (int)v;
 }
 
 extern "C" const char *bdct_status_string(int status)

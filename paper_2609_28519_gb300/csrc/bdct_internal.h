@@ -6,7 +6,7 @@
 #include <stddef.h>
 #include <stdint.h>
 
-#include "../../include/bdct.h"
+#include "bdct.h"
 
 namespace bdct {
 
@@ -42,8 +42,9 @@ enum Dir { DIR_FWD = 0, DIR_INV = 1, DIR_RT = 2 };
 cudaError_t fused_init_device(int device);
 // True if (rows, cols) has a fused register-tile kernel.
 bool fused_supported(int rows, int cols);
+// `status` is the plan's device status word (bounded waits record timeouts).
 cudaError_t fused_launch(int rows, int cols, Dir dir, const DirScales &sc, const ExecGeom &g,
-                         cudaStream_t stream);
+                         unsigned int *status, cudaStream_t stream);
 
 // ---- dense_passes.cu
 // Separable dense passes through a workspace, any shape.  `op_h`, `op_w` are

@@ -19,17 +19,15 @@
 // Every twiddle comes from one FP32 table c_cos[r] = cos(pi r / 8192) built
 // on the GPU in FP64 at plan time; all indices fold to constants.
 //
-// On-chip organization (the GPU counterpart of the paper's Algorithm 1 and
-// Section 3.2 padded stride): a CTA of 256 threads stages A = 256/max(h,w)
-// arrays in shared memory with a row pitch of w+4 floats, so that a thread
-// reading a column (pass 1) and a thread reading a row with 16-byte loads
-// (pass 2) both hit 32 distinct banks.  Pass 1 gives one column per thread,
-// pass 2 one row per thread; each line lives in registers while its 1D core
-// runs.  HBM traffic is one coalesced 16-byte read and one 16-byte write of
-// every element.
+// On-chip organization (the GPU counterpart of the paper's Algorithm 1 and of
+// its Section 3.2 padded stride): arrays are staged in shared memory by TMA
+// bulk copies, one array per 16-byte-padded slot; pass 1 gives each thread one
+// column, pass 2 one row, and each line lives in registers while its 1D core
+// runs.  HBM traffic is one read and one write of every element.
 #include <cuda_runtime.h>
 
 #include "bdct_internal.h"
+#include "ptx.cuh"
 
 namespace bdct {
 
@@ -196,122 +194,269 @@ __device__ __forceinline__ void line_op(float (&x)[N], AxisScale s)
 }
 
 // ------------------------------------------------------------ kernel
-constexpr int kThreads = 256;
-
+// Pipeline organization.  A persistent CTA of NW warps owns a ring of STAGES
+// shared-memory stages; each stage holds a chunk of G arrays (or G adjacent
+// image tiles).  Warp 0 fills stages ahead with TMA bulk copies completing on
+// the stage's mbarrier and drains finished stages with TMA bulk stores, so
+// HBM reads, the arithmetic and HBM writes of different chunks overlap; all
+// warps share the arithmetic of a chunk.
+//
+// Two shared-memory layouts, both bank-conflict-free for the column pass
+// (one column per thread, scalar loads) and the row pass (one row per
+// thread, 16-byte loads):
+//  * contiguous batch -> "slots": array a at a*P, P = h*w + 4 floats, one bulk
+//    copy per array; a warp instruction touches 8 arrays at once (4 adjacent
+//    columns each in pass 1, one row each in pass 2), and the 16-byte gap
+//    between slots spreads them over all 32 banks;
+//  * tiled image -> "strip": the G tiles of a block row side by side, row r
+//    at r*SP, SP = G*w + 4 floats, one bulk copy per image row; pass 1 lanes
+//    take 32 adjacent strip columns, pass 2 lanes take 8 rows of one tile,
+//    which the odd 16-byte row pitch spreads over all banks.
 template <int H, int W>
-struct SmallGeom {
-    static constexpr int LMAX = H > W ? H : W;
-    static constexpr int A = kThreads / LMAX;          // arrays per CTA
-    static constexpr int RP = W + 4;                   // row pitch (floats)
-    static constexpr int AP = H * RP + (W < 32 ? W : 0);  // array pitch (floats)
-    static constexpr int SMEM_FLOATS = A * AP;
+struct FusedCfg {
+    static constexpr int HW = H * W;
+    static constexpr int G = (HW <= 64) ? 16 : 8;  // arrays per chunk
+    static constexpr int NW_MAX = G * (H < W ? H : W) / 32;
+    static constexpr int NW = NW_MAX > 8 ? 8 : NW_MAX;  // warps per CTA
+    static constexpr int THREADS = 32 * NW;
+    static constexpr int P = HW + 4;       // slot pitch (floats)
+    static constexpr int SP = G * W + 4;   // strip row pitch (floats)
+    static constexpr int STAGE_FLOATS = (G * P > H * SP) ? G * P : H * SP;
+    static constexpr int STAGE_BYTES = STAGE_FLOATS * 4;
+    static constexpr int ST_RAW = (32 * 1024) / STAGE_BYTES;
+    static constexpr int STAGES = ST_RAW < 2 ? 2 : (ST_RAW > 4 ? 4 : ST_RAW);
+    static constexpr int J1 = G * W / THREADS;  // columns per thread (pass 1)
+    static constexpr int J2 = G * H / THREADS;  // rows per thread (pass 2)
+    static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + STAGES * 8;
+    static_assert(J1 >= 1 && J2 >= 1 && J1 * THREADS == G * W && J2 * THREADS == G * H, "lane mapping");
+    static_assert((P % 8) == 4 && (SP % 8) == 4, "pitches must be 4 mod 8 floats");
 };
 
-template <int H, int W, int DIR, bool TILED>
-__global__ void __launch_bounds__(kThreads) k_fused_small(ExecGeom g, DirScales sc)
+// Element (a, r, c) of a stage: array/tile a, row r, column c.
+template <int H, int W, bool TILED>
+__device__ __forceinline__ int elem(int a, int r, int c)
 {
-    using Gm = SmallGeom<H, W>;
-    constexpr int A = Gm::A, RP = Gm::RP, AP = Gm::AP;
-    constexpr int HW = H * W;
-    extern __shared__ float4 smem4[];
-    float *sm = reinterpret_cast<float *>(smem4);
+    using C = FusedCfg<H, W>;
+    if constexpr (TILED) return r * C::SP + a * W + c;
+    else return a * C::P + r * W + c;
+}
 
-    const int tid = threadIdx.x;
-    // Arrays handled by this CTA: [first, first + n)
+// Pass 1 line j of this thread -> (array, column).
+template <int H, int W, bool TILED>
+__device__ __forceinline__ void map_col(int j, int warp, int lane, int &a, int &col)
+{
+    using C = FusedCfg<H, W>;
+    if constexpr (TILED) {
+        const int s = lane + 32 * (warp + C::NW * j);  // strip column
+        a = s / W;
+        col = s % W;
+    } else {
+        const int combo = warp + C::NW * j;
+        a = (lane & 7) + 8 * (combo % (C::G / 8));
+        col = (lane >> 3) + 4 * (combo / (C::G / 8));
+    }
+}
+
+// Pass 2 line j of this thread -> (array, row).
+template <int H, int W, bool TILED>
+__device__ __forceinline__ void map_row(int j, int warp, int lane, int &a, int &r)
+{
+    using C = FusedCfg<H, W>;
+    if constexpr (TILED) {
+        const int u = (lane >> 3) + 4 * (warp + C::NW * j);
+        a = u % C::G;
+        r = (lane & 7) + 8 * (u / C::G);
+    } else {
+        const int combo = warp + C::NW * j;
+        a = (lane & 7) + 8 * (combo % (C::G / 8));
+        r = (lane >> 3) + 4 * (combo / (C::G / 8));
+    }
+}
+
+struct FusedParams {
+    const float *in;
+    float *out;
+    long long count;      // arrays (contiguous) or tiles (tiled)
+    int tiles_per_row;    // tiled only
+    int chunks_per_row;   // tiled only: ceil(tiles_per_row / G)
+    long long ld_in, ld_out;  // tiled only (floats)
+    int nchunks;          // < 2^31, checked by the host
+    DirScales sc;
+    unsigned int *status;
+};
+
+// Where a chunk lives: arrays [first, first + n) of a contiguous batch, or
+// tiles t0 .. t0 + n - 1 of block row brow of an image.
+struct ChunkGeom {
     long long first;
-    int n;
-    long long brow = 0;
-    int t0 = 0;
-    if constexpr (!TILED) {
-        first = (long long)blockIdx.x * A;
-        long long rem = g.count - first;
-        n = rem < A ? (int)rem : A;
-    } else {
-        const int cpr = (g.tiles_per_row + A - 1) / A;
-        brow = blockIdx.x / cpr;
-        t0 = (int)(blockIdx.x % cpr) * A;
-        int rem = g.tiles_per_row - t0;
-        n = rem < A ? rem : A;
-        first = 0;
-    }
-    if (n <= 0) return;
+    long long brow;
+    int n, t0;
+};
 
-    // ---- load: coalesced 16-byte reads into the padded tile
+template <int H, int W, bool TILED>
+__device__ __forceinline__ ChunkGeom chunk_geom(const FusedParams &p, int c)
+{
+    using C = FusedCfg<H, W>;
+    ChunkGeom g;
     if constexpr (!TILED) {
-        const float4 *src = reinterpret_cast<const float4 *>(g.in + first * HW);
-        const int nvec = n * HW / 4;
-        for (int q = tid; q < nvec; q += kThreads) {
-            const int e = q * 4;
-            const int a = e / HW, o = e % HW, r = o / W, c = o % W;
-            *reinterpret_cast<float4 *>(sm + a * AP + r * RP + c) = __ldg(src + q);
-        }
+        g.first = (long long)c * C::G;
+        const long long rem = p.count - g.first;
+        g.n = rem < C::G ? (int)rem : C::G;
+        g.brow = 0;
+        g.t0 = 0;
     } else {
-        // strip of H image rows by A*W columns; columns of absent tiles skipped
-        constexpr int SW = A * W;
-        const float *base = g.in + (brow * H) * g.ld_in + (long long)t0 * W;
-        for (int q = tid; q < H * SW / 4; q += kThreads) {
-            const int e = q * 4;
-            const int r = e / SW, col = e % SW, a = col / W, c = col % W;
-            if (a < n)
-                *reinterpret_cast<float4 *>(sm + a * AP + r * RP + c) =
-                    __ldg(reinterpret_cast<const float4 *>(base + r * g.ld_in + col));
+        const unsigned int br = (unsigned int)c / (unsigned int)p.chunks_per_row;
+        g.brow = br;
+        g.t0 = (int)((unsigned int)c - br * (unsigned int)p.chunks_per_row) * C::G;
+        const int rem = p.tiles_per_row - g.t0;
+        g.n = rem < C::G ? rem : C::G;
+        g.first = 0;
+    }
+    return g;
+}
+
+// Issue the copies that fill one stage (all lanes of warp 0).
+template <int H, int W, bool TILED>
+__device__ __forceinline__ void issue_fill(const FusedParams &p, const ChunkGeom &g, float *stage, uint64_t *bar,
+                                           int lane)
+{
+    using C = FusedCfg<H, W>;
+    if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)(g.n * C::HW * 4));
+    __syncwarp();
+    if constexpr (!TILED) {
+        for (int a = lane; a < g.n; a += 32)
+            bulk_load(stage + a * C::P, p.in + (g.first + a) * C::HW, C::HW * 4, bar);
+    } else {
+        for (int r = lane; r < H; r += 32) {
+            const float *src = p.in + (g.brow * H + r) * p.ld_in + (long long)g.t0 * W;
+            bulk_load(stage + r * C::SP, src, (uint32_t)(g.n * W * 4), bar);
         }
     }
+}
+
+// Issue the copies that drain one stage (all lanes of warp 0).
+template <int H, int W, bool TILED>
+__device__ __forceinline__ void issue_drain(const FusedParams &p, const ChunkGeom &g, const float *stage, int lane)
+{
+    using C = FusedCfg<H, W>;
+    if constexpr (!TILED) {
+        for (int a = lane; a < g.n; a += 32) bulk_store(p.out + (g.first + a) * C::HW, stage + a * C::P, C::HW * 4);
+    } else {
+        for (int r = lane; r < H; r += 32) {
+            float *dst = p.out + (g.brow * H + r) * p.ld_out + (long long)g.t0 * W;
+            bulk_store(dst, stage + r * C::SP, (uint32_t)(g.n * W * 4));
+        }
+    }
+}
+
+template <int H, int W>
+__device__ __forceinline__ void cta_sync()
+{
+    if constexpr (FusedCfg<H, W>::NW == 1) __syncwarp();
+    else __syncthreads();
+}
+
+template <int H, int W, int DIR, bool TILED>
+__global__ void __launch_bounds__(FusedCfg<H, W>::THREADS) k_fused(const FusedParams p)
+{
+    using C = FusedCfg<H, W>;
+    extern __shared__ __align__(128) float smem[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + C::STAGES * C::STAGE_FLOATS);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int grid = (int)gridDim.x;
+
+    if (tid == 0) {
+        for (int s = 0; s < C::STAGES; ++s) mbar_init(&full[s], 1);
+        fence_mbar_init();
+    }
+    // the next kernel may start launching; global memory is touched only
+    // after every prerequisite grid has finished
+    pdl_launch_dependents();
+    pdl_wait_prerequisites();
     __syncthreads();
 
-    // ---- pass 1: one column per thread, 1D core along h
-    if (tid < A * W) {
-        const int a = tid / W, c = tid % W;
-        if (a < n) {
-            float x[H];
-            float *p = sm + a * AP + c;
-#pragma unroll
-            for (int i = 0; i < H; ++i) x[i] = p[i * RP];
-            line_op<H, DIR>(x, sc.h);
-#pragma unroll
-            for (int i = 0; i < H; ++i) p[i * RP] = x[i];
+    // prologue: fill every stage
+    if (warp == 0) {
+        for (int s = 0; s < C::STAGES; ++s) {
+            const int c = (int)blockIdx.x + s * grid;
+            if (c < p.nchunks)
+                issue_fill<H, W, TILED>(p, chunk_geom<H, W, TILED>(p, c), smem + s * C::STAGE_FLOATS, &full[s], lane);
         }
     }
-    __syncthreads();
 
-    // ---- pass 2: one row per thread, 1D core along w
-    if (tid < A * H) {
-        const int a = tid / H, r = tid % H;
-        if (a < n) {
-            float x[W];
-            float4 *p = reinterpret_cast<float4 *>(sm + a * AP + r * RP);
+    int s = 0;            // stage of the current chunk
+    uint32_t phase = 0;   // parity of the stage's current use
+    int prev_s = 0;
+    for (int c = (int)blockIdx.x, k = 0; c < p.nchunks; c += grid, ++k) {
+        float *stage = smem + s * C::STAGE_FLOATS;
+        bool ok = mbar_wait_bounded(&full[s], phase);
+        if constexpr (C::NW == 1) ok = __all_sync(0xffffffffu, ok);
+        else ok = __syncthreads_and(ok);
+        if (!ok) {
+            if (tid == 0) record_timeout(p.status);
+            break;
+        }
+        const ChunkGeom g = chunk_geom<H, W, TILED>(p, c);
+        const int n = g.n;
+
+        // pass 1: one column per thread per step, 1D core along h
 #pragma unroll
-            for (int q = 0; q < W / 4; ++q) {
-                float4 v = p[q];
-                x[4 * q] = v.x; x[4 * q + 1] = v.y; x[4 * q + 2] = v.z; x[4 * q + 3] = v.w;
+        for (int j = 0; j < C::J1; ++j) {
+            int a, col;
+            map_col<H, W, TILED>(j, warp, lane, a, col);
+            if (a < n) {
+                float *q = stage + elem<H, W, TILED>(a, 0, col);
+                constexpr int RS = TILED ? C::SP : W;  // row stride
+                float x[H];
+#pragma unroll
+                for (int i = 0; i < H; ++i) x[i] = q[i * RS];
+                line_op<H, DIR>(x, p.sc.h);
+#pragma unroll
+                for (int i = 0; i < H; ++i) q[i * RS] = x[i];
             }
-            line_op<W, DIR>(x, sc.w);
-#pragma unroll
-            for (int q = 0; q < W / 4; ++q) p[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
         }
-    }
-    __syncthreads();
+        cta_sync<H, W>();
 
-    // ---- store: coalesced 16-byte writes
-    if constexpr (!TILED) {
-        float4 *dst = reinterpret_cast<float4 *>(g.out + first * HW);
-        const int nvec = n * HW / 4;
-        for (int q = tid; q < nvec; q += kThreads) {
-            const int e = q * 4;
-            const int a = e / HW, o = e % HW, r = o / W, c = o % W;
-            dst[q] = *reinterpret_cast<const float4 *>(sm + a * AP + r * RP + c);
+        // pass 2: one row per thread per step, 1D core along w
+#pragma unroll
+        for (int j = 0; j < C::J2; ++j) {
+            int a, r;
+            map_row<H, W, TILED>(j, warp, lane, a, r);
+            if (a < n) {
+                float4 *q = reinterpret_cast<float4 *>(stage + elem<H, W, TILED>(a, r, 0));
+                float x[W];
+#pragma unroll
+                for (int v = 0; v < W / 4; ++v) {
+                    const float4 t = q[v];
+                    x[4 * v] = t.x; x[4 * v + 1] = t.y; x[4 * v + 2] = t.z; x[4 * v + 3] = t.w;
+                }
+                line_op<W, DIR>(x, p.sc.w);
+#pragma unroll
+                for (int v = 0; v < W / 4; ++v) q[v] = make_float4(x[4 * v], x[4 * v + 1], x[4 * v + 2], x[4 * v + 3]);
+            }
         }
-    } else {
-        constexpr int SW = A * W;
-        float *base = g.out + (brow * H) * g.ld_out + (long long)t0 * W;
-        for (int q = tid; q < H * SW / 4; q += kThreads) {
-            const int e = q * 4;
-            const int r = e / SW, col = e % SW, a = col / W, c = col % W;
-            if (a < n)
-                *reinterpret_cast<float4 *>(base + r * g.ld_out + col) =
-                    *reinterpret_cast<const float4 *>(sm + a * AP + r * RP + c);
+        fence_proxy_async_smem();
+        cta_sync<H, W>();
+
+        if (warp == 0) {
+            // bulk groups are per thread: every lane commits the stores it issued
+            issue_drain<H, W, TILED>(p, g, stage, lane);
+            bulk_commit();
+            // refill the stage drained in the previous iteration once its reads are done
+            if (k >= 1) {
+                const int cn = c + (C::STAGES - 1) * grid;
+                if (cn < p.nchunks) {
+                    bulk_wait_read<1>();
+                    __syncwarp();
+                    issue_fill<H, W, TILED>(p, chunk_geom<H, W, TILED>(p, cn), smem + prev_s * C::STAGE_FLOATS,
+                                            &full[prev_s], lane);
+                }
+            }
         }
+        prev_s = s;
+        if (++s == C::STAGES) { s = 0; phase ^= 1u; }
     }
+    if (warp == 0) bulk_wait<0>();
 }
 
 // ------------------------------------------------------------ host side
@@ -348,58 +493,92 @@ bool fused_supported(int rows, int cols)
 }
 
 template <int H, int W, int DIR, bool TILED>
-static cudaError_t launch_one(const DirScales &sc, const ExecGeom &g, cudaStream_t stream)
+static cudaError_t launch_one(const DirScales &sc, const ExecGeom &g, unsigned int *status, cudaStream_t stream)
 {
-    using Gm = SmallGeom<H, W>;
-    const size_t smem = (size_t)Gm::SMEM_FLOATS * sizeof(float);
-    auto kern = k_fused_small<H, W, DIR, TILED>;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    using C = FusedCfg<H, W>;
+    auto kern = k_fused<H, W, DIR, TILED>;
+    static int blocks_per_sm[64];
+    static int num_sms[64];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (blocks_per_sm[dev] == 0) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[dev], kern, C::THREADS, C::SMEM);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&num_sms[dev], cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        if (blocks_per_sm[dev] < 1) return cudaErrorInvalidConfiguration;
     }
-    long long blocks;
-    if (!TILED) blocks = (g.count + Gm::A - 1) / Gm::A;
-    else {
-        long long cpr = (g.tiles_per_row + Gm::A - 1) / Gm::A;
-        blocks = (g.count / g.tiles_per_row) * cpr;
+    FusedParams p{};
+    p.in = g.in;
+    p.out = g.out;
+    p.count = g.count;
+    p.tiles_per_row = g.tiles_per_row;
+    p.ld_in = g.ld_in;
+    p.ld_out = g.ld_out;
+    p.sc = sc;
+    p.status = status;
+    long long nch;
+    if (!TILED) {
+        nch = (g.count + C::G - 1) / C::G;
+    } else {
+        p.chunks_per_row = (g.tiles_per_row + C::G - 1) / C::G;
+        nch = (g.count / g.tiles_per_row) * p.chunks_per_row;
     }
-    if (blocks <= 0) return cudaSuccess;
-    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    kern<<<(unsigned)blocks, kThreads, smem, stream>>>(g, sc);
-    return cudaGetLastError();
+    if (nch <= 0) return cudaSuccess;
+    if (nch > 0x7ff00000LL) return cudaErrorInvalidValue;  // keeps c + STAGES * grid within int
+    p.nchunks = (int)nch;
+    // persistent: as many CTAs as fit on the device
+    long long grid = (long long)blocks_per_sm[dev] * num_sms[dev];
+    if (grid > p.nchunks) grid = p.nchunks;
+    // programmatic dependent launch: this grid may be scheduled while the
+    // previous kernel in the stream drains; it waits for it before any access
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(C::THREADS);
+    cfg.dynamicSmemBytes = C::SMEM;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, p);
 }
 
 template <int H, int W>
-static cudaError_t launch_hw(Dir dir, const DirScales &sc, const ExecGeom &g, cudaStream_t s)
+static cudaError_t launch_hw(Dir dir, const DirScales &sc, const ExecGeom &g, unsigned int *st, cudaStream_t s)
 {
     const bool t = g.tiled != 0;
     switch (dir) {
-        case DIR_FWD: return t ? launch_one<H, W, DIR_FWD, true>(sc, g, s) : launch_one<H, W, DIR_FWD, false>(sc, g, s);
-        case DIR_INV: return t ? launch_one<H, W, DIR_INV, true>(sc, g, s) : launch_one<H, W, DIR_INV, false>(sc, g, s);
-        default: return t ? launch_one<H, W, DIR_RT, true>(sc, g, s) : launch_one<H, W, DIR_RT, false>(sc, g, s);
+        case DIR_FWD: return t ? launch_one<H, W, DIR_FWD, true>(sc, g, st, s) : launch_one<H, W, DIR_FWD, false>(sc, g, st, s);
+        case DIR_INV: return t ? launch_one<H, W, DIR_INV, true>(sc, g, st, s) : launch_one<H, W, DIR_INV, false>(sc, g, st, s);
+        default: return t ? launch_one<H, W, DIR_RT, true>(sc, g, st, s) : launch_one<H, W, DIR_RT, false>(sc, g, st, s);
     }
 }
 
 template <int H>
-static cudaError_t launch_h(int cols, Dir dir, const DirScales &sc, const ExecGeom &g, cudaStream_t s)
+static cudaError_t launch_h(int cols, Dir dir, const DirScales &sc, const ExecGeom &g, unsigned int *st,
+                            cudaStream_t s)
 {
     switch (cols) {
-        case 8: return launch_hw<H, 8>(dir, sc, g, s);
-        case 16: return launch_hw<H, 16>(dir, sc, g, s);
-        case 32: return launch_hw<H, 32>(dir, sc, g, s);
+        case 8: return launch_hw<H, 8>(dir, sc, g, st, s);
+        case 16: return launch_hw<H, 16>(dir, sc, g, st, s);
+        case 32: return launch_hw<H, 32>(dir, sc, g, st, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t fused_launch(int rows, int cols, Dir dir, const DirScales &sc, const ExecGeom &g,
-                         cudaStream_t stream)
+                         unsigned int *status, cudaStream_t stream)
 {
     switch (rows) {
-        case 8: return launch_h<8>(cols, dir, sc, g, stream);
-        case 16: return launch_h<16>(cols, dir, sc, g, stream);
-        case 32: return launch_h<32>(cols, dir, sc, g, stream);
+        case 8: return launch_h<8>(cols, dir, sc, g, status, stream);
+        case 16: return launch_h<16>(cols, dir, sc, g, status, stream);
+        case 32: return launch_h<32>(cols, dir, sc, g, status, stream);
         default: return cudaErrorInvalidValue;
     }
 }

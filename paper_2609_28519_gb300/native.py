@@ -30,7 +30,8 @@ STATUS = {0: "OK", 1: "ERR_INVALID_ARG", 2: "ERR_UNSUPPORTED_SHAPE", 3: "ERR_KIN
 # every symbol the header declares, in declaration order
 EXPORTS = [
     "bdct_plan_create", "bdct_plan_destroy", "bdct_forward", "bdct_inverse", "bdct_roundtrip",
-    "bdct_execute", "bdct_execute_tiled", "bdct_plan_get_info", "bdct_status_string",
+    "bdct_execute", "bdct_execute_tiled", "bdct_plan_get_info", "bdct_plan_device_status",
+    "bdct_selftest_wait_timeout", "bdct_status_string",
     "bdct_last_cuda_error", "bdct_version",
 ]
 
@@ -73,6 +74,8 @@ def lib() -> ctypes.CDLL:
             L.bdct_execute.argtypes = [vp, cu, vp, vp, sz, vp]
             L.bdct_execute_tiled.argtypes = [vp, cu, vp, vp, ci, ci, sz, sz, vp]
             L.bdct_plan_get_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
+            L.bdct_plan_device_status.argtypes = [vp, ci]
+            L.bdct_selftest_wait_timeout.argtypes = [cu]
             L.bdct_status_string.argtypes = [ci]
             L.bdct_status_string.restype = ctypes.c_char_p
             L.bdct_last_cuda_error.restype = ci
@@ -120,6 +123,14 @@ class Plan:
         inf = PlanInfo()
         _check(lib().bdct_plan_get_info(self.handle, ctypes.byref(inf)), "bdct_plan_get_info")
         return inf
+
+    def device_status(self, clear: bool = True) -> int:
+        """Synchronize and return the plan's device status (0, or 8 after a
+        bounded device wait expired); raises on host errors."""
+        st = lib().bdct_plan_device_status(self.handle, 1 if clear else 0)
+        if st not in (0, 8):
+            _check(st, "bdct_plan_device_status")
+        return st
 
     def close(self) -> None:
         if getattr(self, "_h", None) is not None and _lib is not None:

@@ -213,3 +213,19 @@ def test_argument_errors_on_device(cuda_dev):
     assert L.bdct_execute(plan.handle, 1, None, None, 0, None) == 0
     with pytest.raises(BdctError):
         Plan(16, 12, path="bf16")
+
+
+def test_bounded_wait_gives_up_with_status(cuda_dev):
+    """A wait on a barrier nothing completes gives up after its limit, records
+    BDCT_ERR_DEVICE_TIMEOUT and leaves the context usable."""
+    import torch
+    from paper_2609_28519_gb300 import Plan, native
+    L = native.lib()
+    assert L.bdct_selftest_wait_timeout(20000) == 8
+    # the context still works afterwards
+    plan = Plan(8, 8)
+    x = torch.ones(4, 8, 8, device=cuda_dev)
+    y = plan.forward(x)
+    torch.cuda.synchronize()
+    assert abs(float(y[0, 0, 0]) - 8.0) < 1e-5
+    assert plan.device_status() == 0
