@@ -137,6 +137,31 @@ int bdct_plan_get_info(const bdct_plan *plan, bdct_plan_info *info);
  * returned as usual.                                                         */
 int bdct_plan_device_status(const bdct_plan *plan, int clear);
 
+/* Allocation-free transform, for callers that cannot allocate device memory
+ * (their memory is owned by another allocator, or they must avoid the device
+ * synchronization that allocation and release can cause, or their footprint
+ * must be fixed when the library loads).  No plan is needed and nothing is
+ * allocated: the separable dense route (FP64-generated operator matrices,
+ * then a row pass and a column pass through an intermediate buffer) keeps
+ * all of its scratch in one file-scope device array of 8 MiB, which every
+ * GPU that loads the library holds until the process exits.
+ * Arguments as in bdct_plan_create + bdct_execute: kind is ONE of
+ * BDCT_FORWARD / BDCT_INVERSE / BDCT_ROUNDTRIP; in and out are 16-byte
+ * aligned device pointers to `batch` contiguous rows x cols arrays (equal or
+ * disjoint).  Limits: 1 <= rows, cols <= 512, cols a multiple of 4; larger
+ * sides return BDCT_ERR_UNSUPPORTED_SHAPE.  Batches larger than the scratch
+ * holds are processed in chunks.
+ * The first call on each device looks up the array's device address once
+ * (cudaGetSymbolAddress with that device current); make that first call
+ * before any stream capture.  Every call shares the one array and leaves its
+ * contents behind; each call rewrites everything it reads, so nothing needs
+ * to start at zero, but calls that overlap on the GPU (different streams,
+ * or host threads racing) corrupt each other's scratch and must be
+ * serialized by the caller.
+ * The paper has no counterpart to this entry point.                          */
+int bdct_execute_noalloc(int rows, int cols, unsigned kind, int norm, const float *in, float *out,
+                         size_t batch, void *stream);
+
 /* Self-test of the bounded device-side wait: launches one thread that waits
  * on a barrier nothing completes, with a limit of limit_us microseconds
  * (1..2000000), and returns the status it recorded -- BDCT_ERR_DEVICE_TIMEOUT

@@ -31,7 +31,7 @@ STATUS = {0: "OK", 1: "ERR_INVALID_ARG", 2: "ERR_UNSUPPORTED_SHAPE", 3: "ERR_KIN
 EXPORTS = [
     "bdct_plan_create", "bdct_plan_destroy", "bdct_forward", "bdct_inverse", "bdct_roundtrip",
     "bdct_execute", "bdct_execute_tiled", "bdct_plan_get_info", "bdct_plan_device_status",
-    "bdct_selftest_wait_timeout", "bdct_status_string",
+    "bdct_execute_noalloc", "bdct_selftest_wait_timeout", "bdct_status_string",
     "bdct_last_cuda_error", "bdct_version",
 ]
 
@@ -76,6 +76,7 @@ def lib() -> ctypes.CDLL:
             L.bdct_plan_get_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
             L.bdct_plan_device_status.argtypes = [vp, ci]
             L.bdct_selftest_wait_timeout.argtypes = [cu]
+            L.bdct_execute_noalloc.argtypes = [ci, ci, cu, ci, vp, vp, sz, vp]
             L.bdct_status_string.argtypes = [ci]
             L.bdct_status_string.restype = ctypes.c_char_p
             L.bdct_last_cuda_error.restype = ci
