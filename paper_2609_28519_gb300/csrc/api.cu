@@ -36,7 +36,7 @@ struct bdct_plan {
     unsigned kind = 0;
     int norm = 0;
     int path = 0;
-    int variant = 0;  // 1 fused register tile, 2 separable dense passes
+    int variant = 0;  // 1 fused register tile, 2 separable dense passes, 3 tensor core
     int device = -1;
     DirScales scales[3];  // per Dir
     // separable route
@@ -47,6 +47,10 @@ struct bdct_plan {
     long long chunk_arrays = 0;
     size_t table_bytes = 0;
     unsigned int *status = nullptr;  // device status word written by bounded waits
+    // tensor-core route: per direction, the operator term tables
+    __nv_bfloat16 *tc_ops = nullptr;
+    size_t tc_off[3] = {0, 0, 0};
+    int tc_terms = 3;
 };
 
 static AxisScale axis_scale(int n, Dir dir, int norm)
@@ -84,6 +88,7 @@ static void plan_free(bdct_plan *p)
     if (!p) return;
     if (p->ops) cudaFree(p->ops);
     if (p->status) cudaFree(p->status);
+    if (p->tc_ops) cudaFree(p->tc_ops);
     if (p->work) cudaFree(p->work);
     delete p;
 }
@@ -104,8 +109,14 @@ extern "C" int bdct_plan_create(bdct_plan **plan, int rows, int cols, unsigned k
     if (st != BDCT_OK) return st;
 
     int resolved = path;
-    if (resolved == BDCT_PATH_AUTO) resolved = BDCT_PATH_FP32;
-    if (resolved != BDCT_PATH_FP32) return BDCT_ERR_PATH;
+    if (resolved == BDCT_PATH_AUTO) {
+        // fused FP32 where it exists, else the tensor-core route, else dense passes
+        if (fused_supported(rows, cols)) resolved = BDCT_PATH_FP32;
+        else if (tc_supported(rows, cols)) resolved = BDCT_PATH_SPLIT_TC;
+        else resolved = BDCT_PATH_FP32;
+    }
+    const bool tc = resolved == BDCT_PATH_SPLIT_TC || resolved == BDCT_PATH_SPLIT_HILO || resolved == BDCT_PATH_BF16;
+    if (tc && !tc_supported(rows, cols)) return BDCT_ERR_UNSUPPORTED_SHAPE;
 
     bdct_plan *p = new (std::nothrow) bdct_plan;
     if (!p) return BDCT_ERR_NO_MEMORY;
@@ -127,7 +138,35 @@ extern "C" int bdct_plan_create(bdct_plan **plan, int rows, int cols, unsigned k
     e = cudaMemset(p->status, 0, sizeof(unsigned int));
     if (e != cudaSuccess) { plan_free(p); return cuda_fail(e); }
 
-    if (fused_supported(rows, cols)) {
+    if (tc) {
+        p->variant = 3;
+        p->tc_terms = resolved == BDCT_PATH_SPLIT_TC ? 3 : (resolved == BDCT_PATH_SPLIT_HILO ? 2 : 1);
+        const size_t te = tc_table_elems(rows);
+        const size_t ntab = ((kind & BDCT_FORWARD) ? 1 : 0) + ((kind & BDCT_INVERSE) ? 1 : 0) +
+                            ((kind & BDCT_ROUNDTRIP) ? 2 : 0);
+        e = cudaMalloc(&p->tc_ops, ntab * te * sizeof(__nv_bfloat16));
+        if (e != cudaSuccess) { plan_free(p); t_last_cuda_error = (int)e; return BDCT_ERR_NO_MEMORY; }
+        p->table_bytes = ntab * te * sizeof(__nv_bfloat16);
+        size_t off = 0;
+        if (kind & BDCT_FORWARD) {
+            p->tc_off[DIR_FWD] = off;
+            e = tc_gen_tables(p->tc_ops + off, rows, 1, norm, 0);
+            off += te;
+        }
+        if (e == cudaSuccess && (kind & BDCT_INVERSE)) {
+            p->tc_off[DIR_INV] = off;
+            e = tc_gen_tables(p->tc_ops + off, rows, 2, norm, 0);
+            off += te;
+        }
+        if (e == cudaSuccess && (kind & BDCT_ROUNDTRIP)) {
+            // the round trip is normalized: orthonormal forward, then its adjoint
+            p->tc_off[DIR_RT] = off;
+            e = tc_gen_tables(p->tc_ops + off, rows, 1, BDCT_NORM_ORTHO, 0);
+            if (e == cudaSuccess) e = tc_gen_tables(p->tc_ops + off + te, rows, 2, BDCT_NORM_ORTHO, 0);
+            off += 2 * te;
+        }
+        if (e != cudaSuccess) { plan_free(p); return cuda_fail(e); }
+    } else if (fused_supported(rows, cols)) {
         p->variant = 1;
     } else {
         p->variant = 2;
@@ -257,6 +296,11 @@ extern "C" int bdct_execute(const bdct_plan *plan, unsigned kind, const float *i
         cudaError_t e = fused_launch(plan->rows, plan->cols, dir, plan->scales[dir], g, plan->status, s);
         return e == cudaSuccess ? BDCT_OK : cuda_fail(e);
     }
+    if (plan->variant == 3) {
+        ExecGeom g{in, out, (long long)batch, 0, 0, 0, 0};
+        cudaError_t e = tc_launch(plan->rows, dir, plan->tc_terms, g, plan->tc_ops + plan->tc_off[dir], plan->status, s);
+        return e == cudaSuccess ? BDCT_OK : cuda_fail(e);
+    }
     return run_separable(plan, dir, in, out, (long long)batch, s);
 }
 
@@ -289,7 +333,7 @@ extern "C" int bdct_execute_tiled(const bdct_plan *plan, unsigned kind, const fl
     if (img_rows % plan->rows || img_cols % plan->cols) return BDCT_ERR_UNSUPPORTED_SHAPE;
     if (ld_in < (size_t)img_cols || ld_out < (size_t)img_cols) return BDCT_ERR_INVALID_ARG;
     if ((((uintptr_t)in | (uintptr_t)out) & 15u) || (ld_in % 4) || (ld_out % 4)) return BDCT_ERR_ALIGN;
-    if (plan->variant != 1) return BDCT_ERR_PATH;
+    if (plan->variant != 1 && plan->variant != 3) return BDCT_ERR_PATH;
     const size_t span_in = ((size_t)(img_rows - 1) * ld_in + img_cols) * sizeof(float);
     const size_t span_out = ((size_t)(img_rows - 1) * ld_out + img_cols) * sizeof(float);
     if (in != out) {
@@ -301,8 +345,12 @@ extern "C" int bdct_execute_tiled(const bdct_plan *plan, unsigned kind, const fl
     const int tpr = img_cols / plan->cols;
     const long long tiles = (long long)(img_rows / plan->rows) * tpr;
     ExecGeom g{in, out, tiles, 1, tpr, (long long)ld_in, (long long)ld_out};
-    cudaError_t e = fused_launch(plan->rows, plan->cols, dir, plan->scales[dir], g, plan->status,
-                                 (cudaStream_t)stream);
+    cudaError_t e;
+    if (plan->variant == 3)
+        e = tc_launch(plan->rows, dir, plan->tc_terms, g, plan->tc_ops + plan->tc_off[dir], plan->status,
+                      (cudaStream_t)stream);
+    else
+        e = fused_launch(plan->rows, plan->cols, dir, plan->scales[dir], g, plan->status, (cudaStream_t)stream);
     return e == cudaSuccess ? BDCT_OK : cuda_fail(e);
 }
 

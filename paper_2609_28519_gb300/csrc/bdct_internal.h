@@ -2,6 +2,7 @@
 // Host-side only declarations; no CUDA types leak into include/bdct.h.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -45,6 +46,19 @@ bool fused_supported(int rows, int cols);
 // `status` is the plan's device status word (bounded waits record timeouts).
 cudaError_t fused_launch(int rows, int cols, Dir dir, const DirScales &sc, const ExecGeom &g,
                          unsigned int *status, cudaStream_t stream);
+
+// ---- tc_split.cu
+// Split-BF16 tcgen05 route for square sides 16, 32, 64.
+bool tc_supported(int rows, int cols);
+// BF16 elements of one operator's term table (three terms of n x n).
+size_t tc_table_elems(int n);
+// Split the FP64 operator matrix of (direction 1 fwd / 2 inv, norm) into three
+// BF16 terms in the tensor-core B layout.
+cudaError_t tc_gen_tables(__nv_bfloat16 *dst, int n, int direction, int norm, cudaStream_t s);
+// `ops` holds one table (forward or inverse) or two adjacent (round trip:
+// orthonormal forward, then orthonormal inverse); terms = 3, 2 or 1.
+cudaError_t tc_launch(int n, Dir dir, int terms, const ExecGeom &g, const __nv_bfloat16 *ops,
+                      unsigned int *status, cudaStream_t stream);
 
 // ---- dense_passes.cu
 // Separable dense passes through a workspace, any shape.  `op_h`, `op_w` are

@@ -1,0 +1,479 @@
+// Split-BF16 tensor-core 2D DCT: C X C^T on tcgen05 with FP32 accumulation.
+//
+// What is computed: Eq. 2 of the BRiDCT paper as two dense contractions,
+// Y = M_h X M_w^T, with M the 1D operator of the direction (Q_n of Eq. 1 for
+// the orthonormal forward transform, Q_n^T for the inverse, the REDFT pair for
+// the unnormalized setting); the round trip chains the forward and the
+// inverse (four contractions).  Direct matrix evaluation costs n
+// multiply-adds per point (Section 1.2); here the tensor cores take them.
+//
+// Exactness with BF16 operands (the paper excludes approximated matrices,
+// Section 1.1): every FP32 operand x is split into BF16 terms
+// x = x0 + x1 + x2 (each the round-to-nearest BF16 of the remaining residual,
+// together holding the 24-bit significand), the FP64 operator matrix likewise,
+// and the products x_a * m_b with a + b <= 2 are accumulated in FP32, smallest
+// first.  Three terms and six products reach FP32 accuracy; the report-only
+// variants keep two terms and three products (hi/lo) or one term and one
+// product.
+//
+// Organization for an n x n array (n = 16, 32, 64), 128 threads per CTA:
+// a tile stacks 128/n arrays so that thread t owns stack row t and TMEM lane
+// t.  Pass 1: A = the rows of X (K-major, K = column index), B = M_w
+// (K-major), D1[row][l] = T row in TMEM.  Pass 2 contracts over the row index:
+// each thread re-splits its T row and stores it as the MN-major A operand
+// (stack rows become the M dimension), B = M_h, D2[(array, l)][k] = Y[k][l];
+// thread (array, l) then holds column l of Y and stores it coalesced across
+// lanes.  Odd passes use K-major A, even passes MN-major A, which is what lets
+// every pass start from values a thread already holds.
+//
+// Shared-memory operand layout (no swizzle), verified on the device: core
+// matrices of 8 rows x 16 bytes stored as 128 contiguous bytes; the
+// descriptor's leading byte offset is the stride between core matrices along
+// K and the stride byte offset the stride along M/N, for both operand majors.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "bdct_internal.h"
+#include "ptx.cuh"
+
+namespace bdct {
+
+// ------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
+    return d;                 // base offset 0, relative offsets, no swizzle
+}
+
+// kind::f16 instruction descriptor: D = F32, A = B = BF16, M = 128.
+__host__ __device__ constexpr uint32_t tc_idesc(int n, bool a_mn_major)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | (a_mn_major ? (1u << 15) : 0u) |
+           ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// ------------------------------------------------------------ splitting
+// x = t0 + t1 + t2, each term the round-to-nearest BF16 of what is left.
+template <int TERMS>
+__device__ __forceinline__ void split3(float x, __nv_bfloat16 (&t)[3])
+{
+    t[0] = __float2bfloat16_rn(x);
+    if constexpr (TERMS > 1) {
+        const float r1 = x - __bfloat162float(t[0]);  // exact
+        t[1] = __float2bfloat16_rn(r1);
+        if constexpr (TERMS > 2) {
+            const float r2 = r1 - __bfloat162float(t[1]);  // exact
+            t[2] = __float2bfloat16_rn(r2);
+        }
+    }
+}
+
+// ------------------------------------------------------------ kernel
+template <int N>
+struct TcCfg {
+    static constexpr int G = 128 / N;               // arrays per tile
+    static constexpr int A_TERM_BYTES = 128 * N * 2;
+    static constexpr int B_TERM_BYTES = N * N * 2;
+    static constexpr int KSTEPS = N / 16;
+    static constexpr int KMAJ_SBO = (N / 8) * 128;  // M/N-adjacent core stride, K-major
+    static constexpr int MN_LBO = 16 * 128;         // K-adjacent core stride, MN-major (M = 128)
+    static constexpr int TMEM_COLS = 2 * N < 32 ? 32 : 2 * N;
+};
+
+struct TcParams {
+    const float *in;
+    float *out;
+    long long count;          // arrays (contiguous) or tiles (tiled)
+    int tiles_per_row;        // tiled only
+    int chunks_per_row;       // tiled only: ceil(tiles_per_row / G)
+    long long ld_in, ld_out;  // tiled only
+    int ntiles;
+    const __nv_bfloat16 *ops;  // operator term tables, [op][term][B layout]
+    unsigned int *status;
+};
+
+// Byte offset of element (r, k) of a K-major operand with K = kdim columns.
+__device__ __forceinline__ int kmaj_off_bytes(int r, int k, int kdim)
+{
+    return (((r >> 3) * (kdim >> 3) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1);
+}
+
+// Byte offset of element (m, k) of an MN-major operand with M = 128 rows.
+__device__ __forceinline__ int mnmaj_off_bytes(int m, int k)
+{
+    return (((k >> 3) * 16 + (m >> 3)) << 7) + ((k & 7) << 4) + ((m & 7) << 1);
+}
+
+// Write this thread's N values as split terms into the A buffer: K-major row
+// `row` (values along K), or MN-major column `col` of rows base .. base+N-1.
+template <int N, int TERMS, bool MN>
+__device__ __forceinline__ void stage_a(uint8_t *a_buf, const float *v, int row_or_col, int base)
+{
+    using C = TcCfg<N>;
+#pragma unroll
+    for (int q = 0; q < N / 8; ++q) {
+        __nv_bfloat16 t[TERMS][8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            __nv_bfloat16 s[3];
+            split3<TERMS>(v[8 * q + e], s);
+#pragma unroll
+            for (int tt = 0; tt < TERMS; ++tt) t[tt][e] = s[tt];
+        }
+        int off;
+        if constexpr (!MN) off = kmaj_off_bytes(row_or_col, 8 * q, N);
+        else off = mnmaj_off_bytes(base + 8 * q, row_or_col);
+#pragma unroll
+        for (int tt = 0; tt < TERMS; ++tt)
+            *reinterpret_cast<uint4 *>(a_buf + tt * C::A_TERM_BYTES + off) = *reinterpret_cast<const uint4 *>(t[tt]);
+    }
+}
+
+// Issue one pass: D = sum over products of A_ta * B_tb^T, smallest first.
+template <int N, int TERMS, bool MN>
+__device__ __forceinline__ void issue_pass(uint32_t a_base, uint32_t b_base, uint32_t d_tmem)
+{
+    using C = TcCfg<N>;
+    constexpr uint32_t idesc = tc_idesc(N, MN);
+    constexpr int NP = TERMS == 3 ? 6 : (TERMS == 2 ? 3 : 1);
+    // products (a, b) with a + b <= TERMS - 1, smallest terms first
+    constexpr int pa[6] = {2, 1, 0, 1, 0, 0};
+    constexpr int pb[6] = {0, 1, 2, 0, 1, 0};
+    constexpr int first = 6 - NP;
+    bool acc = false;
+#pragma unroll
+    for (int p = first; p < 6; ++p) {
+#pragma unroll
+        for (int ks = 0; ks < C::KSTEPS; ++ks) {
+            uint64_t da;
+            if constexpr (!MN) da = smem_desc(a_base + pa[p] * C::A_TERM_BYTES + ks * 256, 128, C::KMAJ_SBO);
+            else da = smem_desc(a_base + pa[p] * C::A_TERM_BYTES + ks * 2 * C::MN_LBO, C::MN_LBO, 128);
+            const uint64_t db = smem_desc(b_base + pb[p] * C::B_TERM_BYTES + ks * 256, 128, C::KMAJ_SBO);
+            tc_mma(d_tmem, da, db, idesc, acc ? 1u : 0u);
+            acc = true;
+        }
+    }
+}
+
+template <int N, bool TILED>
+__device__ __forceinline__ void tile_geom(const TcParams &p, int tile, long long &first, int &n, long long &brow,
+                                          int &t0)
+{
+    using C = TcCfg<N>;
+    if constexpr (!TILED) {
+        first = (long long)tile * C::G;
+        const long long rem = p.count - first;
+        n = rem < C::G ? (int)rem : C::G;
+        brow = 0;
+        t0 = 0;
+    } else {
+        const unsigned int br = (unsigned int)tile / (unsigned int)p.chunks_per_row;
+        brow = br;
+        t0 = (int)((unsigned int)tile - br * (unsigned int)p.chunks_per_row) * C::G;
+        const int rem = p.tiles_per_row - t0;
+        n = rem < C::G ? rem : C::G;
+        first = 0;
+    }
+}
+
+// NPASS = 2 (forward or inverse; ops 0, 0) or 4 (round trip; ops 0, 0, 1, 1).
+template <int N, int NPASS, int TERMS, bool TILED>
+__global__ void __launch_bounds__(128) k_tc_split(const TcParams p)
+{
+    using C = TcCfg<N>;
+    constexpr int NOPS = NPASS / 2;
+    extern __shared__ __align__(1024) uint8_t tsm[];
+    uint8_t *a_buf = tsm;                                   // TERMS A terms
+    uint8_t *b_buf = tsm + TERMS * C::A_TERM_BYTES;         // NOPS x 3 B terms
+    uint64_t *bar = reinterpret_cast<uint64_t *>(b_buf + NOPS * 3 * C::B_TERM_BYTES);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + 2);
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);  // MMA completion
+        mbar_init(&bar[1], 1);  // operator tables landed
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(C::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    pdl_launch_dependents();
+    pdl_wait_prerequisites();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t d_tmem[2] = {tmem, tmem + N};
+    const uint32_t a_base = smem_u32(a_buf), b_base = smem_u32(b_buf);
+
+    // operator term tables (constant across tiles): one bulk copy
+    if (tid == 0) {
+        const uint32_t bytes = NOPS * 3 * C::B_TERM_BYTES;
+        mbar_arrive_expect_tx(&bar[1], bytes);
+        bulk_load(b_buf, p.ops, bytes, &bar[1]);
+    }
+    bool ok = mbar_wait_bounded(&bar[1], 0);
+    ok = __syncthreads_and(ok);
+    uint32_t mma_phase = 0;
+
+    const int b_local = tid / N, r_local = tid % N;  // this thread's stack row: array, row
+    float v[N];
+    for (int tile = blockIdx.x; ok && tile < p.ntiles; tile += gridDim.x) {
+        long long first, brow;
+        int n, t0;
+        tile_geom<N, TILED>(p, tile, first, n, brow, t0);
+        const bool active = b_local < n;
+        // ---- load this thread's input row (zeros for absent arrays)
+        if (active) {
+            const float *src;
+            if constexpr (!TILED) src = p.in + (first + b_local) * (long long)(N * N) + r_local * N;
+            else src = p.in + (brow * N + r_local) * p.ld_in + (long long)(t0 + b_local) * N;
+#pragma unroll
+            for (int q = 0; q < N / 4; ++q) {
+                const float4 t = __ldg(reinterpret_cast<const float4 *>(src) + q);
+                v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < N; ++j) v[j] = 0.0f;
+        }
+#pragma unroll 1
+        for (int pass = 0; pass < NPASS; ++pass) {
+            const bool mn = (pass & 1) != 0;
+            // ---- stage A: odd passes K-major from a held row, even passes MN-major
+            if (!mn) stage_a<N, TERMS, false>(a_buf, v, tid, 0);
+            else stage_a<N, TERMS, true>(a_buf, v, r_local, b_local * N);
+            fence_proxy_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+            if (tid == 0) {
+                const uint32_t bop = b_base + (pass >> 1) * 3 * C::B_TERM_BYTES;
+                if (!mn) issue_pass<N, TERMS, false>(a_base, bop, d_tmem[pass & 1]);
+                else issue_pass<N, TERMS, true>(a_base, bop, d_tmem[pass & 1]);
+                tc_commit(&bar[0]);
+            }
+            ok = mbar_wait_bounded(&bar[0], mma_phase);
+            mma_phase ^= 1u;
+            ok = __syncthreads_and(ok);
+            if (!ok) break;
+            tc_fence_after();
+            // ---- this thread's TMEM lane of the result
+            const uint32_t taddr = d_tmem[pass & 1] + ((uint32_t)(32 * warp) << 16);
+#pragma unroll
+            for (int c = 0; c < N / 16; ++c) tmem_ld16(taddr + 16 * c, v + 16 * c);
+        }
+        if (!ok) break;
+        // ---- store.  After two passes thread (array, c) holds column c of the
+        // result (values over the row index): stores are coalesced across
+        // lanes.  After four passes thread (array, i) holds row i.
+        if (active) {
+            if constexpr (NPASS == 2) {
+#pragma unroll
+                for (int k = 0; k < N; ++k) {
+                    float *dst;
+                    if constexpr (!TILED) dst = p.out + (first + b_local) * (long long)(N * N) + k * N + r_local;
+                    else dst = p.out + (brow * N + k) * p.ld_out + (long long)(t0 + b_local) * N + r_local;
+                    *dst = v[k];
+                }
+            } else {
+                float *dst;
+                if constexpr (!TILED) dst = p.out + (first + b_local) * (long long)(N * N) + r_local * N;
+                else dst = p.out + (brow * N + r_local) * p.ld_out + (long long)(t0 + b_local) * N;
+#pragma unroll
+                for (int q = 0; q < N / 4; ++q)
+                    reinterpret_cast<float4 *>(dst)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+    }
+    if (!ok && tid == 0) record_timeout(p.status);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS) : "memory");
+}
+
+// ------------------------------------------------------------ tables
+// Operator matrix M (direction/norm as in the dense route) split into three
+// BF16 terms in FP64, written in the K-major B layout: B[l][j] = M[l][j]
+// (rows = output index, K = input index).
+__global__ void k_gen_split_op(__nv_bfloat16 *dst, int n, int direction, int norm)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * n) return;
+    const int r = idx / n, k = idx % n;  // B row (output index), K (input index)
+    // forward: M[r][k] = s_r cos(pi (2k+1) r / (2n)); inverse: M[r][k] = s_k cos(pi (2r+1) k / (2n))
+    const int kk = direction == 1 ? r : k;   // frequency index
+    const int jj = direction == 1 ? k : r;   // sample index
+    double s;
+    if (norm == 0) s = (kk == 0) ? sqrt(1.0 / n) : sqrt(2.0 / n);
+    else if (direction == 1) s = 2.0;
+    else s = (kk == 0) ? 1.0 : 2.0;
+    // cos(pi m / (2n)) with the argument reduced exactly
+    long long m = (2LL * jj + 1) * kk;
+    const long long d = 2LL * n;
+    long long red = m % (2 * d);
+    if (red > d) red = 2 * d - red;
+    double sign = 1.0;
+    if (2 * red > d) { red = d - red; sign = -1.0; }
+    double c;
+    if (red == 0) c = sign;
+    else if (2 * red == d) c = 0.0;
+    else c = sign * cospi((double)red / (double)d);
+    const double val = s * c;
+    const __nv_bfloat16 t0 = __double2bfloat16(val);
+    const double r1 = val - (double)__bfloat162float(t0);
+    const __nv_bfloat16 t1 = __double2bfloat16(r1);
+    const double r2 = r1 - (double)__bfloat162float(t1);
+    const __nv_bfloat16 t2 = __double2bfloat16(r2);
+    const int off = (((r >> 3) * (n >> 3) + (k >> 3)) << 6) + ((r & 7) << 3) + (k & 7);  // elements
+    dst[off] = t0;
+    dst[n * n + off] = t1;
+    dst[2 * n * n + off] = t2;
+}
+
+bool tc_supported(int rows, int cols) { return rows == cols && (rows == 16 || rows == 32 || rows == 64); }
+
+size_t tc_table_elems(int n) { return (size_t)3 * n * n; }
+
+cudaError_t tc_gen_tables(__nv_bfloat16 *dst, int n, int direction, int norm, cudaStream_t s)
+{
+    k_gen_split_op<<<(n * n + 255) / 256, 256, 0, s>>>(dst, n, direction, norm);
+    return cudaGetLastError();
+}
+
+template <int N, int NPASS, int TERMS, bool TILED>
+static cudaError_t tc_launch_one(const TcParams &p0, const __nv_bfloat16 *ops, cudaStream_t stream)
+{
+    using C = TcCfg<N>;
+    constexpr int NOPS = NPASS / 2;
+    auto kern = k_tc_split<N, NPASS, TERMS, TILED>;
+    const size_t smem = (size_t)TERMS * C::A_TERM_BYTES + (size_t)NOPS * 3 * C::B_TERM_BYTES + 64;
+    static int blocks_per_sm[64], num_sms[64];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (blocks_per_sm[dev] == 0) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int occ = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 128, smem);
+        if (e != cudaSuccess) return e;
+        // resident CTAs must fit in the 512 TMEM columns, or tcgen05.alloc would wait
+        const int tmem_cap = 512 / C::TMEM_COLS;
+        blocks_per_sm[dev] = occ < tmem_cap ? occ : tmem_cap;
+        e = cudaDeviceGetAttribute(&num_sms[dev], cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        if (blocks_per_sm[dev] < 1) return cudaErrorInvalidConfiguration;
+    }
+    TcParams p = p0;
+    p.ops = ops;
+    long long nt;
+    if (!TILED) {
+        nt = (p.count + C::G - 1) / C::G;
+    } else {
+        p.chunks_per_row = (p.tiles_per_row + C::G - 1) / C::G;
+        nt = (p.count / p.tiles_per_row) * p.chunks_per_row;
+    }
+    if (nt <= 0) return cudaSuccess;
+    if (nt > 0x7ff00000LL) return cudaErrorInvalidValue;
+    p.ntiles = (int)nt;
+    long long grid = (long long)blocks_per_sm[dev] * num_sms[dev];
+    if (grid > nt) grid = nt;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(128);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, p);
+}
+
+template <int N, int TERMS>
+static cudaError_t tc_launch_nt(Dir dir, const TcParams &p, const __nv_bfloat16 *ops, cudaStream_t s, bool tiled)
+{
+    if (dir == DIR_RT)
+        return tiled ? tc_launch_one<N, 4, TERMS, true>(p, ops, s) : tc_launch_one<N, 4, TERMS, false>(p, ops, s);
+    return tiled ? tc_launch_one<N, 2, TERMS, true>(p, ops, s) : tc_launch_one<N, 2, TERMS, false>(p, ops, s);
+}
+
+template <int N>
+static cudaError_t tc_launch_n(Dir dir, int terms, const TcParams &p, const __nv_bfloat16 *ops, cudaStream_t s,
+                               bool tiled)
+{
+    switch (terms) {
+        case 3: return tc_launch_nt<N, 3>(dir, p, ops, s, tiled);
+        case 2: return tc_launch_nt<N, 2>(dir, p, ops, s, tiled);
+        default: return tc_launch_nt<N, 1>(dir, p, ops, s, tiled);
+    }
+}
+
+cudaError_t tc_launch(int n, Dir dir, int terms, const ExecGeom &g, const __nv_bfloat16 *ops, unsigned int *status,
+                      cudaStream_t stream)
+{
+    TcParams p{};
+    p.in = g.in;
+    p.out = g.out;
+    p.count = g.count;
+    p.tiles_per_row = g.tiles_per_row;
+    p.ld_in = g.ld_in;
+    p.ld_out = g.ld_out;
+    p.status = status;
+    const bool tiled = g.tiled != 0;
+    switch (n) {
+        case 16: return tc_launch_n<16>(dir, terms, p, ops, stream, tiled);
+        case 32: return tc_launch_n<32>(dir, terms, p, ops, stream, tiled);
+        case 64: return tc_launch_n<64>(dir, terms, p, ops, stream, tiled);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace bdct

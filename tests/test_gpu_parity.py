@@ -229,3 +229,59 @@ def test_bounded_wait_gives_up_with_status(cuda_dev):
     torch.cuda.synchronize()
     assert abs(float(y[0, 0, 0]) - 8.0) < 1e-5
     assert plan.device_status() == 0
+
+
+# ------------------------------------------------------------ tensor-core route
+@pytest.mark.parametrize("n", [16, 32, 64])
+@pytest.mark.parametrize("norm", [0, 1])
+def test_split_tc_accepted(oracle_mod, cuda_dev, n, norm):
+    """Split-BF16 tcgen05 route, three terms / six products: accepted bars."""
+    from paper_2609_28519_gb300 import Plan
+    plan = Plan(n, n, norm=norm, path="split_tc")
+    assert plan.info().variant == 3
+    per_tile = 128 // n
+    batch = 7 * per_tile + 1  # several tiles and a ragged tail
+    x = inputs.uniform(4000 + n + norm, batch, n, n)
+    for kind in KINDS:
+        y = _run(plan, kind, x, cuda_dev)
+        _assert_parity(oracle_mod, y, _ref(oracle_mod, kind, x, norm), x, norm, kind, ("tc", n, norm, kind))
+    assert plan.device_status() == 0
+
+
+@pytest.mark.parametrize("n", [16, 64])
+def test_split_tc_report_only_variants(oracle_mod, cuda_dev, n):
+    """hi/lo (2 terms, 3 products) and single BF16: reported, not accepted.
+    Their errors must sit where the term count puts them."""
+    from paper_2609_28519_gb300 import Plan
+    x = inputs.uniform(4100 + n, 16, n, n)
+    ref = oracle_mod.forward(x, 0)
+    errs = {}
+    for path in ("split_hilo", "bf16"):
+        y = _run(Plan(n, n, path=path), "forward", x, cuda_dev)
+        errs[path] = oracle_mod.metrics(y, ref, x)["e_rel_max"]
+    assert 1e-7 < errs["split_hilo"] < 1e-4
+    assert 1e-4 < errs["bf16"] < 3e-2
+
+
+def test_split_tc_image_tiles(oracle_mod, cuda_dev):
+    """The 2048x2048 image as 16x16 blocks through the tensor-core route."""
+    import torch
+    from paper_2609_28519_gb300 import Plan
+    img = inputs.ramp_image(2)
+    blocks = inputs.image_to_blocks(img, 16, 16)
+    plan = Plan(16, 16, path="split_tc")
+    dimg = torch.from_numpy(img).to(cuda_dev)
+    spec = plan.execute_tiled("forward", dimg)
+    back = plan.execute_tiled("inverse", spec)
+    torch.cuda.synchronize()
+    spec_b = inputs.image_to_blocks(spec.cpu().numpy(), 16, 16)
+    _assert_parity(oracle_mod, spec_b, oracle_mod.forward(blocks, 0), blocks, 0, "forward", "tc-tiled")
+    back_b = inputs.image_to_blocks(back.cpu().numpy(), 16, 16)
+    _assert_parity(oracle_mod, back_b, blocks.astype(np.float64), blocks, 0, "roundtrip", "tc-f-then-i")
+
+
+def test_auto_picks_tensor_core_where_no_fused_fp32(cuda_dev):
+    from paper_2609_28519_gb300 import Plan
+    assert Plan(64, 64).info().variant == 3
+    assert Plan(16, 16).info().variant == 1
+    assert Plan(128, 128).info().variant == 2
