@@ -169,13 +169,14 @@ def run_reference(args):
 
 
 def traffic_from_profiles(kernel_key: str):
-    """DRAM bytes per launch recorded by an ncu capture, if the kernel source
-    has not changed since (the summary stores the source hash)."""
+    """DRAM bytes per launch recorded by an ncu capture, if the kernel's source
+    file has not changed since (the summary stores the source hash)."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "traffic_per_launch.txt")
     if not os.path.exists(p):
         return None
-    src = os.path.join(ROOT, "paper_2609_28519_gb300", "csrc", "fp32_fused.cu")
+    fname = "tc_split.cu" if kernel_key.startswith("k_tc_split") else "fp32_fused.cu"
+    src = os.path.join(ROOT, "paper_2609_28519_gb300", "csrc", fname)
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     for ln in open(p):
         parts = ln.split()
@@ -185,61 +186,53 @@ def traffic_from_profiles(kernel_key: str):
     return None
 
 
-def run_ours(args):
+class ImageWorkload:
+    """The rotating pool of images, spectra and outputs on one device."""
+
+    def __init__(self, dev, rank):
+        import torch
+        from paper_2609_28519_gb300 import inputs
+        l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+        self.img_bytes = IMG * IMG * 4
+        self.pool = max(4, int(np.ceil(2.5 * l2 / (3 * self.img_bytes))))
+        base = torch.from_numpy(inputs.ramp_image(2 + rank)).to(dev)
+        self.imgs = [base.clone() for _ in range(self.pool)]
+        for i in range(1, self.pool):
+            self.imgs[i].add_(float(i) * 1e-3)
+        self.specs = [torch.empty_like(base) for _ in range(self.pool)]
+        self.outs = [torch.empty_like(base) for _ in range(self.pool)]
+
+
+def time_path(path, work, dev, stream, steps, warmup):
+    """Graph-timed forward-then-inverse steps of one path; returns timings in ms
+    and the plan's resolved variant."""
+    import ctypes
     import torch
-    rank, world, local = _dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    from paper_2609_28519_gb300 import Plan, inputs, native
-    from paper_2609_28519_gb300 import build as B
-    if not os.path.exists(native.LIB_PATH):
-        B.build()
-    plan = Plan(BLK, BLK, kind=native.FORWARD | native.INVERSE | native.ROUNDTRIP, norm="ortho",
-                path=args.path)
+    from paper_2609_28519_gb300 import Plan, native
+    plan = Plan(BLK, BLK, kind=native.FORWARD | native.INVERSE | native.ROUNDTRIP, norm="ortho", path=path)
     info = plan.info()
     L = native.lib()
-
-    # pool of images: inputs + spectra + outputs > 2 x L2
-    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
-    img_bytes = IMG * IMG * 4
-    pool = max(4, int(np.ceil(2.5 * l2 / (3 * img_bytes))))
-    base = torch.from_numpy(inputs.ramp_image(2 + rank)).to(dev)
-    imgs = [base.clone() for _ in range(pool)]
-    for i in range(1, pool):
-        imgs[i].add_(float(i) * 1e-3)
-    specs = [torch.empty_like(base) for _ in range(pool)]
-    outs = [torch.empty_like(base) for _ in range(pool)]
-    stream = torch.cuda.current_stream(dev)
-    s_ptr = __import__("ctypes").c_void_p(stream.cuda_stream)
-    c_void_p = __import__("ctypes").c_void_p
-    ptr_in = [c_void_p(t.data_ptr()) for t in imgs]
-    ptr_sp = [c_void_p(t.data_ptr()) for t in specs]
-    ptr_out = [c_void_p(t.data_ptr()) for t in outs]
+    c_void_p = ctypes.c_void_p
+    pool = work.pool
+    p_in = [c_void_p(t.data_ptr()) for t in work.imgs]
+    p_sp = [c_void_p(t.data_ptr()) for t in work.specs]
+    p_out = [c_void_p(t.data_ptr()) for t in work.outs]
     h = plan.handle
     ex = L.bdct_execute_tiled
 
-    def step(i, evs=None):
-        k = i % pool
-        if evs is not None:
-            evs[0].record(stream)
-        st = ex(h, native.FORWARD, ptr_in[k], ptr_sp[k], IMG, IMG, IMG, IMG, s_ptr)
-        if evs is not None:
-            evs[1].record(stream)
-        st |= ex(h, native.INVERSE, ptr_sp[k], ptr_out[k], IMG, IMG, IMG, IMG, s_ptr)
-        if evs is not None:
-            evs[2].record(stream)
-        if st:
-            raise RuntimeError(f"bdct_execute_tiled failed: {st}")
+    def launch(kind, src, dst, sp):
+        if ex(h, kind, src, dst, IMG, IMG, IMG, IMG, sp):
+            raise RuntimeError("bdct_execute_tiled failed")
 
-    for i in range(args.warmup):
-        step(i)
+    s_cur = c_void_p(stream.cuda_stream)
+    for i in range(warmup):
+        k = i % pool
+        launch(native.FORWARD, p_in[k], p_sp[k], s_cur)
+        launch(native.INVERSE, p_sp[k], p_out[k], s_cur)
     torch.cuda.synchronize()
 
     # The steps are tiny (16 MiB per launch), so host launch latency would
-    # dominate a Python loop: the K timed steps are captured once into a CUDA
+    # dominate a Python loop: the timed steps are captured once into a CUDA
     # graph and replayed, which feeds the GPU back to back.
     def capture(fn):
         g = torch.cuda.CUDAGraph()
@@ -251,54 +244,82 @@ def run_ours(args):
         return g
 
     def steps_fn(sp):
-        for i in range(args.steps):
+        for i in range(steps):
             k = i % pool
-            st = ex(h, native.FORWARD, ptr_in[k], ptr_sp[k], IMG, IMG, IMG, IMG, sp)
-            st |= ex(h, native.INVERSE, ptr_sp[k], ptr_out[k], IMG, IMG, IMG, IMG, sp)
-            if st:
-                raise RuntimeError(f"bdct_execute_tiled failed: {st}")
+            launch(native.FORWARD, p_in[k], p_sp[k], sp)
+            launch(native.INVERSE, p_sp[k], p_out[k], sp)
 
     def only_fn(kind, src, dst):
         def fn(sp):
-            for i in range(args.steps):
+            for i in range(steps):
                 k = i % pool
-                if ex(h, kind, src[k], dst[k], IMG, IMG, IMG, IMG, sp):
-                    raise RuntimeError("bdct_execute_tiled failed")
+                launch(kind, src[k], dst[k], sp)
         return fn
 
-    g_steps = capture(steps_fn)
-    g_fwd = capture(only_fn(native.FORWARD, ptr_in, ptr_sp))
-    g_inv = capture(only_fn(native.INVERSE, ptr_sp, ptr_out))
-    for g in (g_steps, g_fwd, g_inv):
+    graphs = {"steps": capture(steps_fn), "forward": capture(only_fn(native.FORWARD, p_in, p_sp)),
+              "inverse": capture(only_fn(native.INVERSE, p_sp, p_out))}
+    for g in graphs.values():
         g.replay()
     torch.cuda.synchronize()
+    return plan, info, graphs
+
+
+def replay_ms(g, stream):
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    g.replay()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b)
+
+
+def path_accuracy(work):
+    """Forward error of spectra[0] and forward-then-inverse error of outs[0]
+    against the FP64 oracle on 256 sampled blocks."""
+    import oracle
+    from paper_2609_28519_gb300 import inputs
+    src = inputs.image_to_blocks(work.imgs[0].cpu().numpy(), BLK, BLK)
+    spec = inputs.image_to_blocks(work.specs[0].cpu().numpy(), BLK, BLK)
+    back = inputs.image_to_blocks(work.outs[0].cpu().numpy(), BLK, BLK)
+    idx = np.random.default_rng(0).choice(len(src), 256, replace=False)
+    mf = oracle.metrics(spec[idx], oracle.forward(src[idx], 0), src[idx])
+    mb = oracle.metrics(back[idx], src[idx].astype(np.float64), src[idx])
+    return {"forward_e_rel_max": mf["e_rel_max"], "forward_max_abs_ratio": mf["max_abs_ratio_max"],
+            "f_then_i_e_rel_max": mb["e_rel_max"], "accepted": bool(oracle.accept(mf) and oracle.accept(mb)),
+            "sampled_blocks": 256}
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = _dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2609_28519_gb300 import native
+    from paper_2609_28519_gb300 import build as B
+    if not os.path.exists(native.LIB_PATH):
+        B.build()
+    import ctypes
+    stream = torch.cuda.current_stream(dev)
+    work = ImageWorkload(dev, rank)
+    plan, info, graphs = time_path(args.path, work, dev, stream, args.steps, args.warmup)
 
     # ---- timed region: K steps (graph replay), CUDA events on the launch stream
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    t_start.record(stream)
-    g_steps.replay()
-    t_end.record(stream)
-    torch.cuda.synchronize()
+    ms_total = replay_ms(graphs["steps"], stream)
     if world > 1:
         torch.distributed.barrier()
     # per-kernel averages: the same K launches of one kernel alone, same pool
-    kt = {}
-    for name, g in (("forward", g_fwd), ("inverse", g_inv)):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        g.replay()
-        b.record(stream)
-        torch.cuda.synchronize()
-        kt[name] = a.elapsed_time(b) / args.steps
+    kt = {name: replay_ms(graphs[name], stream) / args.steps for name in ("forward", "inverse")}
     clocks = sampler.stop()
-    ms_total = t_start.elapsed_time(t_end)
     if world > 1:
         t = torch.tensor([ms_total], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -306,11 +327,12 @@ def run_ours(args):
     elems = IMG * IMG
     step_bytes = elems * BYTES_PER_ELEM_STEP
     value = world * args.steps * step_bytes / (ms_total * 1e-3) / 1e9
+    kern = {1: "k_fused", 3: "k_tc_split"}.get(info.variant, "dense")
 
     # ---- dominant kernel roofline (8 B/element/launch)
     fwd_avg, inv_avg = kt["forward"], kt["inverse"]
-    dom_key, dom_avg = ("k_fused<16,16,FWD,tiled>", fwd_avg) if fwd_avg >= inv_avg else \
-        ("k_fused<16,16,INV,tiled>", inv_avg)
+    dom_key, dom_avg = (f"{kern}<16,16,FWD,tiled>", fwd_avg) if fwd_avg >= inv_avg else \
+        (f"{kern}<16,16,INV,tiled>", inv_avg)
     peak, peak_kind = _peaks()
     achieved = elems * 8 / (dom_avg * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -319,12 +341,37 @@ def run_ours(args):
                 "avg_launch_us": {"forward": fwd_avg * 1e3, "inverse": inv_avg * 1e3},
                 "timing": "K back-to-back launches of the kernel alone (CUDA graph), same rotating pool"}
 
+    parity = path_accuracy(work) if (rank == 0 and not args.no_check) else None
+
+    # ---- the same workload on every path (FP32 vs split-BF16 tensor cores)
+    paths = None
+    if rank == 0 and not args.no_paths:
+        paths = {}
+        for pth in ("fp32", "split_tc", "split_hilo", "bf16"):
+            ksteps = min(args.steps, 200)
+            pl, inf, gr = time_path(pth, work, dev, stream, ksteps, 3)
+            ms = replay_ms(gr["steps"], stream)
+            f_ms = replay_ms(gr["forward"], stream) / ksteps
+            entry = {"variant": inf.variant, "GB/s": ksteps * step_bytes / (ms * 1e-3) / 1e9,
+                     "forward_us": f_ms * 1e3,
+                     "forward_frac_of_hbm": elems * 8 / (f_ms * 1e-3) / 1e9 / peak}
+            if not args.no_check:
+                entry.update(path_accuracy(work))
+            paths[pth] = entry
+            pl.close()
+
     # ---- end to end through host buffers (pinned), copies inside the timed region
     e2e = None
     if rank == 0 or world > 1:
+        from paper_2609_28519_gb300 import inputs
+        L = native.lib()
+        h = plan.handle
+        ex = L.bdct_execute_tiled
+        c_void_p = ctypes.c_void_p
+        s_ptr = c_void_p(stream.cuda_stream)
         host_in = torch.from_numpy(inputs.ramp_image(2 + rank)).pin_memory()
         host_out = torch.empty_like(host_in).pin_memory()
-        d_in, d_sp, d_out = imgs[0], specs[0], outs[0]
+        d_in, d_sp, d_out = work.imgs[0], work.specs[0], work.outs[0]
         pin, psp, pout = c_void_p(d_in.data_ptr()), c_void_p(d_sp.data_ptr()), c_void_p(d_out.data_ptr())
         k_e2e = max(10, args.steps // 4)
 
@@ -345,22 +392,9 @@ def run_ours(args):
         torch.cuda.synchronize()
         e2e_ms = a.elapsed_time(b) / k_e2e
         e2e = {"value": world * step_bytes / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
-               "h2d_bytes_per_step": img_bytes, "d2h_bytes_per_step": img_bytes,
-               "ms_per_step": e2e_ms, "steps": k_e2e}
-
-    # ---- correctness of the timed configuration on sampled blocks
-    parity = None
-    if rank == 0 and not args.no_check:
-        import oracle
-        sp = specs[0].cpu().numpy()
-        src = imgs[0].cpu().numpy()
-        blocks = inputs.image_to_blocks(src, BLK, BLK)
-        got = inputs.image_to_blocks(sp, BLK, BLK)
-        rng = np.random.default_rng(0)
-        idx = rng.choice(len(blocks), 256, replace=False)
-        m = oracle.metrics(got[idx], oracle.forward(blocks[idx], 0), blocks[idx])
-        parity = {"forward_e_rel_max": m["e_rel_max"], "forward_max_abs_ratio": m["max_abs_ratio_max"],
-                  "sampled_blocks": 256}
+               "h2d_bytes_per_step": work.img_bytes, "d2h_bytes_per_step": work.img_bytes,
+               "ms_per_step": e2e_ms, "steps": k_e2e,
+               "how": "pinned host image -> device, forward, inverse, device -> pinned host, per step"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -376,7 +410,7 @@ def run_ours(args):
                                    "per block (tiled view), path " + args.path,
                        "global_batch": 16384 * world, "seq_len": None,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "l2": f"rotating pool of {pool} images ({3 * pool * img_bytes >> 20} MiB) > 2x L2",
+                       "l2": f"rotating pool of {work.pool} images ({3 * work.pool * work.img_bytes >> 20} MiB) > 2x L2",
                        "plan_variant": info.variant, "plan_path": info.path,
                        "elements_per_s": world * args.steps * elems / (ms_total * 1e-3)},
             "roofline": roofline,
@@ -386,6 +420,7 @@ def run_ours(args):
             "launch": "CUDA graph of the K steps (2 kernels per step)",
             "clocks": clocks,
             "parity": parity,
+            "paths": paths,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -435,9 +470,10 @@ def main():
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--path", default="auto", choices=["auto", "fp32", "split_tc"])
+    ap.add_argument("--path", default="auto", choices=["auto", "fp32", "split_tc", "split_hilo", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--no-paths", action="store_true", help="skip the per-path comparison")
     ap.add_argument("--sweep", action="store_true", help="square-size sweep instead of the headline")
     ap.add_argument("--sizes", default="8,16,32,64,128,256")
     args = ap.parse_args()

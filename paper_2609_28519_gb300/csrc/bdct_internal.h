@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 #include "bdct.h"
 
@@ -36,6 +37,14 @@ struct ExecGeom {
 };
 
 enum Dir { DIR_FWD = 0, DIR_INV = 1, DIR_RT = 2 };
+
+// True when the environment variable BDCT_DEBUG is set: kernel launchers then
+// print their launch configuration once to stderr.
+inline bool debug_enabled()
+{
+    static const bool on = getenv("BDCT_DEBUG") != nullptr;
+    return on;
+}
 
 // ---- fp32_fused.cu
 // Builds the cosine table in constant memory of the current device (FP64 on

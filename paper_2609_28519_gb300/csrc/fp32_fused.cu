@@ -29,6 +29,8 @@
 #include "bdct_internal.h"
 #include "ptx.cuh"
 
+#include <cstdio>
+
 namespace bdct {
 
 static __constant__ float c_cos[4097];  // cos(pi r / 8192), r = 0..4096
@@ -212,48 +214,67 @@ __device__ __forceinline__ void line_op(float (&x)[N], AxisScale s)
 //    at r*SP, SP = G*w + 4 floats, one bulk copy per image row; pass 1 lanes
 //    take 32 adjacent strip columns, pass 2 lanes take 8 rows of one tile,
 //    which the odd 16-byte row pitch spreads over all banks.
-template <int H, int W>
+// Shared-memory layouts of a stage (see the comment above).
+enum Layout { LAY_SLOT = 0, LAY_STRIP = 1, LAY_ROWPAD = 2 };
+
+template <int H, int W, bool TILED>
 struct FusedCfg {
     static constexpr int HW = H * W;
-    static constexpr int G = (HW <= 64) ? 16 : 8;  // arrays per chunk
-    static constexpr int NW_MAX = G * (H < W ? H : W) / 32;
+    static constexpr int LAYOUT = W >= 64 ? LAY_ROWPAD : (TILED ? LAY_STRIP : LAY_SLOT);
+    // arrays per chunk
+    static constexpr int G = LAYOUT == LAY_ROWPAD ? (HW >= 8192 ? 1 : 2) : ((HW <= 64) ? 16 : 8);
+    static constexpr int LINES_MIN = G * (H < W ? H : W);
+    static constexpr int NW_MAX = LINES_MIN / 32;
     static constexpr int NW = NW_MAX > 8 ? 8 : NW_MAX;  // warps per CTA
     static constexpr int THREADS = 32 * NW;
     static constexpr int P = HW + 4;       // slot pitch (floats)
     static constexpr int SP = G * W + 4;   // strip row pitch (floats)
-    static constexpr int STAGE_FLOATS = (G * P > H * SP) ? G * P : H * SP;
+    static constexpr int RP = W + 4;       // padded row pitch (floats)
+    static constexpr int AP = H * RP;      // padded array pitch (floats)
+    static constexpr int STAGE_FLOATS =
+        LAYOUT == LAY_ROWPAD ? G * AP : (LAYOUT == LAY_STRIP ? H * SP : G * P);
     static constexpr int STAGE_BYTES = STAGE_FLOATS * 4;
-    static constexpr int ST_RAW = (32 * 1024) / STAGE_BYTES;
+    static constexpr int ST_RAW = (LAYOUT == LAY_ROWPAD ? 72 * 1024 : 32 * 1024) / STAGE_BYTES;
     static constexpr int STAGES = ST_RAW < 2 ? 2 : (ST_RAW > 4 ? 4 : ST_RAW);
     static constexpr int J1 = G * W / THREADS;  // columns per thread (pass 1)
     static constexpr int J2 = G * H / THREADS;  // rows per thread (pass 2)
     static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + STAGES * 8;
     static_assert(J1 >= 1 && J2 >= 1 && J1 * THREADS == G * W && J2 * THREADS == G * H, "lane mapping");
-    static_assert((P % 8) == 4 && (SP % 8) == 4, "pitches must be 4 mod 8 floats");
+    static_assert((P % 8) == 4 && (SP % 8) == 4 && (RP % 8) == 4, "pitches must be 4 mod 8 floats");
 };
 
 // Element (a, r, c) of a stage: array/tile a, row r, column c.
 template <int H, int W, bool TILED>
 __device__ __forceinline__ int elem(int a, int r, int c)
 {
-    using C = FusedCfg<H, W>;
-    if constexpr (TILED) return r * C::SP + a * W + c;
+    using C = FusedCfg<H, W, TILED>;
+    if constexpr (C::LAYOUT == LAY_ROWPAD) return a * C::AP + r * C::RP + c;
+    else if constexpr (C::LAYOUT == LAY_STRIP) return r * C::SP + a * W + c;
     else return a * C::P + r * W + c;
+}
+
+// Row stride of a stage in floats.
+template <int H, int W, bool TILED>
+__device__ __forceinline__ constexpr int row_stride()
+{
+    using C = FusedCfg<H, W, TILED>;
+    return C::LAYOUT == LAY_ROWPAD ? C::RP : (C::LAYOUT == LAY_STRIP ? C::SP : W);
 }
 
 // Pass 1 line j of this thread -> (array, column).
 template <int H, int W, bool TILED>
 __device__ __forceinline__ void map_col(int j, int warp, int lane, int &a, int &col)
 {
-    using C = FusedCfg<H, W>;
-    if constexpr (TILED) {
-        const int s = lane + 32 * (warp + C::NW * j);  // strip column
-        a = s / W;
-        col = s % W;
-    } else {
+    using C = FusedCfg<H, W, TILED>;
+    if constexpr (C::LAYOUT == LAY_SLOT) {
         const int combo = warp + C::NW * j;
         a = (lane & 7) + 8 * (combo % (C::G / 8));
         col = (lane >> 3) + 4 * (combo / (C::G / 8));
+    } else {
+        // 32 adjacent columns (of the strip, or of one padded array)
+        const int s = lane + 32 * (warp + C::NW * j);
+        a = s / W;
+        col = s % W;
     }
 }
 
@@ -261,15 +282,20 @@ __device__ __forceinline__ void map_col(int j, int warp, int lane, int &a, int &
 template <int H, int W, bool TILED>
 __device__ __forceinline__ void map_row(int j, int warp, int lane, int &a, int &r)
 {
-    using C = FusedCfg<H, W>;
-    if constexpr (TILED) {
+    using C = FusedCfg<H, W, TILED>;
+    if constexpr (C::LAYOUT == LAY_SLOT) {
+        const int combo = warp + C::NW * j;
+        a = (lane & 7) + 8 * (combo % (C::G / 8));
+        r = (lane >> 3) + 4 * (combo / (C::G / 8));
+    } else if constexpr (C::LAYOUT == LAY_STRIP) {
         const int u = (lane >> 3) + 4 * (warp + C::NW * j);
         a = u % C::G;
         r = (lane & 7) + 8 * (u / C::G);
     } else {
-        const int combo = warp + C::NW * j;
-        a = (lane & 7) + 8 * (combo % (C::G / 8));
-        r = (lane >> 3) + 4 * (combo / (C::G / 8));
+        // 32 adjacent rows of one padded array
+        const int s = lane + 32 * (warp + C::NW * j);
+        a = s / H;
+        r = s % H;
     }
 }
 
@@ -296,7 +322,7 @@ struct ChunkGeom {
 template <int H, int W, bool TILED>
 __device__ __forceinline__ ChunkGeom chunk_geom(const FusedParams &p, int c)
 {
-    using C = FusedCfg<H, W>;
+    using C = FusedCfg<H, W, TILED>;
     ChunkGeom g;
     if constexpr (!TILED) {
         g.first = (long long)c * C::G;
@@ -320,16 +346,24 @@ template <int H, int W, bool TILED>
 __device__ __forceinline__ void issue_fill(const FusedParams &p, const ChunkGeom &g, float *stage, uint64_t *bar,
                                            int lane)
 {
-    using C = FusedCfg<H, W>;
+    using C = FusedCfg<H, W, TILED>;
     if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)(g.n * C::HW * 4));
     __syncwarp();
-    if constexpr (!TILED) {
+    if constexpr (C::LAYOUT == LAY_SLOT) {
         for (int a = lane; a < g.n; a += 32)
             bulk_load(stage + a * C::P, p.in + (g.first + a) * C::HW, C::HW * 4, bar);
-    } else {
+    } else if constexpr (C::LAYOUT == LAY_STRIP) {
         for (int r = lane; r < H; r += 32) {
             const float *src = p.in + (g.brow * H + r) * p.ld_in + (long long)g.t0 * W;
             bulk_load(stage + r * C::SP, src, (uint32_t)(g.n * W * 4), bar);
+        }
+    } else {
+        for (int q = lane; q < g.n * H; q += 32) {
+            const int a = q / H, r = q % H;
+            const float *src;
+            if constexpr (TILED) src = p.in + (g.brow * H + r) * p.ld_in + (long long)(g.t0 + a) * W;
+            else src = p.in + (g.first + a) * C::HW + (long long)r * W;
+            bulk_load(stage + a * C::AP + r * C::RP, src, W * 4, bar);
         }
     }
 }
@@ -338,28 +372,36 @@ __device__ __forceinline__ void issue_fill(const FusedParams &p, const ChunkGeom
 template <int H, int W, bool TILED>
 __device__ __forceinline__ void issue_drain(const FusedParams &p, const ChunkGeom &g, const float *stage, int lane)
 {
-    using C = FusedCfg<H, W>;
-    if constexpr (!TILED) {
+    using C = FusedCfg<H, W, TILED>;
+    if constexpr (C::LAYOUT == LAY_SLOT) {
         for (int a = lane; a < g.n; a += 32) bulk_store(p.out + (g.first + a) * C::HW, stage + a * C::P, C::HW * 4);
-    } else {
+    } else if constexpr (C::LAYOUT == LAY_STRIP) {
         for (int r = lane; r < H; r += 32) {
             float *dst = p.out + (g.brow * H + r) * p.ld_out + (long long)g.t0 * W;
             bulk_store(dst, stage + r * C::SP, (uint32_t)(g.n * W * 4));
         }
+    } else {
+        for (int q = lane; q < g.n * H; q += 32) {
+            const int a = q / H, r = q % H;
+            float *dst;
+            if constexpr (TILED) dst = p.out + (g.brow * H + r) * p.ld_out + (long long)(g.t0 + a) * W;
+            else dst = p.out + (g.first + a) * C::HW + (long long)r * W;
+            bulk_store(dst, stage + a * C::AP + r * C::RP, W * 4);
+        }
     }
 }
 
-template <int H, int W>
+template <int NW>
 __device__ __forceinline__ void cta_sync()
 {
-    if constexpr (FusedCfg<H, W>::NW == 1) __syncwarp();
+    if constexpr (NW == 1) __syncwarp();
     else __syncthreads();
 }
 
 template <int H, int W, int DIR, bool TILED>
-__global__ void __launch_bounds__(FusedCfg<H, W>::THREADS) k_fused(const FusedParams p)
+__global__ void __launch_bounds__(FusedCfg<H, W, TILED>::THREADS) k_fused(const FusedParams p)
 {
-    using C = FusedCfg<H, W>;
+    using C = FusedCfg<H, W, TILED>;
     extern __shared__ __align__(128) float smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + C::STAGES * C::STAGE_FLOATS);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -406,7 +448,7 @@ __global__ void __launch_bounds__(FusedCfg<H, W>::THREADS) k_fused(const FusedPa
             map_col<H, W, TILED>(j, warp, lane, a, col);
             if (a < n) {
                 float *q = stage + elem<H, W, TILED>(a, 0, col);
-                constexpr int RS = TILED ? C::SP : W;  // row stride
+                constexpr int RS = row_stride<H, W, TILED>();
                 float x[H];
 #pragma unroll
                 for (int i = 0; i < H; ++i) x[i] = q[i * RS];
@@ -415,7 +457,7 @@ __global__ void __launch_bounds__(FusedCfg<H, W>::THREADS) k_fused(const FusedPa
                 for (int i = 0; i < H; ++i) q[i * RS] = x[i];
             }
         }
-        cta_sync<H, W>();
+        cta_sync<C::NW>();
 
         // pass 2: one row per thread per step, 1D core along w
 #pragma unroll
@@ -436,7 +478,7 @@ __global__ void __launch_bounds__(FusedCfg<H, W>::THREADS) k_fused(const FusedPa
             }
         }
         fence_proxy_async_smem();
-        cta_sync<H, W>();
+        cta_sync<C::NW>();
 
         if (warp == 0) {
             // bulk groups are per thread: every lane commits the stores it issued
@@ -489,13 +531,13 @@ cudaError_t fused_init_device(int device)
 bool fused_supported(int rows, int cols)
 {
     auto ok = [](int n) { return n == 8 || n == 16 || n == 32; };
-    return ok(rows) && ok(cols);
+    return (ok(rows) && ok(cols)) || (rows == 64 && cols == 64);
 }
 
 template <int H, int W, int DIR, bool TILED>
 static cudaError_t launch_one(const DirScales &sc, const ExecGeom &g, unsigned int *status, cudaStream_t stream)
 {
-    using C = FusedCfg<H, W>;
+    using C = FusedCfg<H, W, TILED>;
     auto kern = k_fused<H, W, DIR, TILED>;
     static int blocks_per_sm[64];
     static int num_sms[64];
@@ -511,6 +553,9 @@ static cudaError_t launch_one(const DirScales &sc, const ExecGeom &g, unsigned i
         e = cudaDeviceGetAttribute(&num_sms[dev], cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
         if (blocks_per_sm[dev] < 1) return cudaErrorInvalidConfiguration;
+        if (debug_enabled())
+            fprintf(stderr, "[bdct] k_fused<%d,%d,%d,%d>: %d CTAs/SM x %d threads, %d stages, smem %zu B\n", H, W, DIR,
+                    (int)TILED, blocks_per_sm[dev], C::THREADS, C::STAGES, C::SMEM);
     }
     FusedParams p{};
     p.in = g.in;
@@ -575,6 +620,7 @@ static cudaError_t launch_h(int cols, Dir dir, const DirScales &sc, const ExecGe
 cudaError_t fused_launch(int rows, int cols, Dir dir, const DirScales &sc, const ExecGeom &g,
                          unsigned int *status, cudaStream_t stream)
 {
+    if (rows == 64 && cols == 64) return launch_hw<64, 64>(dir, sc, g, status, stream);
     switch (rows) {
         case 8: return launch_h<8>(cols, dir, sc, g, status, stream);
         case 16: return launch_h<16>(cols, dir, sc, g, status, stream);

@@ -36,6 +36,8 @@
 #include "bdct_internal.h"
 #include "ptx.cuh"
 
+#include <cstdio>
+
 namespace bdct {
 
 // ------------------------------------------------------------ PTX wrappers
@@ -400,15 +402,33 @@ static cudaError_t tc_launch_one(const TcParams &p0, const __nv_bfloat16 *ops, c
     if (blocks_per_sm[dev] == 0) {
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        int occ = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 128, smem);
+        // Resident CTAs per SM from threads, registers and shared memory, capped so
+        // that their TMEM allocations fit in the 512 columns (a CTA beyond that
+        // would wait in tcgen05.alloc until another one exits).  Computed here
+        // because the runtime's occupancy query reports one CTA for kernels that
+        // allocate tensor memory.
+        cudaFuncAttributes fa;
+        e = cudaFuncGetAttributes(&fa, kern);
         if (e != cudaSuccess) return e;
-        // resident CTAs must fit in the 512 TMEM columns, or tcgen05.alloc would wait
+        int smem_per_sm = 0, regs_per_sm = 0, reserved = 0;
+        cudaDeviceGetAttribute(&smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        cudaDeviceGetAttribute(&regs_per_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+        const int by_threads = 2048 / 128;
+        const int regs_cta = ((fa.numRegs * 32 + 255) / 256) * 256 * 4;  // per-warp allocation granularity
+        const int by_regs = regs_cta > 0 ? regs_per_sm / regs_cta : by_threads;
+        const int by_smem = (int)((size_t)smem_per_sm / (smem + fa.sharedSizeBytes + (size_t)reserved));
         const int tmem_cap = 512 / C::TMEM_COLS;
+        int occ = by_threads;
+        if (by_regs < occ) occ = by_regs;
+        if (by_smem < occ) occ = by_smem;
         blocks_per_sm[dev] = occ < tmem_cap ? occ : tmem_cap;
         e = cudaDeviceGetAttribute(&num_sms[dev], cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
         if (blocks_per_sm[dev] < 1) return cudaErrorInvalidConfiguration;
+        if (debug_enabled())
+            fprintf(stderr, "[bdct] k_tc_split<%d,%d,%d,%d>: %d CTAs/SM (regs %d, smem %zu B, TMEM cap %d)\n", N,
+                    NPASS, TERMS, (int)TILED, blocks_per_sm[dev], fa.numRegs, smem, tmem_cap);
     }
     TcParams p = p0;
     p.ops = ops;

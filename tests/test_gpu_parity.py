@@ -12,7 +12,7 @@ from paper_2609_28519_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-FUSED_SHAPES = [(h, w) for h in (8, 16, 32) for w in (8, 16, 32)]
+FUSED_SHAPES = [(h, w) for h in (8, 16, 32) for w in (8, 16, 32)] + [(64, 64)]
 SEPARABLE_SHAPES = [(64, 64), (128, 128), (256, 256), (64, 256), (128, 512), (24, 40), (12, 8)]
 KINDS = ["forward", "inverse", "roundtrip"]
 
@@ -48,8 +48,8 @@ def test_fused_shapes_all_kinds(oracle_mod, cuda_dev, h, w, norm):
     from paper_2609_28519_gb300 import Plan
     plan = Plan(h, w, norm=norm, path="fp32")
     assert plan.info().variant == 1
-    per_cta = 256 // max(h, w)
-    batch = 5 * per_cta + 3  # several CTAs and a ragged tail
+    per_chunk = 16 if h * w <= 64 else (8 if max(h, w) <= 32 else 2)
+    batch = 5 * per_chunk + 3  # several chunks and a ragged tail
     x = inputs.uniform(1000 + h * 7 + w, batch, h, w)
     for kind in KINDS:
         y = _run(plan, kind, x, cuda_dev)
@@ -170,6 +170,20 @@ def test_sweep_distributions(oracle_mod, cuda_dev, n):
     assert np.all(np.isfinite(weak_rel))  # reported, not accepted
 
 
+def test_fused_64_tiled_image(oracle_mod, cuda_dev):
+    """64x64 blocks of a 1024x512 image through the padded-row layout."""
+    import torch
+    from paper_2609_28519_gb300 import Plan
+    img = inputs.ramp_image(9, 1024, 512)
+    blocks = inputs.image_to_blocks(img, 64, 64)
+    plan = Plan(64, 64)
+    d = torch.from_numpy(img).to(cuda_dev)
+    spec = plan.execute_tiled("forward", d)
+    torch.cuda.synchronize()
+    got = inputs.image_to_blocks(spec.cpu().numpy(), 64, 64)
+    _assert_parity(oracle_mod, got, oracle_mod.forward(blocks, 0), blocks, 0, "forward", "tiled64")
+
+
 def test_inplace_and_tail_and_guards(oracle_mod, cuda_dev):
     import torch
     from paper_2609_28519_gb300 import Plan
@@ -280,8 +294,9 @@ def test_split_tc_image_tiles(oracle_mod, cuda_dev):
     _assert_parity(oracle_mod, back_b, blocks.astype(np.float64), blocks, 0, "roundtrip", "tc-f-then-i")
 
 
-def test_auto_picks_tensor_core_where_no_fused_fp32(cuda_dev):
+def test_auto_path_choice(cuda_dev):
     from paper_2609_28519_gb300 import Plan
-    assert Plan(64, 64).info().variant == 3
+    assert Plan(64, 64).info().variant == 1
     assert Plan(16, 16).info().variant == 1
     assert Plan(128, 128).info().variant == 2
+    assert Plan(64, 64, path="split_tc").info().variant == 3
