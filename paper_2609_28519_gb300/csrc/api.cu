@@ -36,7 +36,8 @@ struct bdct_plan {
     unsigned kind = 0;
     int norm = 0;
     int path = 0;
-    int variant = 0;  // 1 fused register tile, 2 separable dense passes, 3 tensor core
+    int variant = 0;  // 1 fused register tile, 2 separable passes, 3 tensor core
+    bool lines = false;  // separable passes through the FFT line engine (else dense GEMM passes)
     int device = -1;
     DirScales scales[3];  // per Dir
     // separable route
@@ -168,6 +169,17 @@ extern "C" int bdct_plan_create(bdct_plan **plan, int rows, int cols, unsigned k
         if (e != cudaSuccess) { plan_free(p); return cuda_fail(e); }
     } else if (fused_supported(rows, cols)) {
         p->variant = 1;
+    } else if (lines_supported(rows) && lines_supported(cols)) {
+        // two FFT line passes through the workspace, each writing transposed
+        p->variant = 2;
+        p->lines = true;
+        const size_t arr_bytes = (size_t)rows * cols * sizeof(float);
+        long long chunk = (long long)(kChunkBytes / arr_bytes);
+        if (chunk < 1) chunk = 1;
+        p->chunk_arrays = chunk;
+        p->work_bytes = (size_t)chunk * arr_bytes;
+        e = cudaMalloc(&p->work, p->work_bytes);
+        if (e != cudaSuccess) { plan_free(p); t_last_cuda_error = (int)e; return BDCT_ERR_NO_MEMORY; }
     } else {
         p->variant = 2;
         // operator matrices: forward and inverse in the plan's norm, and the
@@ -245,9 +257,24 @@ static bool ranges_partially_overlap(const void *a, const void *b, size_t bytes)
     return x < y + bytes && y < x + bytes;
 }
 
+static int run_lines(const bdct_plan *p, Dir dir, const float *in, float *out, long long count, cudaStream_t s)
+{
+    const int h = p->rows, w = p->cols;
+    const long long hw = (long long)h * w;
+    for (long long b0 = 0; b0 < count; b0 += p->chunk_arrays) {
+        const long long nb = (count - b0) < p->chunk_arrays ? (count - b0) : p->chunk_arrays;
+        // rows of X (h lines of w) -> workspace (w x h), then rows of that (w lines of h) -> out (h x w)
+        cudaError_t e = lines_pass(in + b0 * hw, p->work, h, w, nb, dir, p->scales[dir].w, p->status, s);
+        if (e == cudaSuccess) e = lines_pass(p->work, out + b0 * hw, w, h, nb, dir, p->scales[dir].h, p->status, s);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return BDCT_OK;
+}
+
 static int run_separable(const bdct_plan *p, Dir dir, const float *in, float *out, long long count,
                          cudaStream_t s)
 {
+    if (p->lines) return run_lines(p, dir, in, out, count, s);
     const int h = p->rows, w = p->cols;
     const long long hw = (long long)h * w;
     const float *oph = p->ops + p->op_h_off[dir];

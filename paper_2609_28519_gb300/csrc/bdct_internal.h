@@ -56,6 +56,20 @@ bool fused_supported(int rows, int cols);
 cudaError_t fused_launch(int rows, int cols, Dir dir, const DirScales &sc, const ExecGeom &g,
                          unsigned int *status, cudaStream_t stream);
 
+// ---- fp32_lines.cu
+// Copy the cosine table (device buffer, 4097 floats) into the line engine's
+// constant memory (called by fused_init_device).
+cudaError_t lines_init_table(const float *d_table);
+// True if n has an FFT-based line engine (powers of two 64..4096).
+bool lines_supported(int n);
+// One separable pass over `count` arrays of rows x n: every row (length n)
+// gets the 1D transform of `dir` with per-index scales `sc` (forward: output
+// scale, inverse: input scale, round trip: the E^2 correction), and the
+// result is written transposed: dst[b][k][r] = row r's output k, arrays of
+// n x rows.  Two such passes give the 2D transform in natural layout.
+cudaError_t lines_pass(const float *src, float *dst, int rows, int n, long long count, Dir dir,
+                       AxisScale sc, unsigned int *status, cudaStream_t stream);
+
 // ---- tc_split.cu
 // Split-BF16 tcgen05 route for square sides 16, 32, 64.
 bool tc_supported(int rows, int cols);

@@ -13,7 +13,8 @@ from paper_2609_28519_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 FUSED_SHAPES = [(h, w) for h in (8, 16, 32) for w in (8, 16, 32)] + [(64, 64)]
-SEPARABLE_SHAPES = [(64, 64), (128, 128), (256, 256), (64, 256), (128, 512), (24, 40), (12, 8)]
+SEPARABLE_SHAPES = [(128, 128), (256, 256), (64, 256), (128, 512), (1024, 1024), (2048, 64),
+                    (512, 2048), (24, 40), (12, 8), (768, 64)]
 KINDS = ["forward", "inverse", "roundtrip"]
 
 
@@ -57,14 +58,18 @@ def test_fused_shapes_all_kinds(oracle_mod, cuda_dev, h, w, norm):
 
 
 @pytest.mark.parametrize("h,w", SEPARABLE_SHAPES)
-def test_separable_shapes(oracle_mod, cuda_dev, h, w):
+@pytest.mark.parametrize("norm", [0, 1])
+def test_separable_shapes(oracle_mod, cuda_dev, h, w, norm):
+    """Shapes beyond the fused kernels: FFT line passes for power-of-two sides
+    64..2048, dense passes otherwise."""
     from paper_2609_28519_gb300 import Plan
-    plan = Plan(h, w, norm="ortho", path="fp32")
-    batch = 3
+    plan = Plan(h, w, norm=norm, path="fp32")
+    assert plan.info().variant == 2
+    batch = 3 if h * w <= 65536 else 2
     x = inputs.gaussian(2000 + h + w, batch, h, w)
     for kind in KINDS:
         y = _run(plan, kind, x, cuda_dev)
-        _assert_parity(oracle_mod, y, _ref(oracle_mod, kind, x, 0), x, 0, kind, (h, w, kind))
+        _assert_parity(oracle_mod, y, _ref(oracle_mod, kind, x, norm), x, norm, kind, (h, w, norm, kind))
 
 
 def test_paper_input_categories(oracle_mod, cuda_dev):
