@@ -137,6 +137,43 @@ int bdct_plan_get_info(const bdct_plan *plan, bdct_plan_info *info);
  * returned as usual.                                                         */
 int bdct_plan_device_status(const bdct_plan *plan, int clear);
 
+/* ------------------------------------------------------------ ragged batches
+ * A batch of arrays of mixed shapes (the paper transforms one array per call
+ * and loops over batches in C, Section 3.2).  Array i has rows[i] x cols[i]
+ * elements, contiguous and row-major, starting in_off[i] and out_off[i]
+ * floats after the base pointers given at execution (offsets multiples of 4;
+ * arrays must not overlap, except an array whose in and out spans coincide).
+ * Arrays are grouped by shape; each group gets a plan whose path, when `path`
+ * is BDCT_PATH_AUTO, is the faster of the accepted candidates (FP32, and the
+ * split-BF16 tensor-core path where it exists) timed on scratch arrays at
+ * creation -- or read from the file named by the environment variable
+ * BDCT_TUNE_CACHE, to which new choices are appended.  Creation allocates,
+ * synchronizes and runs those timing launches.
+ * Execution launches one persistent kernel per shape class, reading the
+ * arrays through device offset tables, from a CUDA graph captured on the first
+ * call for each (kind, in_base, out_base) and replayed afterwards on `stream`.
+ * The first call for new pointers should not itself run inside a stream
+ * capture.  Calls on the same ragged plan must not overlap on the GPU.      */
+typedef struct bdct_ragged bdct_ragged;
+
+typedef struct bdct_ragged_class {
+    int rows, cols;
+    size_t count;              /* arrays of this shape */
+    int path;                  /* chosen path */
+    int variant;               /* kernel family, as in bdct_plan_info */
+    double tuned_us_per_array; /* measured at creation (0 if not timed) */
+} bdct_ragged_class;
+
+int bdct_ragged_create(bdct_ragged **ragged, size_t n, const int *rows, const int *cols,
+                       const size_t *in_off, const size_t *out_off, unsigned kind, int norm, int path);
+int bdct_ragged_execute(bdct_ragged *ragged, unsigned kind, const float *in_base, float *out_base,
+                        void *stream);
+int bdct_ragged_destroy(bdct_ragged *ragged);
+/* Number of shape classes (or a negated status). */
+int bdct_ragged_num_classes(const bdct_ragged *ragged);
+/* Classes are ordered by total elements, largest first. */
+int bdct_ragged_class_info(const bdct_ragged *ragged, int index, bdct_ragged_class *info);
+
 /* Allocation-free transform, for callers that cannot allocate device memory
  * (their memory is owned by another allocator, or they must avoid the device
  * synchronization that allocation and release can cause, or their footprint

@@ -9,5 +9,5 @@ synthetic workloads.
 from .native import (  # noqa: F401
     FORWARD, INVERSE, ROUNDTRIP, NORM_ORTHO, NORM_NONE,
     PATH_AUTO, PATH_FP32, PATH_SPLIT_TC, PATH_SPLIT_HILO, PATH_BF16,
-    BdctError, Plan, lib,
+    BdctError, Plan, Ragged, lib,
 )

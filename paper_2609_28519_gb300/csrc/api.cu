@@ -12,6 +12,7 @@
 #include <new>
 
 #include "bdct_internal.h"
+#include "plan.h"
 
 using namespace bdct;
 
@@ -30,29 +31,6 @@ int cuda_fail(cudaError_t e)
 constexpr size_t kChunkBytes = 64ull << 20;
 
 }  // namespace
-
-struct bdct_plan {
-    int rows = 0, cols = 0;
-    unsigned kind = 0;
-    int norm = 0;
-    int path = 0;
-    int variant = 0;  // 1 fused register tile, 2 separable passes, 3 tensor core
-    bool lines = false;  // separable passes through the FFT line engine (else dense GEMM passes)
-    int device = -1;
-    DirScales scales[3];  // per Dir
-    // separable route
-    float *ops = nullptr;  // [dir][axis] operator matrices, see op_ptr()
-    size_t op_h_off[3] = {0, 0, 0}, op_w_off[3] = {0, 0, 0};
-    float *work = nullptr;
-    size_t work_bytes = 0;
-    long long chunk_arrays = 0;
-    size_t table_bytes = 0;
-    unsigned int *status = nullptr;  // device status word written by bounded waits
-    // tensor-core route: per direction, the operator term tables
-    __nv_bfloat16 *tc_ops = nullptr;
-    size_t tc_off[3] = {0, 0, 0};
-    int tc_terms = 3;
-};
 
 static AxisScale axis_scale(int n, Dir dir, int norm)
 {
@@ -257,24 +235,29 @@ static bool ranges_partially_overlap(const void *a, const void *b, size_t bytes)
     return x < y + bytes && y < x + bytes;
 }
 
-static int run_lines(const bdct_plan *p, Dir dir, const float *in, float *out, long long count, cudaStream_t s)
+static int run_lines(const bdct_plan *p, Dir dir, const float *in, const long long *in_off, float *out,
+                     const long long *out_off, long long count, cudaStream_t s)
 {
     const int h = p->rows, w = p->cols;
     const long long hw = (long long)h * w;
     for (long long b0 = 0; b0 < count; b0 += p->chunk_arrays) {
         const long long nb = (count - b0) < p->chunk_arrays ? (count - b0) : p->chunk_arrays;
+        const float *src = in_off ? in : in + b0 * hw;
+        float *dst = out_off ? out : out + b0 * hw;
         // rows of X (h lines of w) -> workspace (w x h), then rows of that (w lines of h) -> out (h x w)
-        cudaError_t e = lines_pass(in + b0 * hw, p->work, h, w, nb, dir, p->scales[dir].w, p->status, s);
-        if (e == cudaSuccess) e = lines_pass(p->work, out + b0 * hw, w, h, nb, dir, p->scales[dir].h, p->status, s);
+        cudaError_t e = lines_pass(src, p->work, h, w, nb, dir, p->scales[dir].w, p->status, s,
+                                   in_off ? in_off + b0 : nullptr, nullptr);
+        if (e == cudaSuccess)
+            e = lines_pass(p->work, dst, w, h, nb, dir, p->scales[dir].h, p->status, s, nullptr,
+                           out_off ? out_off + b0 : nullptr);
         if (e != cudaSuccess) return cuda_fail(e);
     }
     return BDCT_OK;
 }
 
-static int run_separable(const bdct_plan *p, Dir dir, const float *in, float *out, long long count,
-                         cudaStream_t s)
+static int run_separable(const bdct_plan *p, Dir dir, const float *in, const long long *in_off, float *out,
+                         const long long *out_off, long long count, cudaStream_t s)
 {
-    if (p->lines) return run_lines(p, dir, in, out, count, s);
     const int h = p->rows, w = p->cols;
     const long long hw = (long long)h * w;
     const float *oph = p->ops + p->op_h_off[dir];
@@ -286,21 +269,48 @@ static int run_separable(const bdct_plan *p, Dir dir, const float *in, float *ou
         const long long nb = (count - b0) < p->chunk_arrays ? (count - b0) : p->chunk_arrays;
         const float *src = in + b0 * hw;
         float *dst = out + b0 * hw;
+        const long long *ioff = in_off ? in_off + b0 : nullptr;
+        const long long *ooff = out_off ? out_off + b0 : nullptr;
         cudaError_t e;
+        // first pass: rows of the input into w1
+        if (ioff) e = dense_pass_rows_indexed(in, ioff, w1, opw, h, w, nb, s);
+        else e = dense_pass_rows(src, w1, opw, (int)(nb * h), w, s);
         if (dir != DIR_RT) {
-            e = dense_pass_rows(src, w1, opw, (int)(nb * h), w, s);
-            if (e == cudaSuccess) e = dense_pass_cols(w1, dst, oph, h, w, nb, s);
+            if (e == cudaSuccess) {
+                if (ooff) e = dense_pass_cols_indexed(w1, out, ooff, oph, h, w, nb, s);
+                else e = dense_pass_cols(w1, dst, oph, h, w, nb, s);
+            }
         } else {
             // forward core, then the adjoint core (orthonormal pair)
             const float *ioph = oph + per_dir, *iopw = opw + per_dir;
-            e = dense_pass_rows(src, w1, opw, (int)(nb * h), w, s);
             if (e == cudaSuccess) e = dense_pass_cols(w1, w2, oph, h, w, nb, s);
             if (e == cudaSuccess) e = dense_pass_cols(w2, w1, ioph, h, w, nb, s);
-            if (e == cudaSuccess) e = dense_pass_rows(w1, dst, iopw, (int)(nb * h), w, s);
+            if (e == cudaSuccess) {
+                if (ooff) e = dense_pass_rows_out_indexed(w1, out, ooff, iopw, h, w, nb, s);
+                else e = dense_pass_rows(w1, dst, iopw, (int)(nb * h), w, s);
+            }
         }
         if (e != cudaSuccess) return cuda_fail(e);
     }
     return BDCT_OK;
+}
+
+int bdct::plan_execute(const bdct_plan *p, Dir dir, const float *in, const long long *in_off, float *out,
+                       const long long *out_off, long long count, cudaStream_t s)
+{
+    if (count <= 0) return BDCT_OK;
+    if (p->variant == 1) {
+        ExecGeom g{in, out, count, 0, 0, 0, 0, in_off, out_off};
+        cudaError_t e = fused_launch(p->rows, p->cols, dir, p->scales[dir], g, p->status, s);
+        return e == cudaSuccess ? BDCT_OK : cuda_fail(e);
+    }
+    if (p->variant == 3) {
+        ExecGeom g{in, out, count, 0, 0, 0, 0, in_off, out_off};
+        cudaError_t e = tc_launch(p->rows, dir, p->tc_terms, g, p->tc_ops + p->tc_off[dir], p->status, s);
+        return e == cudaSuccess ? BDCT_OK : cuda_fail(e);
+    }
+    if (p->lines) return run_lines(p, dir, in, in_off, out, out_off, count, s);
+    return run_separable(p, dir, in, in_off, out, out_off, count, s);
 }
 
 extern "C" int bdct_execute(const bdct_plan *plan, unsigned kind, const float *in, float *out,
@@ -317,18 +327,7 @@ extern "C" int bdct_execute(const bdct_plan *plan, unsigned kind, const float *i
     const size_t hw = (size_t)plan->rows * plan->cols;
     if (batch > (size_t)INT64_MAX / (hw * sizeof(float))) return BDCT_ERR_INVALID_ARG;
     if (ranges_partially_overlap(in, out, batch * hw * sizeof(float))) return BDCT_ERR_ALIAS;
-    cudaStream_t s = (cudaStream_t)stream;
-    if (plan->variant == 1) {
-        ExecGeom g{in, out, (long long)batch, 0, 0, 0, 0};
-        cudaError_t e = fused_launch(plan->rows, plan->cols, dir, plan->scales[dir], g, plan->status, s);
-        return e == cudaSuccess ? BDCT_OK : cuda_fail(e);
-    }
-    if (plan->variant == 3) {
-        ExecGeom g{in, out, (long long)batch, 0, 0, 0, 0};
-        cudaError_t e = tc_launch(plan->rows, dir, plan->tc_terms, g, plan->tc_ops + plan->tc_off[dir], plan->status, s);
-        return e == cudaSuccess ? BDCT_OK : cuda_fail(e);
-    }
-    return run_separable(plan, dir, in, out, (long long)batch, s);
+    return plan_execute(plan, dir, in, nullptr, out, nullptr, (long long)batch, (cudaStream_t)stream);
 }
 
 extern "C" int bdct_forward(const bdct_plan *plan, const float *in, float *out, size_t batch, void *stream)

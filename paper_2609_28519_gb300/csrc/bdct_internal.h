@@ -34,6 +34,9 @@ struct ExecGeom {
     int tiled;              // 0: contiguous batch, 1: tiles of an image
     int tiles_per_row;      // tiled: img_cols / cols
     long long ld_in, ld_out;  // tiled: leading dimensions in floats
+    // indexed batch (ragged classes): array a starts at in + in_off[a] and
+    // out + out_off[a] (device arrays of element offsets); null = contiguous
+    const long long *in_off = nullptr, *out_off = nullptr;
 };
 
 enum Dir { DIR_FWD = 0, DIR_INV = 1, DIR_RT = 2 };
@@ -68,7 +71,8 @@ bool lines_supported(int n);
 // result is written transposed: dst[b][k][r] = row r's output k, arrays of
 // n x rows.  Two such passes give the 2D transform in natural layout.
 cudaError_t lines_pass(const float *src, float *dst, int rows, int n, long long count, Dir dir,
-                       AxisScale sc, unsigned int *status, cudaStream_t stream);
+                       AxisScale sc, unsigned int *status, cudaStream_t stream,
+                       const long long *src_off = nullptr, const long long *dst_off = nullptr);
 
 // ---- tc_split.cu
 // Split-BF16 tcgen05 route for square sides 16, 32, 64.
@@ -92,5 +96,12 @@ cudaError_t dense_pass_rows(const float *in, float *out, const float *op_w, int 
                             cudaStream_t stream);
 cudaError_t dense_pass_cols(const float *in, float *out, const float *op_h, int h, int w,
                             long long count, cudaStream_t stream);
+// Indexed variants: array b of the batch at base + off[b] (element offsets).
+cudaError_t dense_pass_rows_indexed(const float *in, const long long *in_off, float *out, const float *op_w, int h,
+                                    int w, long long count, cudaStream_t stream);
+cudaError_t dense_pass_rows_out_indexed(const float *in, float *out, const long long *out_off, const float *op_w,
+                                        int h, int w, long long count, cudaStream_t stream);
+cudaError_t dense_pass_cols_indexed(const float *in, float *out, const long long *out_off, const float *op_h, int h,
+                                    int w, long long count, cudaStream_t stream);
 
 }  // namespace bdct

@@ -64,6 +64,9 @@ struct GemmArgs {
     const float *B; long long sBb, sBk, sBn;
     float *C; long long sCb, sCm, sCn;
     int M, N, K;
+    // indexed batch: batch element b of A / B / C starts at off[b] (element offsets)
+    const long long *aoff = nullptr, *boff = nullptr, *coff = nullptr;
+    long long b0 = 0;  // index of this launch's first batch element in the offset arrays
 };
 
 __global__ void __launch_bounds__(256) k_gemm_strided(GemmArgs g)
@@ -72,9 +75,9 @@ __global__ void __launch_bounds__(256) k_gemm_strided(GemmArgs g)
     __shared__ float Bs[16][64 + 4];
     const int b = blockIdx.z;
     const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
-    const float *A = g.A + b * g.sAb;
-    const float *B = g.B + b * g.sBb;
-    float *C = g.C + b * g.sCb;
+    const float *A = g.aoff ? g.A + g.aoff[g.b0 + b] : g.A + b * g.sAb;
+    const float *B = g.boff ? g.B + g.boff[g.b0 + b] : g.B + b * g.sBb;
+    float *C = g.coff ? g.C + g.coff[g.b0 + b] : g.C + b * g.sCb;
     const int tid = threadIdx.x;
     const int tm = (tid / 16) * 4, tn = (tid % 16) * 4;
     float acc[4][4] = {};
@@ -89,6 +92,10 @@ __global__ void __launch_bounds__(256) k_gemm_strided(GemmArgs g)
             Bs[bk][bn] = (gk2 < g.K && gn < g.N) ? B[gk2 * g.sBk + gn * g.sBn] : 0.0f;
         }
         __syncthreads();
+        // two-level summation: each K tile of 16 products is summed on its own
+        // and then added to the running total, so the rounding error grows
+        // like 16 + K/16 rather than K for long dot products
+        float part[4][4] = {};
 #pragma unroll
         for (int kk = 0; kk < 16; ++kk) {
             float a[4], bb[4];
@@ -97,8 +104,12 @@ __global__ void __launch_bounds__(256) k_gemm_strided(GemmArgs g)
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], bb[j], acc[i][j]);
+                for (int j = 0; j < 4; ++j) part[i][j] = fmaf(a[i], bb[j], part[i][j]);
         }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] += part[i][j];
         __syncthreads();
     }
 #pragma unroll
@@ -117,9 +128,10 @@ static cudaError_t gemm(const GemmArgs &g, long long batch, cudaStream_t stream)
     for (long long b0 = 0; b0 < batch; b0 += 65535) {
         const long long nb = (batch - b0) < 65535 ? (batch - b0) : 65535;
         GemmArgs s = g;
-        s.A += b0 * g.sAb;
-        s.B += b0 * g.sBb;
-        s.C += b0 * g.sCb;
+        if (g.aoff || g.boff || g.coff) s.b0 = g.b0 + b0;
+        if (!g.aoff) s.A += b0 * g.sAb;
+        if (!g.boff) s.B += b0 * g.sBb;
+        if (!g.coff) s.C += b0 * g.sCb;
         dim3 grid((g.N + 63) / 64, (g.M + 63) / 64, (unsigned)nb);
         if (grid.y > 65535) return cudaErrorInvalidConfiguration;
         k_gemm_strided<<<grid, 256, 0, stream>>>(s);
@@ -150,6 +162,36 @@ cudaError_t dense_pass_cols(const float *in, float *out, const float *op_h, int 
 {
     const long long hw = (long long)h * w;
     GemmArgs g{op_h, 0, h, 1, in, hw, w, 1, out, hw, w, 1, h, w, h};
+    return gemm(g, count, stream);
+}
+
+// Indexed batch: rows pass reads array b at in + in_off[b] and writes the
+// workspace contiguously; the columns pass reads the workspace and writes
+// array b at out + out_off[b].
+cudaError_t dense_pass_rows_indexed(const float *in, const long long *in_off, float *out, const float *op_w, int h,
+                                    int w, long long count, cudaStream_t stream)
+{
+    const long long hw = (long long)h * w;
+    GemmArgs g{in, 0, w, 1, op_w, 0, 1, w, out, hw, w, 1, h, w, w};
+    g.aoff = in_off;
+    return gemm(g, count, stream);
+}
+
+cudaError_t dense_pass_rows_out_indexed(const float *in, float *out, const long long *out_off, const float *op_w, int h,
+                                        int w, long long count, cudaStream_t stream)
+{
+    const long long hw = (long long)h * w;
+    GemmArgs g{in, hw, w, 1, op_w, 0, 1, w, out, 0, w, 1, h, w, w};
+    g.coff = out_off;
+    return gemm(g, count, stream);
+}
+
+cudaError_t dense_pass_cols_indexed(const float *in, float *out, const long long *out_off, const float *op_h, int h,
+                                    int w, long long count, cudaStream_t stream)
+{
+    const long long hw = (long long)h * w;
+    GemmArgs g{op_h, 0, h, 1, in, hw, w, 1, out, 0, w, 1, h, w, h};
+    g.coff = out_off;
     return gemm(g, count, stream);
 }
 

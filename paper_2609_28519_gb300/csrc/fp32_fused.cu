@@ -138,7 +138,18 @@ struct FusedParams {
     int nchunks;          // < 2^31, checked by the host
     DirScales sc;
     unsigned int *status;
+    const long long *in_off, *out_off;  // indexed batch, or null
 };
+
+// Start of array a of the batch (contiguous or indexed).
+__device__ __forceinline__ const float *arr_in(const FusedParams &p, long long a, int hw)
+{
+    return p.in_off ? p.in + p.in_off[a] : p.in + a * hw;
+}
+__device__ __forceinline__ float *arr_out(const FusedParams &p, long long a, int hw)
+{
+    return p.out_off ? p.out + p.out_off[a] : p.out + a * hw;
+}
 
 // Where a chunk lives: arrays [first, first + n) of a contiguous batch, or
 // tiles t0 .. t0 + n - 1 of block row brow of an image.
@@ -180,7 +191,7 @@ __device__ __forceinline__ void issue_fill(const FusedParams &p, const ChunkGeom
     __syncwarp();
     if constexpr (C::LAYOUT == LAY_SLOT) {
         for (int a = lane; a < g.n; a += 32)
-            bulk_load(stage + a * C::P, p.in + (g.first + a) * C::HW, C::HW * 4, bar);
+            bulk_load(stage + a * C::P, arr_in(p, g.first + a, C::HW), C::HW * 4, bar);
     } else if constexpr (C::LAYOUT == LAY_STRIP) {
         for (int r = lane; r < H; r += 32) {
             const float *src = p.in + (g.brow * H + r) * p.ld_in + (long long)g.t0 * W;
@@ -191,7 +202,7 @@ __device__ __forceinline__ void issue_fill(const FusedParams &p, const ChunkGeom
             const int a = q / H, r = q % H;
             const float *src;
             if constexpr (TILED) src = p.in + (g.brow * H + r) * p.ld_in + (long long)(g.t0 + a) * W;
-            else src = p.in + (g.first + a) * C::HW + (long long)r * W;
+            else src = arr_in(p, g.first + a, C::HW) + (long long)r * W;
             bulk_load(stage + a * C::AP + r * C::RP, src, W * 4, bar);
         }
     }
@@ -203,7 +214,7 @@ __device__ __forceinline__ void issue_drain(const FusedParams &p, const ChunkGeo
 {
     using C = FusedCfg<H, W, TILED>;
     if constexpr (C::LAYOUT == LAY_SLOT) {
-        for (int a = lane; a < g.n; a += 32) bulk_store(p.out + (g.first + a) * C::HW, stage + a * C::P, C::HW * 4);
+        for (int a = lane; a < g.n; a += 32) bulk_store(arr_out(p, g.first + a, C::HW), stage + a * C::P, C::HW * 4);
     } else if constexpr (C::LAYOUT == LAY_STRIP) {
         for (int r = lane; r < H; r += 32) {
             float *dst = p.out + (g.brow * H + r) * p.ld_out + (long long)g.t0 * W;
@@ -214,7 +225,7 @@ __device__ __forceinline__ void issue_drain(const FusedParams &p, const ChunkGeo
             const int a = q / H, r = q % H;
             float *dst;
             if constexpr (TILED) dst = p.out + (g.brow * H + r) * p.ld_out + (long long)(g.t0 + a) * W;
-            else dst = p.out + (g.first + a) * C::HW + (long long)r * W;
+            else dst = arr_out(p, g.first + a, C::HW) + (long long)r * W;
             bulk_store(dst, stage + a * C::AP + r * C::RP, W * 4);
         }
     }
@@ -396,6 +407,8 @@ static cudaError_t launch_one(const DirScales &sc, const ExecGeom &g, unsigned i
     p.ld_out = g.ld_out;
     p.sc = sc;
     p.status = status;
+    p.in_off = g.in_off;
+    p.out_off = g.out_off;
     long long nch;
     if (!TILED) {
         nch = (g.count + C::G - 1) / C::G;

@@ -222,6 +222,7 @@ struct LinesParams {
     long long nrows;     // total rows
     int npanels;
     AxisScale sc;        // forward: output scales; inverse: input scales; round trip: E^2
+    const long long *src_off, *dst_off;  // indexed arrays (element offsets), or null
 };
 
 template <int N, int DIR>
@@ -248,11 +249,14 @@ __global__ void __launch_bounds__(LineCfg<N>::THREADS) k_lines(const LinesParams
 
     for (int pn = blockIdx.x; pn < p.npanels; pn += gridDim.x) {
         const long long r0 = (long long)pn * C::PR;  // first global row of the panel
+        const long long b = r0 / p.rows;             // its array (panels never straddle two)
+        const int rr = (int)(r0 - b * p.rows);
+        const float *srcb = p.src_off ? p.src + p.src_off[b] : p.src + b * (long long)N * p.rows;
         // ---- load the panel (rows r0 .. r0+PR-1), coalesced 16-byte reads
         constexpr int V4 = N / 4;
         for (int i = tid; i < C::PR * V4; i += C::THREADS) {
             const int l = i / V4, q = i % V4;
-            const float4 v = __ldg(reinterpret_cast<const float4 *>(p.src + (r0 + l) * N) + q);
+            const float4 v = __ldg(reinterpret_cast<const float4 *>(srcb + (long long)(rr + l) * N) + q);
             float *row = panel + l * C::PP;
             if constexpr (DIR == DIR_INV) {
                 reinterpret_cast<float2 *>(row)[2 * q] = make_float2(v.x, v.y);
@@ -284,9 +288,7 @@ __global__ void __launch_bounds__(LineCfg<N>::THREADS) k_lines(const LinesParams
         }
         __syncthreads();
         // ---- transposed store: dst[b][k][r] with rows r0.. (same array b)
-        const long long b = r0 / p.rows;
-        const int rr = (int)(r0 - b * p.rows);
-        float *dstb = p.dst + b * (long long)N * p.rows;
+        float *dstb = p.dst_off ? p.dst + p.dst_off[b] : p.dst + b * (long long)N * p.rows;
         for (int i = tid; i < C::PR * N; i += C::THREADS) {
             const int k = i / C::PR, l = i % C::PR;
             dstb[(long long)k * p.rows + rr + l] = panel[l * C::PP + k];
@@ -348,12 +350,14 @@ static cudaError_t lines_dir(Dir dir, const LinesParams &p, cudaStream_t s)
 }
 
 cudaError_t lines_pass(const float *src, float *dst, int rows, int n, long long count, Dir dir, AxisScale sc,
-                       unsigned int *status, cudaStream_t stream)
+                       unsigned int *status, cudaStream_t stream, const long long *src_off, const long long *dst_off)
 {
     (void)status;
     LinesParams p{};
     p.src = src;
     p.dst = dst;
+    p.src_off = src_off;
+    p.dst_off = dst_off;
     p.rows = rows;
     p.nrows = (long long)rows * count;
     p.sc = sc;

@@ -1,0 +1,37 @@
+// Internal definition of a plan (shared by the API and the ragged executor).
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "bdct_internal.h"
+
+struct bdct_plan {
+    int rows = 0, cols = 0;
+    unsigned kind = 0;
+    int norm = 0;
+    int path = 0;
+    int variant = 0;  // 1 fused register tile, 2 separable passes, 3 tensor core
+    bool lines = false;  // separable passes through the FFT line engine (else dense GEMM passes)
+    int device = -1;
+    bdct::DirScales scales[3];  // per Dir
+    // separable route
+    float *ops = nullptr;  // dense route: operator matrices, see op_h_off / op_w_off
+    size_t op_h_off[3] = {0, 0, 0}, op_w_off[3] = {0, 0, 0};
+    float *work = nullptr;
+    size_t work_bytes = 0;
+    long long chunk_arrays = 0;
+    size_t table_bytes = 0;
+    unsigned int *status = nullptr;  // device status word written by bounded waits
+    // tensor-core route: per direction, the operator term tables
+    __nv_bfloat16 *tc_ops = nullptr;
+    size_t tc_off[3] = {0, 0, 0};
+    int tc_terms = 3;
+};
+
+namespace bdct {
+// Run one direction of a plan on `count` arrays; with in_off/out_off (device
+// arrays of element offsets) array b lives at in + in_off[b] and out +
+// out_off[b], otherwise the batch is contiguous.  Returns a BDCT status.
+int plan_execute(const bdct_plan *p, Dir dir, const float *in, const long long *in_off, float *out,
+                 const long long *out_off, long long count, cudaStream_t s);
+}  // namespace bdct

@@ -129,6 +129,7 @@ struct TcParams {
     int ntiles;
     const __nv_bfloat16 *ops;  // operator term tables, [op][term][B layout]
     unsigned int *status;
+    const long long *in_off, *out_off;  // indexed batch, or null
 };
 
 // Byte offset of element (r, k) of a K-major operand with K = kdim columns.
@@ -268,7 +269,9 @@ __global__ void __launch_bounds__(128) k_tc_split(const TcParams p)
         // ---- load this thread's input row (zeros for absent arrays)
         if (active) {
             const float *src;
-            if constexpr (!TILED) src = p.in + (first + b_local) * (long long)(N * N) + r_local * N;
+            if constexpr (!TILED)
+                src = (p.in_off ? p.in + p.in_off[first + b_local] : p.in + (first + b_local) * (long long)(N * N)) +
+                      r_local * N;
             else src = p.in + (brow * N + r_local) * p.ld_in + (long long)(t0 + b_local) * N;
 #pragma unroll
             for (int q = 0; q < N / 4; ++q) {
@@ -314,13 +317,17 @@ __global__ void __launch_bounds__(128) k_tc_split(const TcParams p)
 #pragma unroll
                 for (int k = 0; k < N; ++k) {
                     float *dst;
-                    if constexpr (!TILED) dst = p.out + (first + b_local) * (long long)(N * N) + k * N + r_local;
+                    if constexpr (!TILED)
+                        dst = (p.out_off ? p.out + p.out_off[first + b_local]
+                                         : p.out + (first + b_local) * (long long)(N * N)) + k * N + r_local;
                     else dst = p.out + (brow * N + k) * p.ld_out + (long long)(t0 + b_local) * N + r_local;
                     *dst = v[k];
                 }
             } else {
                 float *dst;
-                if constexpr (!TILED) dst = p.out + (first + b_local) * (long long)(N * N) + r_local * N;
+                if constexpr (!TILED)
+                    dst = (p.out_off ? p.out + p.out_off[first + b_local]
+                                     : p.out + (first + b_local) * (long long)(N * N)) + r_local * N;
                 else dst = p.out + (brow * N + r_local) * p.ld_out + (long long)(t0 + b_local) * N;
 #pragma unroll
                 for (int q = 0; q < N / 4; ++q)
@@ -487,6 +494,8 @@ cudaError_t tc_launch(int n, Dir dir, int terms, const ExecGeom &g, const __nv_b
     p.ld_in = g.ld_in;
     p.ld_out = g.ld_out;
     p.status = status;
+    p.in_off = g.in_off;
+    p.out_off = g.out_off;
     const bool tiled = g.tiled != 0;
     switch (n) {
         case 16: return tc_launch_n<16>(dir, terms, p, ops, stream, tiled);

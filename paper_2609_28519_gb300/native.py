@@ -31,7 +31,8 @@ STATUS = {0: "OK", 1: "ERR_INVALID_ARG", 2: "ERR_UNSUPPORTED_SHAPE", 3: "ERR_KIN
 EXPORTS = [
     "bdct_plan_create", "bdct_plan_destroy", "bdct_forward", "bdct_inverse", "bdct_roundtrip",
     "bdct_execute", "bdct_execute_tiled", "bdct_plan_get_info", "bdct_plan_device_status",
-    "bdct_execute_noalloc", "bdct_selftest_wait_timeout", "bdct_status_string",
+    "bdct_ragged_create", "bdct_ragged_execute", "bdct_ragged_destroy", "bdct_ragged_num_classes",
+    "bdct_ragged_class_info", "bdct_execute_noalloc", "bdct_selftest_wait_timeout", "bdct_status_string",
     "bdct_last_cuda_error", "bdct_version",
 ]
 
@@ -51,6 +52,11 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [("rows", ctypes.c_int), ("cols", ctypes.c_int), ("kind", ctypes.c_uint),
                 ("norm", ctypes.c_int), ("path", ctypes.c_int), ("variant", ctypes.c_int),
                 ("workspace_bytes", ctypes.c_size_t), ("table_bytes", ctypes.c_size_t)]
+
+
+class RaggedClass(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int), ("cols", ctypes.c_int), ("count", ctypes.c_size_t),
+                ("path", ctypes.c_int), ("variant", ctypes.c_int), ("tuned_us_per_array", ctypes.c_double)]
 
 
 _lib = None
@@ -77,6 +83,11 @@ def lib() -> ctypes.CDLL:
             L.bdct_plan_device_status.argtypes = [vp, ci]
             L.bdct_selftest_wait_timeout.argtypes = [cu]
             L.bdct_execute_noalloc.argtypes = [ci, ci, cu, ci, vp, vp, sz, vp]
+            L.bdct_ragged_create.argtypes = [ctypes.POINTER(vp), sz, vp, vp, vp, vp, cu, ci, ci]
+            L.bdct_ragged_execute.argtypes = [vp, cu, vp, vp, vp]
+            L.bdct_ragged_destroy.argtypes = [vp]
+            L.bdct_ragged_num_classes.argtypes = [vp]
+            L.bdct_ragged_class_info.argtypes = [vp, ci, ctypes.POINTER(RaggedClass)]
             L.bdct_status_string.argtypes = [ci]
             L.bdct_status_string.restype = ctypes.c_char_p
             L.bdct_last_cuda_error.restype = ci
@@ -189,3 +200,67 @@ class Plan:
                                         img.stride(0), out.stride(0), _stream_of(img, stream)),
                "bdct_execute_tiled")
         return out
+
+
+class Ragged:
+    """A ragged batch of mixed shapes (``bdct_ragged_create``).
+
+    ``shapes`` is a list of (rows, cols); arrays are packed back to back in
+    that order (element offsets rounded up to multiples of 4) unless explicit
+    ``in_off`` / ``out_off`` lists are given.
+    """
+
+    def __init__(self, shapes, kind=FORWARD | INVERSE | ROUNDTRIP, norm="ortho", path="auto",
+                 in_off=None, out_off=None):
+        import numpy as np
+        L = lib()
+        self.shapes = [(int(r), int(c)) for r, c in shapes]
+        n = len(self.shapes)
+        rows = np.array([r for r, _ in self.shapes], dtype=np.int32)
+        cols = np.array([c for _, c in self.shapes], dtype=np.int32)
+        if in_off is None:
+            sizes = rows.astype(np.int64) * cols
+            padded = (sizes + 3) // 4 * 4
+            in_off = np.concatenate([[0], np.cumsum(padded)[:-1]]).astype(np.uint64)
+            self.total = int(np.sum(padded))
+        else:
+            in_off = np.asarray(in_off, dtype=np.uint64)
+            self.total = int(max(int(o) + r * c for o, (r, c) in zip(in_off, self.shapes))) if n else 0
+        out_off = in_off.copy() if out_off is None else np.asarray(out_off, dtype=np.uint64)
+        self.in_off, self.out_off = in_off, out_off
+        norm = NORMS[norm] if isinstance(norm, str) else int(norm)
+        path = PATHS[path] if isinstance(path, str) else int(path)
+        h = ctypes.c_void_p()
+        _check(L.bdct_ragged_create(ctypes.byref(h), n, rows.ctypes.data, cols.ctypes.data,
+                                    in_off.ctypes.data, out_off.ctypes.data, int(kind), norm, path),
+               "bdct_ragged_create")
+        self._h = h
+
+    def classes(self):
+        L = lib()
+        out = []
+        for i in range(L.bdct_ragged_num_classes(self._h)):
+            c = RaggedClass()
+            _check(L.bdct_ragged_class_info(self._h, i, ctypes.byref(c)), "bdct_ragged_class_info")
+            out.append({"rows": c.rows, "cols": c.cols, "count": c.count, "path": c.path,
+                        "variant": c.variant, "tuned_us_per_array": c.tuned_us_per_array})
+        return out
+
+    def execute(self, kind, x, out, stream=None):
+        """x, out: flat CUDA float32 tensors holding the packed arrays."""
+        kind = KINDS[kind] if isinstance(kind, str) else int(kind)
+        _check(lib().bdct_ragged_execute(self._h, kind, ctypes.c_void_p(x.data_ptr()),
+                                         ctypes.c_void_p(out.data_ptr()), _stream_of(x, stream)),
+               "bdct_ragged_execute")
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.bdct_ragged_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

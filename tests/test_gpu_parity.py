@@ -305,3 +305,83 @@ def test_auto_path_choice(cuda_dev):
     assert Plan(16, 16).info().variant == 1
     assert Plan(128, 128).info().variant == 2
     assert Plan(64, 64, path="split_tc").info().variant == 3
+
+
+# ------------------------------------------------------------ ragged batches
+def _ragged_inputs(shapes, seed):
+    import numpy as np
+    arrs = [inputs.uniform(seed + i, 1, r, c)[0] for i, (r, c) in enumerate(shapes)]
+    return arrs
+
+
+def _pack(rg, arrs, dev):
+    import torch
+    flat = torch.zeros(rg.total, dtype=torch.float32)
+    for a, off in zip(arrs, rg.in_off):
+        flat[int(off):int(off) + a.size] = torch.from_numpy(a.ravel())
+    return flat.to(dev)
+
+
+def _unpack(rg, flat, shapes):
+    f = flat.cpu().numpy()
+    return [f[int(o):int(o) + r * c].reshape(r, c) for o, (r, c) in zip(rg.out_off, shapes)]
+
+
+def test_ragged_mixed_shapes_against_oracle(oracle_mod, cuda_dev):
+    """Mixed squares and rectangles in one ragged execution: every array
+    against the oracle; ragged output bit-equal to per-array plan calls on the
+    same path; graph replay equal to the captured first call."""
+    import torch
+    from paper_2609_28519_gb300 import Plan, Ragged
+    rng = np.random.default_rng(44)
+    base = [(8, 8), (16, 16), (32, 32), (64, 64), (128, 128), (256, 256), (64, 256), (128, 512), (16, 8),
+            (32, 16), (24, 40)]
+    shapes = [base[int(i)] for i in rng.integers(0, len(base), size=40)] + [(768, 1024)]
+    arrs = _ragged_inputs(shapes, 500)
+    rg = Ragged(shapes)
+    classes = rg.classes()
+    assert sum(c["count"] for c in classes) == len(shapes)
+    x = _pack(rg, arrs, cuda_dev)
+    for kind in ("forward", "inverse", "roundtrip"):
+        y = torch.full_like(x, float("nan"))
+        rg.execute(kind, x, y)
+        torch.cuda.synchronize()
+        first = y.clone()
+        rg.execute(kind, x, y)  # graph replay
+        torch.cuda.synchronize()
+        assert torch.equal(first, y)
+        outs = _unpack(rg, y, shapes)
+        for a, o, (r, c) in zip(arrs, outs, shapes):
+            ref = _ref(oracle_mod, kind, a[None], 0)[0]
+            _assert_parity(oracle_mod, o[None], ref[None], a[None], 0, kind, ("ragged", r, c, kind))
+        # the same path through a per-array plan gives the same bits
+        by_shape = {(c["rows"], c["cols"]): c["path"] for c in classes}
+        for i in (0, len(shapes) - 1):
+            r, c = shapes[i]
+            pl = Plan(r, c, path={1: "fp32", 2: "split_tc"}[by_shape[(r, c)]])
+            single = pl.execute(kind, torch.from_numpy(arrs[i][None]).to(cuda_dev))
+            torch.cuda.synchronize()
+            assert np.array_equal(single.cpu().numpy()[0], outs[i])
+
+
+def test_ragged_full_workload_sampled(oracle_mod, cuda_dev):
+    """4096 arrays drawn by seed from the nine shapes (~1.6 GiB), forward and
+    inverse in one graph launch each; sampled arrays against the oracle."""
+    import torch
+    from paper_2609_28519_gb300 import Ragged
+    shapes = inputs.ragged_shapes(4, 4096)
+    rg = Ragged(shapes, kind=1 | 2)
+    x = torch.empty(rg.total, dtype=torch.float32, device=cuda_dev)
+    x.uniform_(-1.0, 1.0, generator=torch.Generator(device=cuda_dev).manual_seed(4))
+    y = torch.empty_like(x)
+    rng = np.random.default_rng(4)
+    pick = rng.choice(len(shapes), 10, replace=False)
+    for kind in ("forward", "inverse"):
+        rg.execute(kind, x, y)
+        torch.cuda.synchronize()
+        for i in pick:
+            r, c = shapes[i]
+            o = int(rg.in_off[i])
+            a = x[o:o + r * c].view(1, r, c).cpu().numpy()
+            got = y[o:o + r * c].view(1, r, c).cpu().numpy()
+            _assert_parity(oracle_mod, got, _ref(oracle_mod, kind, a, 0), a, 0, kind, ("ragged-full", r, c, kind))
