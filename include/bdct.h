@@ -118,6 +118,30 @@ int bdct_execute(const bdct_plan *plan, unsigned kind, const float *in, float *o
 int bdct_execute_tiled(const bdct_plan *plan, unsigned kind, const float *in, float *out,
                        int img_rows, int img_cols, size_t ld_in, size_t ld_out, void *stream);
 
+/* ------------------------------------------------------ host-buffer execution
+ * End-to-end calls on HOST buffers (pinned memory gives overlap; pageable
+ * memory works but each copy then blocks the host).  The paper times complete
+ * calls including input copies (Sections 4.1-4.2) and names streaming
+ * workloads with data transfers as future work (Section 8).
+ * bdct_plan_set_host_staging allocates the plan's device staging (two slots
+ * of two chunk_bytes buffers, rounded down to whole arrays, at least one) and
+ * three private streams; call it once before the host entry points.
+ * bdct_execute_host moves `batch` contiguous arrays from h_in through the
+ * device and back to h_out in chunks: the host-to-device copy of one chunk,
+ * the transforms of the previous chunk and the device-to-host copy of the one
+ * before overlap.  kinds[0..nkinds-1] (1..8 directions, each planned) are
+ * applied in order to every chunk on the device, so an intermediate spectrum
+ * never crosses the host link.  bdct_execute_tiled_host does the same for an
+ * img_rows x img_cols host image (leading dimension img_cols) in bands of
+ * whole block rows, through the tiled view.  Both are asynchronous on
+ * `stream`: the host buffers must stay valid until the stream reaches the
+ * end of the call; calls on one plan must not overlap.                      */
+int bdct_plan_set_host_staging(bdct_plan *plan, size_t chunk_bytes);
+int bdct_execute_host(const bdct_plan *plan, const unsigned *kinds, int nkinds, const float *h_in,
+                      float *h_out, size_t batch, void *stream);
+int bdct_execute_tiled_host(const bdct_plan *plan, const unsigned *kinds, int nkinds, const float *h_in,
+                            float *h_out, int img_rows, int img_cols, void *stream);
+
 typedef struct bdct_plan_info {
     int rows, cols;
     unsigned kind;

@@ -68,6 +68,7 @@ static void plan_free(bdct_plan *p)
     if (p->ops) cudaFree(p->ops);
     if (p->status) cudaFree(p->status);
     if (p->tc_ops) cudaFree(p->tc_ops);
+    host_staging_free(p);
     if (p->work) cudaFree(p->work);
     delete p;
 }

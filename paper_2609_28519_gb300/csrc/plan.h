@@ -26,9 +26,19 @@ struct bdct_plan {
     __nv_bfloat16 *tc_ops = nullptr;
     size_t tc_off[3] = {0, 0, 0};
     int tc_terms = 3;
+    // host-buffer execution (bdct_plan_set_host_staging): two slots of two
+    // device buffers, and streams/events of the copy-in / transform /
+    // copy-out pipeline
+    float *stage[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    size_t stage_bytes = 0;
+    cudaStream_t copy_stream = nullptr, comp_stream = nullptr, d2h_stream = nullptr;
+    cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
+    cudaEvent_t ev_start = nullptr, ev_end = nullptr;
 };
 
 namespace bdct {
+// Release the host-staging buffers, streams and events of a plan.
+void host_staging_free(bdct_plan *p);
 // Run one direction of a plan on `count` arrays; with in_off/out_off (device
 // arrays of element offsets) array b lives at in + in_off[b] and out +
 // out_off[b], otherwise the batch is contiguous.  Returns a BDCT status.

@@ -30,7 +30,8 @@ STATUS = {0: "OK", 1: "ERR_INVALID_ARG", 2: "ERR_UNSUPPORTED_SHAPE", 3: "ERR_KIN
 # every symbol the header declares, in declaration order
 EXPORTS = [
     "bdct_plan_create", "bdct_plan_destroy", "bdct_forward", "bdct_inverse", "bdct_roundtrip",
-    "bdct_execute", "bdct_execute_tiled", "bdct_plan_get_info", "bdct_plan_device_status",
+    "bdct_execute", "bdct_execute_tiled", "bdct_plan_set_host_staging", "bdct_execute_host",
+    "bdct_execute_tiled_host", "bdct_plan_get_info", "bdct_plan_device_status",
     "bdct_ragged_create", "bdct_ragged_execute", "bdct_ragged_destroy", "bdct_ragged_num_classes",
     "bdct_ragged_class_info", "bdct_execute_noalloc", "bdct_selftest_wait_timeout", "bdct_status_string",
     "bdct_last_cuda_error", "bdct_version",
@@ -80,6 +81,9 @@ def lib() -> ctypes.CDLL:
             L.bdct_execute.argtypes = [vp, cu, vp, vp, sz, vp]
             L.bdct_execute_tiled.argtypes = [vp, cu, vp, vp, ci, ci, sz, sz, vp]
             L.bdct_plan_get_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
+            L.bdct_plan_set_host_staging.argtypes = [vp, sz]
+            L.bdct_execute_host.argtypes = [vp, vp, ci, vp, vp, sz, vp]
+            L.bdct_execute_tiled_host.argtypes = [vp, vp, ci, vp, vp, ci, ci, vp]
             L.bdct_plan_device_status.argtypes = [vp, ci]
             L.bdct_selftest_wait_timeout.argtypes = [cu]
             L.bdct_execute_noalloc.argtypes = [ci, ci, cu, ci, vp, vp, sz, vp]
@@ -186,6 +190,37 @@ class Plan:
 
     def roundtrip(self, x, out=None, stream=None):
         return self.execute(ROUNDTRIP, x, out, stream)
+
+    def set_host_staging(self, chunk_bytes: int = 8 << 20) -> None:
+        _check(lib().bdct_plan_set_host_staging(self.handle, int(chunk_bytes)), "bdct_plan_set_host_staging")
+
+    @staticmethod
+    def _kinds(kinds):
+        ks = [KINDS[k] if isinstance(k, str) else int(k) for k in kinds]
+        return (ctypes.c_uint * len(ks))(*ks), len(ks)
+
+    def execute_host(self, kinds, h_in, h_out, stream=None):
+        """Host (CPU, ideally pinned) float32 tensors in and out; the directions
+        in `kinds` are applied in order on the device (bdct_execute_host)."""
+        import torch
+        arr, n = self._kinds(kinds)
+        b = h_in.numel() // (self.rows * self.cols)
+        s = torch.cuda.current_stream() if stream is None else stream
+        _check(lib().bdct_execute_host(self.handle, arr, n, ctypes.c_void_p(h_in.data_ptr()),
+                                       ctypes.c_void_p(h_out.data_ptr()), b, ctypes.c_void_p(s.cuda_stream)),
+               "bdct_execute_host")
+        return h_out
+
+    def execute_tiled_host(self, kinds, h_img, h_out, stream=None):
+        """Host image in and out through the tiled view (bdct_execute_tiled_host)."""
+        import torch
+        arr, n = self._kinds(kinds)
+        s = torch.cuda.current_stream() if stream is None else stream
+        _check(lib().bdct_execute_tiled_host(self.handle, arr, n, ctypes.c_void_p(h_img.data_ptr()),
+                                             ctypes.c_void_p(h_out.data_ptr()), h_img.shape[0], h_img.shape[1],
+                                             ctypes.c_void_p(s.cuda_stream)),
+               "bdct_execute_tiled_host")
+        return h_out
 
     def execute_tiled(self, kind: int, img, out=None, stream=None):
         """Transform every rows x cols block of a 2D image (``bdct_execute_tiled``)."""

@@ -385,3 +385,36 @@ def test_ragged_full_workload_sampled(oracle_mod, cuda_dev):
             a = x[o:o + r * c].view(1, r, c).cpu().numpy()
             got = y[o:o + r * c].view(1, r, c).cpu().numpy()
             _assert_parity(oracle_mod, got, _ref(oracle_mod, kind, a, 0), a, 0, kind, ("ragged-full", r, c, kind))
+
+
+# ------------------------------------------------------------ host-buffer execution
+def test_host_buffers_tiled_and_batch(oracle_mod, cuda_dev):
+    """bdct_execute_tiled_host / bdct_execute_host: host in, directions applied
+    on the device in order, host out; equal to the device-buffer calls."""
+    import torch
+    from paper_2609_28519_gb300 import Plan
+    img = inputs.ramp_image(2, 1024, 2048)
+    plan = Plan(16, 16)
+    plan.set_host_staging(1 << 20)  # several chunks, so the pipeline overlaps and wraps
+    h_in = torch.from_numpy(img).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    plan.execute_tiled_host(["forward"], h_in, h_out)
+    torch.cuda.synchronize()
+    d = torch.from_numpy(img).to(cuda_dev)
+    ref = plan.execute_tiled("forward", d)
+    torch.cuda.synchronize()
+    assert np.array_equal(h_out.numpy(), ref.cpu().numpy())
+    plan.execute_tiled_host(["forward", "inverse"], h_in, h_out)
+    torch.cuda.synchronize()
+    blocks = inputs.image_to_blocks(img, 16, 16)
+    back = inputs.image_to_blocks(h_out.numpy(), 16, 16)
+    _assert_parity(oracle_mod, back, blocks.astype(np.float64), blocks, 0, "roundtrip", "host-f-then-i")
+    # contiguous batch, several chunks and a ragged tail
+    x = inputs.uniform(77, 1000, 32, 32)
+    p32 = Plan(32, 32)
+    p32.set_host_staging(64 * 32 * 32 * 4)
+    hx = torch.from_numpy(x).pin_memory()
+    hy = torch.empty_like(hx).pin_memory()
+    p32.execute_host(["forward"], hx, hy)
+    torch.cuda.synchronize()
+    _assert_parity(oracle_mod, hy.numpy(), oracle_mod.forward(x, 0), x, 0, "forward", "host-batch")
