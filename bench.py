@@ -428,7 +428,7 @@ def run_sweep(args):
     peak, _ = _peaks()
     sizes = [int(v) for v in args.sizes.split(",")]
     for n in sizes:
-        batch = (512 << 20) // (4 * n * n)
+        batch = max(1, (args.mib << 20) // (4 * n * n))
         x = torch.empty((batch, n, n), dtype=torch.float32, device=dev).uniform_(-1, 1)
         y = torch.empty_like(x)
         plan = Plan(n, n, path=args.path)
@@ -454,6 +454,88 @@ def run_sweep(args):
     return 0
 
 
+def _time_graph(fn, stream, reps):
+    import torch
+    g = torch.cuda.CUDAGraph()
+    cs = torch.cuda.Stream()
+    cs.wait_stream(stream)
+    with torch.cuda.graph(g, stream=cs):
+        for _ in range(reps):
+            fn(cs)
+    torch.cuda.synchronize()
+    g.replay()
+    torch.cuda.synchronize()
+    return replay_ms(g, stream) / reps
+
+
+def run_ragged(args):
+    """Ragged batch: 4096 arrays drawn by seed from nine shapes (~1.6 GiB),
+    forward and inverse through one ragged plan (graph of per-class launches).
+    One JSON line per direction, 8 B per element per call; not the headline."""
+    import torch
+    from paper_2609_28519_gb300 import Ragged, inputs
+    dev = torch.device("cuda", 0)
+    peak, _ = _peaks()
+    shapes = inputs.ragged_shapes(4, 4096)
+    t0 = time.perf_counter()
+    rg = Ragged(shapes, kind=1 | 2, path=args.path if args.path in ("auto", "fp32", "split_tc") else "auto")
+    create_s = time.perf_counter() - t0
+    x = torch.empty(rg.total, dtype=torch.float32, device=dev).uniform_(-1, 1)
+    y = torch.empty_like(x)
+    elems = sum(r * c for r, c in shapes)
+    stream = torch.cuda.current_stream(dev)
+    for kind in ("forward", "inverse"):
+        for _ in range(2):
+            rg.execute(kind, x, y)
+        torch.cuda.synchronize()
+        # each execute is already one CUDA graph launch
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        a.record(stream)
+        for _ in range(reps):
+            rg.execute(kind, x, y, stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        gbs = elems * 8 / (ms * 1e-3) / 1e9
+        print(json.dumps({"workload": "ragged 4096 arrays (seed 4)", "kind": kind, "elements": elems,
+                          "ms": ms, "GB/s": gbs, "frac_of_measured_hbm": gbs / peak,
+                          "plan_create_s": create_s, "classes": rg.classes()}), flush=True)
+    return 0
+
+
+def run_large(args):
+    """Large whole arrays: 16 x 1024^2, 4 x 4096^2, 1 x 1024x768 (N(0,1)),
+    forward + inverse per shape group; one JSON line per group and direction."""
+    import torch
+    from paper_2609_28519_gb300 import Plan
+    dev = torch.device("cuda", 0)
+    peak, _ = _peaks()
+    stream = torch.cuda.current_stream(dev)
+    for (h, w, b) in [(1024, 1024, 16), (4096, 4096, 4), (1024, 768, 1)]:
+        x = torch.randn(b, h, w, device=dev)
+        y = torch.empty_like(x)
+        for path in ("fp32", "split_tc"):
+            try:
+                plan = Plan(h, w, kind=1 | 2, path=path)
+            except Exception as e:
+                print(json.dumps({"workload": f"{b} x {h}x{w}", "path": path, "unavailable": str(e)}), flush=True)
+                continue
+            for kind in ("forward", "inverse"):
+                plan.execute(kind, x, y)
+                torch.cuda.synchronize()
+                reps = 3 if h * w >= 4096 * 4096 else 10
+                ms = _time_graph(lambda cs: plan.execute(kind, x, y, cs), stream, reps)
+                gbs = b * h * w * 8 / (ms * 1e-3) / 1e9
+                print(json.dumps({"workload": f"{b} x {h}x{w}", "path": path, "variant": plan.info().variant,
+                                  "kind": kind, "ms": ms, "GB/s": gbs, "frac_of_measured_hbm": gbs / peak}),
+                      flush=True)
+            plan.close()
+        del x, y
+        torch.cuda.empty_cache()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -466,6 +548,8 @@ def main():
     ap.add_argument("--no-paths", action="store_true", help="skip the per-path comparison")
     ap.add_argument("--sweep", action="store_true", help="square-size sweep instead of the headline")
     ap.add_argument("--sizes", default="8,16,32,64,128,256")
+    ap.add_argument("--mib", type=int, default=512, help="input MiB per sweep run")
+    ap.add_argument("--workload", default="image", choices=["image", "ragged", "large"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -473,6 +557,10 @@ def main():
         return run_reference(args)
     if args.sweep:
         return run_sweep(args)
+    if args.workload == "ragged":
+        return run_ragged(args)
+    if args.workload == "large":
+        return run_large(args)
     return run_ours(args)
 
 

@@ -68,6 +68,7 @@ static void plan_free(bdct_plan *p)
     if (p->ops) cudaFree(p->ops);
     if (p->status) cudaFree(p->status);
     if (p->tc_ops) cudaFree(p->tc_ops);
+    if (p->line_tw) cudaFree(p->line_tw);
     host_staging_free(p);
     if (p->work) cudaFree(p->work);
     delete p;
@@ -159,6 +160,13 @@ extern "C" int bdct_plan_create(bdct_plan **plan, int rows, int cols, unsigned k
         p->work_bytes = (size_t)chunk * arr_bytes;
         e = cudaMalloc(&p->work, p->work_bytes);
         if (e != cudaSuccess) { plan_free(p); t_last_cuda_error = (int)e; return BDCT_ERR_NO_MEMORY; }
+        p->line_tw_h = (size_t)cols + 1;
+        e = cudaMalloc(&p->line_tw, ((size_t)cols + 1 + (size_t)rows + 1) * sizeof(float2));
+        if (e != cudaSuccess) { plan_free(p); t_last_cuda_error = (int)e; return BDCT_ERR_NO_MEMORY; }
+        e = lines_gen_table(p->line_tw, cols, 0);
+        if (e == cudaSuccess) e = lines_gen_table(p->line_tw + p->line_tw_h, rows, 0);
+        if (e != cudaSuccess) { plan_free(p); return cuda_fail(e); }
+        p->table_bytes = ((size_t)cols + 1 + (size_t)rows + 1) * sizeof(float2);
     } else {
         p->variant = 2;
         // operator matrices: forward and inverse in the plan's norm, and the
@@ -246,11 +254,11 @@ static int run_lines(const bdct_plan *p, Dir dir, const float *in, const long lo
         const float *src = in_off ? in : in + b0 * hw;
         float *dst = out_off ? out : out + b0 * hw;
         // rows of X (h lines of w) -> workspace (w x h), then rows of that (w lines of h) -> out (h x w)
-        cudaError_t e = lines_pass(src, p->work, h, w, nb, dir, p->scales[dir].w, p->status, s,
+        cudaError_t e = lines_pass(src, p->work, h, w, nb, dir, p->scales[dir].w, p->line_tw, p->status, s,
                                    in_off ? in_off + b0 : nullptr, nullptr);
         if (e == cudaSuccess)
-            e = lines_pass(p->work, dst, w, h, nb, dir, p->scales[dir].h, p->status, s, nullptr,
-                           out_off ? out_off + b0 : nullptr);
+            e = lines_pass(p->work, dst, w, h, nb, dir, p->scales[dir].h, p->line_tw + p->line_tw_h, p->status, s,
+                           nullptr, out_off ? out_off + b0 : nullptr);
         if (e != cudaSuccess) return cuda_fail(e);
     }
     return BDCT_OK;

@@ -63,15 +63,19 @@ cudaError_t fused_launch(int rows, int cols, Dir dir, const DirScales &sc, const
 // Copy the cosine table (device buffer, 4097 floats) into the line engine's
 // constant memory (called by fused_init_device).
 cudaError_t lines_init_table(const float *d_table);
-// True if n has an FFT-based line engine (powers of two 64..4096).
+cudaError_t lines_init_table3(const float *d_table);
+// True if n has an FFT-based line engine (powers of two 64..4096, and 768).
 bool lines_supported(int n);
+// The line engine's twiddle table for length n: exp(-i pi r / (2n)), r = 0..n,
+// generated in FP64 (n + 1 float2 entries).
+cudaError_t lines_gen_table(float2 *dst, int n, cudaStream_t s);
 // One separable pass over `count` arrays of rows x n: every row (length n)
 // gets the 1D transform of `dir` with per-index scales `sc` (forward: output
 // scale, inverse: input scale, round trip: the E^2 correction), and the
 // result is written transposed: dst[b][k][r] = row r's output k, arrays of
 // n x rows.  Two such passes give the 2D transform in natural layout.
 cudaError_t lines_pass(const float *src, float *dst, int rows, int n, long long count, Dir dir,
-                       AxisScale sc, unsigned int *status, cudaStream_t stream,
+                       AxisScale sc, const float2 *tw, unsigned int *status, cudaStream_t stream,
                        const long long *src_off = nullptr, const long long *dst_off = nullptr);
 
 // ---- tc_split.cu

@@ -52,10 +52,67 @@ __device__ __forceinline__ void rot(float ar, float ai, int m, int d, float &rr,
 
 // ------------------------------------------------------------ 1D cores
 // Forward complex DFT X_k = sum_j x_j exp(-2 pi i j k / L), radix-2 DIT.
+// Twiddles for lengths with a factor 3: c_cos3[r] = cos(pi r / 1536),
+// r = 0..768 (one copy per translation unit, filled by init_cos_table3).
+static __constant__ float c_cos3[769];
+
+// cos(pi m / d) for d dividing 1536 * 2 (lengths 3 * 2^k <= 3072).
+__device__ __forceinline__ float cospi3_md(int m, int d)
+{
+    int r = (m * (1536 / d)) % 3072;
+    if (r < 0) r += 3072;
+    if (r > 1536) r = 3072 - r;
+    if (r == 0) return 1.0f;
+    if (r == 1536) return -1.0f;
+    if (r == 768) return 0.0f;
+    return (r > 768) ? -c_cos3[1536 - r] : c_cos3[r];
+}
+__device__ __forceinline__ float sinpi3_md(int m, int d) { return cospi3_md(d / 2 - m, d); }
+
+// (ar + i ai) * exp(-2 pi i k / L) for L = 3 * 2^j.
+__device__ __forceinline__ void rot3(float ar, float ai, int k, int L, float &rr, float &ri)
+{
+    if (k % L == 0) { rr = ar; ri = ai; return; }
+    const float c = cospi3_md(2 * k, L), s = sinpi3_md(2 * k, L);
+    rr = fmaf(ar, c, ai * s);
+    ri = fmaf(ai, c, -(ar * s));
+}
+
 template <int L>
 struct FFT {
     static __device__ __forceinline__ void run(float (&re)[L], float (&im)[L])
     {
+        if constexpr (L % 3 == 0) {
+            // radix-3 decimation in time: three interleaved FFTs of L/3, then a
+            // 3-point DFT of (E0_k, w^k E1_k, w^2k E2_k), w = exp(-2 pi i / L)
+            constexpr int M = L / 3;
+            float r0[M], i0[M], r1[M], i1[M], r2[M], i2[M];
+#pragma unroll
+            for (int j = 0; j < M; ++j) {
+                r0[j] = re[3 * j]; i0[j] = im[3 * j];
+                r1[j] = re[3 * j + 1]; i1[j] = im[3 * j + 1];
+                r2[j] = re[3 * j + 2]; i2[j] = im[3 * j + 2];
+            }
+            FFT<M>::run(r0, i0);
+            FFT<M>::run(r1, i1);
+            FFT<M>::run(r2, i2);
+            const float h = cospi3_md(256, 1536);  // cos(pi / 6) = sqrt(3) / 2
+#pragma unroll
+            for (int k = 0; k < M; ++k) {
+                float br, bi, cr, ci;
+                rot3(r1[k], i1[k], k, L, br, bi);
+                rot3(r2[k], i2[k], 2 * k, L, cr, ci);
+                const float tr = br + cr, ti = bi + ci;      // b + c
+                const float dr = br - cr, di = bi - ci;      // b - c
+                const float mr = r0[k] - 0.5f * tr, mi = i0[k] - 0.5f * ti;
+                // -i sqrt(3)/2 (b - c)
+                const float sr = h * di, si = -h * dr;
+                re[k] = r0[k] + tr; im[k] = i0[k] + ti;
+                re[k + M] = mr + sr; im[k + M] = mi + si;
+                re[k + 2 * M] = mr - sr; im[k + 2 * M] = mi - si;
+            }
+            return;
+        }
         float er[L / 2], ei[L / 2], orr[L / 2], oi[L / 2];
 #pragma unroll
         for (int j = 0; j < L / 2; ++j) {
@@ -67,7 +124,7 @@ struct FFT {
 #pragma unroll
         for (int k = 0; k < L / 2; ++k) {
             float tr, ti;
-            rot(orr[k], oi[k], 2 * k, L, tr, ti);  // exp(-2 pi i k / L)
+            rot(orr[k], oi[k], 2 * k, L, tr, ti);  // exp(-2 pi i k / L), L a power of two
             re[k] = er[k] + tr; im[k] = ei[k] + ti;
             re[k + L / 2] = er[k] - tr; im[k + L / 2] = ei[k] - ti;
         }
@@ -189,6 +246,12 @@ __device__ __forceinline__ void line_op(float (&x)[N], AxisScale s)
 static inline cudaError_t init_cos_table(const float *d_table)
 {
     return cudaMemcpyToSymbol(c_cos, d_table, 4097 * sizeof(float), 0, cudaMemcpyDeviceToDevice);
+}
+
+// Same for the radix-3 table: a device buffer holding cos(pi r / 1536), r = 0..768.
+static inline cudaError_t init_cos_table3(const float *d_table)
+{
+    return cudaMemcpyToSymbol(c_cos3, d_table, 769 * sizeof(float), 0, cudaMemcpyDeviceToDevice);
 }
 
 }  // namespace bdct

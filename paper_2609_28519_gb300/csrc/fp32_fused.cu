@@ -350,6 +350,14 @@ __global__ void k_gen_cos_table(float *t)
     t[r] = (r == 4096) ? 0.0f : (float)cospi((double)r / 8192.0);
 }
 
+__global__ void k_gen_cos_table3(float *t)
+{
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r > 768) return;
+    // cos(pi r / 1536) in FP64; exact 0 at r = 768
+    t[r] = (r == 768) ? 0.0f : (float)cospi((double)r / 1536.0);
+}
+
 static bool g_table_ready[64];
 
 cudaError_t fused_init_device(int device)
@@ -363,6 +371,12 @@ cudaError_t fused_init_device(int device)
     e = cudaGetLastError();
     if (e == cudaSuccess) e = init_cos_table(tmp);
     if (e == cudaSuccess) e = lines_init_table(tmp);
+    if (e == cudaSuccess) {
+        k_gen_cos_table3<<<(769 + 255) / 256, 256>>>(tmp);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = init_cos_table3(tmp);
+    if (e == cudaSuccess) e = lines_init_table3(tmp);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     cudaFree(tmp);
     if (e == cudaSuccess) g_table_ready[device] = true;

@@ -1,5 +1,5 @@
 // FFT-based FP32 line engine: one separable pass of the 2D DCT for long
-// power-of-two lines (64 .. 2048 points).
+// lines (64 .. 4096 points, powers of two, and 768 = 2 * 3 * 2^7).
 //
 // What is computed: the 1D factor of Eq. 2 of the BRiDCT paper along every
 // row of a batch of arrays -- y_k = s_k sum_j x_j cos(pi (2j+1) k / (2N))
@@ -17,9 +17,9 @@
 //   O_k = (Z_k - conj Z_{L-k}) / (2i), V_k = E_k + exp(-2 pi i k / N) O_k:
 //   y_k = Re(exp(-i pi k / (2N)) V_k), y_{N-k} = -Im(exp(-i pi k / (2N)) V_k).
 // The DCT-III runs the same steps backwards (its 1/L folded into a factor 2
-// on y_0).  Sub-FFTs of length <= 32 run in registers (dct_cores.cuh); a warp
-// transforms one to four lines; the FFT stays within FP32 rounding of the
-// exact sums (error grows like log N).
+// on y_0).  Sub-FFTs (radix 2 and 3, up to 64 points) run in registers
+// (dct_cores.cuh); a warp transforms one to four lines; the FFT stays within
+// FP32 rounding of the exact sums (error grows like log N).
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -30,36 +30,56 @@
 namespace bdct {
 
 cudaError_t lines_init_table(const float *d_table) { return init_cos_table(d_table); }
+cudaError_t lines_init_table3(const float *d_table) { return init_cos_table3(d_table); }
 
-bool lines_supported(int n) { return n >= 64 && n <= 2048 && (n & (n - 1)) == 0; }
+bool lines_supported(int n)
+{
+    return n == 64 || n == 128 || n == 256 || n == 512 || n == 1024 || n == 2048 || n == 4096 || n == 768;
+}
 
 template <int N>
 struct LineCfg {
     static constexpr int L = N / 2;
-    // four-step split L = L1 * L2 (both <= 32)
-    static constexpr int L1 = (N == 64) ? 4 : (N == 128) ? 8 : (N == 256) ? 8 : (N == 512) ? 16 : (N == 1024) ? 16 : 32;
+    // four-step split L = L1 * L2 (step A: FFTs of L1, step C: FFTs of L2)
+    static constexpr int L1 = (N == 64) ? 4 : (N == 128) ? 8 : (N == 256) ? 8 : (N == 512) ? 16 : (N == 1024) ? 16
+                            : (N == 768) ? 12 : 32;
     static constexpr int L2 = L / L1;
-    static constexpr int TPL = L1 > L2 ? L1 : L2;  // threads per line
-    static constexpr int LPW = 32 / TPL;          // lines per warp at once
-    static constexpr int NW = 8;                   // warps per CTA
+    static constexpr int TPL_RAW = L1 > L2 ? L1 : L2;
+    static constexpr int TPL = TPL_RAW > 32 ? 32 : TPL_RAW;  // threads per line
+    static constexpr int LPW = 32 / TPL;                     // lines per warp at once
+    static constexpr int NW = N >= 4096 ? 4 : 8;             // warps per CTA
     static constexpr int THREADS = 32 * NW;
-    static constexpr int PR = N <= 512 ? 32 : (N == 1024 ? 16 : 8);  // rows per panel
-    static constexpr int PP = N + 2 * L1 + 2;      // panel row pitch (floats): room for A, even
-    static constexpr int SCR = N;                  // per-line scratch (floats)
+    static constexpr int PR = N <= 512 ? 32 : (N <= 1024 ? 16 : (N == 2048 ? 8 : 4));  // rows per panel
+    static constexpr int PP = N + 2 * L1 + 2;                // panel row pitch (floats)
+    static constexpr int A_FLOATS = 2 * L1 * (L2 + 1);       // step-A output, padded
+    static constexpr int SCR = A_FLOATS > N ? A_FLOATS : N;  // per-line scratch (floats)
     static constexpr int ROUNDS = PR / (NW * LPW);
-    static constexpr size_t SMEM = (size_t)PR * PP * 4 + (size_t)NW * LPW * SCR * 4 + (size_t)(2 * N + 1) * 8;
-    static_assert(L1 * L2 == L && L1 <= 32 && L2 <= 32, "split");
+    static constexpr int DELTA = 16 / LPW;                   // row distance of a warp's lines
+    static constexpr int SEG = PR < 16 ? PR : 16;            // rows per transposed-store segment
+    static constexpr int PAIRS = (L / 2 + 1 + TPL - 1) / TPL;  // split tasks per lane
+    static constexpr int TWN = N + 1;                        // quarter-wave twiddles
+    static constexpr size_t SMEM = (size_t)PR * PP * 4 + (size_t)NW * LPW * SCR * 4 + (size_t)TWN * 8;
+    static_assert(L1 * L2 == L && L1 <= 32, "split");
     static_assert(ROUNDS >= 1 && ROUNDS * NW * LPW == PR, "panel");
+    static_assert(LPW == 1 || PR % 16 == 0, "line groups");
+    static_assert((PP % 4) == 2, "row pitch 2 mod 4 floats");
 };
 
-// exp(-i pi r / (2N)) for r in [0, 4N), from the quarter table tw[0..2N].
+// exp(-i pi r / (2N)) for any r, from the quarter table tw[0..N] (angles 0..pi/2).
 template <int N>
 __device__ __forceinline__ float2 twq(const float2 *tw, int r)
 {
-    r &= 4 * N - 1;
-    if (r <= 2 * N) return tw[r];
-    const float2 t = tw[4 * N - r];
-    return make_float2(t.x, -t.y);
+    r %= 4 * N;
+    if (r < 0) r += 4 * N;
+    bool conj = false;
+    if (r > 2 * N) { r = 4 * N - r; conj = true; }  // exp(-i(2pi - a)) = conj(exp(-i a))
+    float2 v;
+    if (r <= N) v = tw[r];
+    else {  // a = pi/2 + b: exp(-i a) = -i exp(-i b)
+        const float2 t = tw[r - N];
+        v = make_float2(t.y, -t.x);
+    }
+    return conj ? make_float2(v.x, -v.y) : v;
 }
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b)
@@ -69,37 +89,33 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b)
 
 __device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
 
-// Step A of the four-step FFT for task m2: z[L2*m1 + m2] (m1 < L1) from `src`
-// (float2 array, natural order), FFT_L1, twiddle, result written to A[k1][m2]
-// (pitch L2 + 1) of `dst` after `sync_before_write`.  conj_in conjugates the
-// inputs (inverse transform through the conjugate trick).
-template <int N, bool CONJ_IN>
-__device__ __forceinline__ void step_a(const float2 *src, float2 *dst, const float2 *tw, int m2, bool active,
-                                       bool sync_before_write)
+// Step A of the four-step FFT: for every task m2 of this lane, the FFT of
+// length L1 of src[L2*m1 + m2] (m1 < L1), times exp(-2 pi i m2 k1 / L),
+// written to A[k1][m2] of dst (pitch L2 + 1).  src and dst are distinct.
+template <int N>
+__device__ __forceinline__ void step_a(const float2 *src, float2 *dst, const float2 *tw, int t)
 {
     using C = LineCfg<N>;
-    float re[C::L1], im[C::L1];
-    if (active) {
+#pragma unroll 1
+    for (int m2 = t; m2 < C::L2; m2 += C::TPL) {
+        float re[C::L1], im[C::L1];
 #pragma unroll
         for (int m1 = 0; m1 < C::L1; ++m1) {
             const float2 v = src[C::L2 * m1 + m2];
             re[m1] = v.x;
-            im[m1] = CONJ_IN ? -v.y : v.y;
+            im[m1] = v.y;
         }
         FFT<C::L1>::run(re, im);
-    }
-    if (sync_before_write) __syncwarp();
-    if (active) {
 #pragma unroll
         for (int k1 = 0; k1 < C::L1; ++k1) {
             // exp(-2 pi i m2 k1 / L) = exp(-i pi (8 m2 k1) / (2N))
-            const float2 t = k1 == 0 ? make_float2(1.f, 0.f) : twq<N>(tw, 8 * m2 * k1);
-            dst[k1 * (C::L2 + 1) + m2] = cmul(make_float2(re[k1], im[k1]), t);
+            const float2 t1 = k1 == 0 ? make_float2(1.f, 0.f) : twq<N>(tw, 8 * m2 * k1);
+            dst[k1 * (C::L2 + 1) + m2] = cmul(make_float2(re[k1], im[k1]), t1);
         }
     }
 }
 
-// Step C for task k1: FFT_L2 of A[k1][*]; returns Z_{k1 + L1 k2} in re/im.
+// Step C for task k1: FFT of length L2 of A[k1][*]; Z_{k1 + L1 k2} in re/im.
 template <int N>
 __device__ __forceinline__ void step_c(const float2 *A, int k1, float (&re)[LineCfg<N>::L2], float (&im)[LineCfg<N>::L2])
 {
@@ -113,43 +129,54 @@ __device__ __forceinline__ void step_c(const float2 *A, int k1, float (&re)[Line
     FFT<C::L2>::run(re, im);
 }
 
-// Forward DCT-II of one line.  On entry `line` holds v (Makhoul order) as
-// float2 z; on exit it holds y_k * s_k in natural order.  `scr` holds N floats.
+// Forward DCT-II of one line.  On entry `line` holds z (Makhoul order, as
+// float2); on exit y_k * s_k in natural order.
 template <int N>
 __device__ __forceinline__ void line_forward(float *line, float *scr, const float2 *tw, int t, AxisScale s)
 {
     using C = LineCfg<N>;
     float2 *z = reinterpret_cast<float2 *>(line);
-    float2 *Z = reinterpret_cast<float2 *>(scr);
-    // step A: z (line) -> A (line, padded); all reads before any write
-    step_a<N, false>(z, z, tw, t, t < C::L2, true);
+    float2 *A = reinterpret_cast<float2 *>(scr);
+    step_a<N>(z, A, tw, t);  // line -> scratch
     __syncwarp();
-    // step C: A (line) -> Z (scratch, natural order)
-    if (t < C::L1) {
+    if (t < C::L1) {  // scratch -> Z (line, natural order)
         float re[C::L2], im[C::L2];
-        step_c<N>(z, t, re, im);
+        step_c<N>(A, t, re, im);
 #pragma unroll
-        for (int k2 = 0; k2 < C::L2; ++k2) Z[t + C::L1 * k2] = make_float2(re[k2], im[k2]);
+        for (int k2 = 0; k2 < C::L2; ++k2) z[t + C::L1 * k2] = make_float2(re[k2], im[k2]);
     }
     __syncwarp();
-    // split: Z (scratch) -> y (line)
-    for (int k = t; k <= C::L / 2; k += C::TPL) {
+    // split: every lane reads its pairs (Z_k, Z_{L-k}) first, then writes y over them
+    float2 za[C::PAIRS], zb[C::PAIRS];
+#pragma unroll
+    for (int q = 0; q < C::PAIRS; ++q) {
+        const int k = t + q * C::TPL;
+        if (k <= C::L / 2) {
+            za[q] = z[k];
+            zb[q] = z[k == 0 ? 0 : C::L - k];
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < C::PAIRS; ++q) {
+        const int k = t + q * C::TPL;
+        if (k > C::L / 2) continue;
         if (k == 0) {
-            const float2 z0 = Z[0];
+            const float2 z0 = za[q];
             line[0] = (z0.x + z0.y) * s.s0;
             line[C::L] = (z0.x - z0.y) * 0.70710678118654752f * s.s1;
             continue;
         }
-        const float2 a = Z[k], c = Z[C::L - k];
+        const float2 a = za[q], c = zb[q];
         const float2 E = make_float2(0.5f * (a.x + c.x), 0.5f * (a.y - c.y));
         const float2 O = make_float2(0.5f * (a.y + c.y), 0.5f * (c.x - a.x));
-        const float2 P = cmul(twq<N>(tw, 4 * k), O);                         // exp(-2 pi i k / N) O_k
-        const float2 V = make_float2(E.x + P.x, E.y + P.y);                 // V_k
-        const float2 WV = cmul(twq<N>(tw, k), V);                           // exp(-i pi k / (2N)) V_k
+        const float2 P = cmul(twq<N>(tw, 4 * k), O);  // exp(-2 pi i k / N) O_k
+        const float2 V = make_float2(E.x + P.x, E.y + P.y);
+        const float2 WV = cmul(twq<N>(tw, k), V);      // exp(-i pi k / (2N)) V_k
         line[k] = WV.x * s.s1;
         line[N - k] = -WV.y * s.s1;
         if (k != C::L - k) {
-            const float2 V2 = make_float2(E.x - P.x, -(E.y - P.y));          // V_{L-k} = conj(E - P)
+            const float2 V2 = make_float2(E.x - P.x, -(E.y - P.y));  // V_{L-k} = conj(E - P)
             const float2 WV2 = cmul(twq<N>(tw, C::L - k), V2);
             line[C::L - k] = WV2.x * s.s1;
             line[C::L + k] = -WV2.y * s.s1;
@@ -168,7 +195,7 @@ __device__ __forceinline__ void line_inverse(float *line, float *scr, const floa
     // y -> conj(Z) (scratch)
     for (int k = t; k <= C::L / 2; k += C::TPL) {
         if (k == 0) {
-            const float v0 = 2.0f * line[0] * s.s0;                  // factor 2 carries 1/L
+            const float v0 = 2.0f * line[0] * s.s0;  // factor 2 carries 1/L
             const float vl = 1.41421356237309505f * line[C::L] * s.s1;
             const float E0 = 0.5f * (v0 + vl), O0 = 0.5f * (v0 - vl);
             Zc[0] = make_float2(E0, -O0);  // Z_0 = E0 + i O0
@@ -193,7 +220,7 @@ __device__ __forceinline__ void line_inverse(float *line, float *scr, const floa
     __syncwarp();
     // forward four-step FFT of conj(Z): step A scratch -> line (padded)
     float2 *A = reinterpret_cast<float2 *>(line);
-    step_a<N, false>(Zc, A, tw, t, t < C::L2, false);
+    step_a<N>(Zc, A, tw, t);
     __syncwarp();
     // step C: conj of the result is z = IFFT(Z) (unnormalized); then v from z, x from v
     float re[C::L2], im[C::L2];
@@ -223,6 +250,7 @@ struct LinesParams {
     int npanels;
     AxisScale sc;        // forward: output scales; inverse: input scales; round trip: E^2
     const long long *src_off, *dst_off;  // indexed arrays (element offsets), or null
+    const float2 *tw;    // exp(-i pi r / (2N)), r = 0..N, generated in FP64 at plan time
 };
 
 template <int N, int DIR>
@@ -238,13 +266,8 @@ __global__ void __launch_bounds__(LineCfg<N>::THREADS) k_lines(const LinesParams
 
     pdl_launch_dependents();
     pdl_wait_prerequisites();
-    // quarter-wave twiddles exp(-i pi r / (2N)), r = 0 .. 2N, from the cosine table
-    for (int r = tid; r <= 2 * N; r += C::THREADS) {
-        const int idx = r * (4096 / N);  // angle pi r / (2N) = pi idx / 8192, idx in [0, 8192]
-        const float c = idx <= 4096 ? c_cos[idx] : -c_cos[8192 - idx];
-        const int sidx = idx <= 4096 ? 4096 - idx : idx - 4096;  // sin = cos(pi/2 - angle) >= 0
-        tw[r] = make_float2(c, -c_cos[sidx]);
-    }
+    // quarter-wave twiddles exp(-i pi r / (2N)), r = 0 .. N, from the plan's table
+    for (int r = tid; r < C::TWN; r += C::THREADS) tw[r] = p.tw[r];
     __syncthreads();
 
     for (int pn = blockIdx.x; pn < p.npanels; pn += gridDim.x) {
@@ -272,7 +295,11 @@ __global__ void __launch_bounds__(LineCfg<N>::THREADS) k_lines(const LinesParams
         // ---- transform every line of the panel
 #pragma unroll 1
         for (int rd = 0; rd < C::ROUNDS; ++rd) {
-            const int l = (rd * C::NW + warp) * C::LPW + sub;
+            // The LPW lines a warp transforms together sit DELTA = 16 / LPW rows
+            // apart: with a row pitch of 2 mod 4 floats their shared-memory
+            // accesses then fall into disjoint banks.
+            const int grp = rd * C::NW + warp;
+            const int l = (C::LPW == 1) ? grp : (grp / C::DELTA) * 16 + (grp % C::DELTA) + sub * C::DELTA;
             float *line = panel + l * C::PP;
             float *scr = scr_all + (warp * C::LPW + sub) * C::SCR;
             if constexpr (DIR == DIR_FWD) {
@@ -289,9 +316,12 @@ __global__ void __launch_bounds__(LineCfg<N>::THREADS) k_lines(const LinesParams
         __syncthreads();
         // ---- transposed store: dst[b][k][r] with rows r0.. (same array b)
         float *dstb = p.dst_off ? p.dst + p.dst_off[b] : p.dst + b * (long long)N * p.rows;
+        // a warp instruction covers SEG rows x (32 / SEG) columns; with a row
+        // pitch of 2 mod 4 floats, 16 rows x 2 columns touch all 32 banks
         for (int i = tid; i < C::PR * N; i += C::THREADS) {
-            const int k = i / C::PR, l = i % C::PR;
-            dstb[(long long)k * p.rows + rr + l] = panel[l * C::PP + k];
+            const int l = i % C::SEG, cj = i / C::SEG;
+            const int k = cj % N, lb = (cj / N) * C::SEG;
+            dstb[(long long)k * p.rows + rr + lb + l] = panel[(lb + l) * C::PP + k];
         }
         __syncthreads();
     }
@@ -320,6 +350,7 @@ static cudaError_t lines_launch(const LinesParams &p0, cudaStream_t stream)
                     blocks_per_sm[dev], C::THREADS, C::PR, C::SMEM);
     }
     LinesParams p = p0;
+    if (p.rows % C::PR != 0) return cudaErrorInvalidValue;  // panels never straddle two arrays
     const long long np = p.nrows / C::PR;
     if (np <= 0) return cudaSuccess;
     if (np > 0x7ff00000LL) return cudaErrorInvalidValue;
@@ -349,19 +380,36 @@ static cudaError_t lines_dir(Dir dir, const LinesParams &p, cudaStream_t s)
     }
 }
 
+__global__ void k_gen_line_tw(float2 *t, int n)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r > n) return;
+    // angle pi r / (2n) in [0, pi/2], evaluated in FP64
+    const double a = (double)r / (2.0 * (double)n);
+    t[r] = make_float2((float)cospi(a), (float)(r == n ? -1.0 : -sinpi(a)));
+    if (r == n) t[r].x = 0.0f;
+}
+
+cudaError_t lines_gen_table(float2 *dst, int n, cudaStream_t s)
+{
+    k_gen_line_tw<<<(n + 1 + 255) / 256, 256, 0, s>>>(dst, n);
+    return cudaGetLastError();
+}
+
 cudaError_t lines_pass(const float *src, float *dst, int rows, int n, long long count, Dir dir, AxisScale sc,
-                       unsigned int *status, cudaStream_t stream, const long long *src_off, const long long *dst_off)
+                       const float2 *tw, unsigned int *status, cudaStream_t stream, const long long *src_off,
+                       const long long *dst_off)
 {
     (void)status;
     LinesParams p{};
     p.src = src;
     p.dst = dst;
+    p.tw = tw;
     p.src_off = src_off;
     p.dst_off = dst_off;
     p.rows = rows;
     p.nrows = (long long)rows * count;
     p.sc = sc;
-    if (rows % 32 != 0) return cudaErrorInvalidValue;  // panels never straddle two arrays
     switch (n) {
         case 64: return lines_dir<64>(dir, p, stream);
         case 128: return lines_dir<128>(dir, p, stream);
@@ -369,6 +417,8 @@ cudaError_t lines_pass(const float *src, float *dst, int rows, int n, long long 
         case 512: return lines_dir<512>(dir, p, stream);
         case 1024: return lines_dir<1024>(dir, p, stream);
         case 2048: return lines_dir<2048>(dir, p, stream);
+        case 4096: return lines_dir<4096>(dir, p, stream);
+        case 768: return lines_dir<768>(dir, p, stream);
         default: return cudaErrorInvalidValue;
     }
 }

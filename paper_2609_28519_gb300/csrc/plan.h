@@ -12,6 +12,8 @@ struct bdct_plan {
     int path = 0;
     int variant = 0;  // 1 fused register tile, 2 separable passes, 3 tensor core
     bool lines = false;  // separable passes through the FFT line engine (else dense GEMM passes)
+    float2 *line_tw = nullptr;        // line engine twiddles: w axis at 0, h axis at line_tw_h
+    size_t line_tw_h = 0;
     int device = -1;
     bdct::DirScales scales[3];  // per Dir
     // separable route

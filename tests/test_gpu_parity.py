@@ -418,3 +418,46 @@ def test_host_buffers_tiled_and_batch(oracle_mod, cuda_dev):
     p32.execute_host(["forward"], hx, hy)
     torch.cuda.synchronize()
     _assert_parity(oracle_mod, hy.numpy(), oracle_mod.forward(x, 0), x, 0, "forward", "host-batch")
+
+
+# ------------------------------------------------------------ large whole arrays
+@pytest.mark.parametrize("h,w", [(1024, 768), (768, 1024), (768, 768)])
+def test_large_non_power_of_two_against_oracle(oracle_mod, cuda_dev, h, w):
+    """768-point lines (radix-3 FFT stage) against the full oracle."""
+    from paper_2609_28519_gb300 import Plan
+    plan = Plan(h, w)
+    assert plan.info().variant == 2
+    x = inputs.gaussian(6000 + h + w, 1, h, w)
+    for kind in KINDS:
+        y = _run(plan, kind, x, cuda_dev)
+        _assert_parity(oracle_mod, y, _ref(oracle_mod, kind, x, 0), x, 0, kind, (h, w, kind))
+
+
+@pytest.mark.parametrize("n", [2048, 4096])
+def test_large_separable_input_and_invariants(oracle_mod, cuda_dev, n):
+    """4096 x 4096 whole arrays: a separable input X = a b^T must give
+    (Q a)(Q b)^T, with the 1D factors from the oracle; Gaussian inputs must
+    keep their norm (Parseval) and come back from the round trip."""
+    import torch
+    from paper_2609_28519_gb300 import Plan
+    rng = np.random.default_rng(n)
+    a = rng.standard_normal(n).astype(np.float32)
+    b = rng.standard_normal(n).astype(np.float32)
+    ya = oracle_mod.forward(a.reshape(1, 1, n), 0).ravel()
+    yb = oracle_mod.forward(b.reshape(1, 1, n), 0).ravel()
+    x = np.outer(a, b).astype(np.float32)[None]
+    plan = Plan(n, n)
+    y = _run(plan, "forward", x, cuda_dev)
+    # x is the float32 rounding of a b^T: compare against the exact product of its factors
+    ref = np.outer(ya, yb)[None]
+    m = oracle_mod.metrics(y, ref, x)
+    assert m["e_rel_max"] < 2e-6, m["e_rel_max"]  # includes the rounding of x itself
+    g = torch.randn(1, n, n, device=cuda_dev, generator=torch.Generator(device=cuda_dev).manual_seed(n))
+    yf = plan.forward(g)
+    back = plan.inverse(yf)
+    rt = plan.roundtrip(g)
+    torch.cuda.synchronize()
+    gn = torch.linalg.vector_norm(g.double())
+    assert abs(float(torch.linalg.vector_norm(yf.double()) / gn) - 1.0) < 1e-6
+    assert float(torch.linalg.vector_norm((back - g).double()) / gn) < 1e-6
+    assert float(torch.linalg.vector_norm((rt - g).double()) / gn) < 1e-6
