@@ -50,10 +50,16 @@ template <int H, int W, bool TILED>
 struct FusedCfg {
     static constexpr int HW = H * W;
     static constexpr int LAYOUT = W >= 64 ? LAY_ROWPAD : (TILED ? LAY_STRIP : LAY_SLOT);
-    // arrays per chunk
-    static constexpr int G = LAYOUT == LAY_ROWPAD ? (HW >= 8192 ? 1 : 2) : ((HW <= 64) ? 16 : 8);
-    static constexpr int LINES_MIN = G * (H < W ? H : W);
-    static constexpr int NW_MAX = LINES_MIN / 32;
+    // arrays per chunk (image strips of 16-wide tiles take 16 tiles so that
+    // every thread gets a column pair in pass 1)
+    static constexpr int G = LAYOUT == LAY_ROWPAD ? (HW >= 8192 ? 1 : 2)
+                           : ((HW <= 64) ? 16 : (LAYOUT == LAY_STRIP && W == 16 && H <= 16 ? 16 : 8));
+    // pass 1 on two adjacent columns per thread (8-byte loads): strip layout
+    static constexpr bool PAIR1 = LAYOUT == LAY_STRIP && W >= 16;
+    // warps: every thread has at least one line (or column pair) in each pass
+    static constexpr int NW_P1 = G * W / ((W >= 16 && LAYOUT == LAY_STRIP) ? 64 : 32);
+    static constexpr int NW_P2 = G * H / 32;
+    static constexpr int NW_MAX = NW_P1 < NW_P2 ? NW_P1 : NW_P2;
     static constexpr int NW = NW_MAX > 8 ? 8 : NW_MAX;  // warps per CTA
     static constexpr int THREADS = 32 * NW;
     static constexpr int P = HW + 4;       // slot pitch (floats)
@@ -65,10 +71,11 @@ struct FusedCfg {
     static constexpr int STAGE_BYTES = STAGE_FLOATS * 4;
     static constexpr int ST_RAW = (LAYOUT == LAY_ROWPAD ? 72 * 1024 : 32 * 1024) / STAGE_BYTES;
     static constexpr int STAGES = ST_RAW < 2 ? 2 : (ST_RAW > 4 ? 4 : ST_RAW);
-    static constexpr int J1 = G * W / THREADS;  // columns per thread (pass 1)
+    static constexpr int J1 = G * W / (PAIR1 ? 2 * THREADS : THREADS);  // column steps per thread (pass 1)
     static constexpr int J2 = G * H / THREADS;  // rows per thread (pass 2)
     static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + STAGES * 8;
-    static_assert(J1 >= 1 && J2 >= 1 && J1 * THREADS == G * W && J2 * THREADS == G * H, "lane mapping");
+    static_assert(J1 >= 1 && J2 >= 1 && J1 * THREADS * (PAIR1 ? 2 : 1) == G * W && J2 * THREADS == G * H,
+                  "lane mapping");
     static_assert((P % 8) == 4 && (SP % 8) == 4 && (RP % 8) == 4, "pitches must be 4 mod 8 floats");
 };
 
@@ -281,7 +288,30 @@ __global__ void __launch_bounds__(FusedCfg<H, W, TILED>::THREADS) k_fused(const 
         const ChunkGeom g = chunk_geom<H, W, TILED>(p, c);
         const int n = g.n;
 
-        // pass 1: one column per thread per step, 1D core along h
+        // pass 1: one column (or two adjacent columns) per thread per step,
+        // 1D core along h
+        if constexpr (C::PAIR1) {
+#pragma unroll
+            for (int j = 0; j < C::J1; ++j) {
+                const int s2 = 2 * (lane + 32 * (warp + C::NW * j));  // even strip column
+                const int a = s2 / W, col = s2 % W;
+                if (a < n) {
+                    float2 *q = reinterpret_cast<float2 *>(stage + elem<H, W, TILED>(a, 0, col));
+                    constexpr int RS2 = C::SP / 2;
+                    float x0[H], x1[H];
+#pragma unroll
+                    for (int i = 0; i < H; ++i) {
+                        const float2 t = q[i * RS2];
+                        x0[i] = t.x;
+                        x1[i] = t.y;
+                    }
+                    line_op<H, DIR>(x0, p.sc.h);
+                    line_op<H, DIR>(x1, p.sc.h);
+#pragma unroll
+                    for (int i = 0; i < H; ++i) q[i * RS2] = make_float2(x0[i], x1[i]);
+                }
+            }
+        } else
 #pragma unroll
         for (int j = 0; j < C::J1; ++j) {
             int a, col;
