@@ -536,6 +536,36 @@ def run_large(args):
     return 0
 
 
+def run_profile(args):
+    """One plan, one direction, a contiguous batch of --mib MiB, executed
+    --warmup + --steps times back to back: the small fixed case the ncu
+    captures under profiles/ are taken on (not a bench line)."""
+    import torch
+    from paper_2609_28519_gb300 import Plan, inputs
+    h, w = (int(v) for v in args.shape.lower().split("x"))
+    dev = torch.device("cuda:0")
+    batch = max(1, args.mib * 2**20 // (h * w * 4))
+    x = torch.from_numpy(inputs.uniform(3, batch, h, w)).to(dev)
+    y = torch.empty_like(x)
+    plan = Plan(h, w, path=args.path)
+    fn = {"f": plan.forward, "i": plan.inverse, "r": plan.roundtrip}[args.kind]
+    for _ in range(args.warmup):
+        fn(x, out=y)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(args.steps):
+        fn(x, out=y)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / args.steps
+    print(json.dumps({"workload": f"{batch} x {h}x{w}", "kind": args.kind, "path": args.path,
+                      "variant": plan.info().variant, "ms_per_launch": ms,
+                      "GB/s": batch * h * w * 8 / (ms * 1e-3) / 1e9}), flush=True)
+    plan.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -549,7 +579,9 @@ def main():
     ap.add_argument("--sweep", action="store_true", help="square-size sweep instead of the headline")
     ap.add_argument("--sizes", default="8,16,32,64,128,256")
     ap.add_argument("--mib", type=int, default=512, help="input MiB per sweep run")
-    ap.add_argument("--workload", default="image", choices=["image", "ragged", "large"])
+    ap.add_argument("--workload", default="image", choices=["image", "ragged", "large", "profile"])
+    ap.add_argument("--shape", default="64x64", help="profile workload: rows x cols")
+    ap.add_argument("--kind", default="f", choices=["f", "i", "r"], help="profile workload: direction")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -561,6 +593,8 @@ def main():
         return run_ragged(args)
     if args.workload == "large":
         return run_large(args)
+    if args.workload == "profile":
+        return run_profile(args)
     return run_ours(args)
 
 
