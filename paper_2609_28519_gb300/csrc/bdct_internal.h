@@ -59,6 +59,14 @@ bool fused_supported(int rows, int cols);
 cudaError_t fused_launch(int rows, int cols, Dir dir, const DirScales &sc, const ExecGeom &g,
                          unsigned int *status, cudaStream_t stream);
 
+// ---- fp32_ring.cu
+// Warp-specialized ring kernels for sides 64 and 128 (all four combinations):
+// contiguous, indexed and tiled batches.
+cudaError_t ring_init_table(const float *d_table);
+bool ring_supported(int rows, int cols);
+cudaError_t ring_launch(int rows, int cols, Dir dir, const DirScales &sc, const ExecGeom &g,
+                        unsigned int *status, cudaStream_t stream);
+
 // ---- fp32_lines.cu
 // Copy the cosine table (device buffer, 4097 floats) into the line engine's
 // constant memory (called by fused_init_device).

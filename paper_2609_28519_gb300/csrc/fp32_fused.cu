@@ -1,4 +1,6 @@
-// FP32 fused 2D DCT kernels for small power-of-two sides (8, 16, 32).
+// FP32 fused 2D DCT kernels for small power-of-two sides (8, 16, 32, in
+// every combination); sides 64 and 128 go to the ring kernels of
+// fp32_ring.cu through the same entry points.
 //
 // What is computed: Eq. 2 of the BRiDCT paper, C(X) = Q_h X Q_w^T (forward,
 // DCT-II), C^{-1}(Y) = Q_h^T Y Q_w (inverse, DCT-III) and the round trip,
@@ -44,16 +46,15 @@ namespace bdct {
 //    take 32 adjacent strip columns, pass 2 lanes take 8 rows of one tile,
 //    which the odd 16-byte row pitch spreads over all banks.
 // Shared-memory layouts of a stage (see the comment above).
-enum Layout { LAY_SLOT = 0, LAY_STRIP = 1, LAY_ROWPAD = 2 };
+enum Layout { LAY_SLOT = 0, LAY_STRIP = 1 };
 
 template <int H, int W, bool TILED>
 struct FusedCfg {
     static constexpr int HW = H * W;
-    static constexpr int LAYOUT = W >= 64 ? LAY_ROWPAD : (TILED ? LAY_STRIP : LAY_SLOT);
+    static constexpr int LAYOUT = TILED ? LAY_STRIP : LAY_SLOT;
     // arrays per chunk (image strips of 16-wide tiles take 16 tiles so that
     // every thread gets a column pair in pass 1)
-    static constexpr int G = LAYOUT == LAY_ROWPAD ? (HW >= 8192 ? 1 : 2)
-                           : ((HW <= 64) ? 16 : (LAYOUT == LAY_STRIP && W == 16 && H <= 16 ? 16 : 8));
+    static constexpr int G = (HW <= 64) ? 16 : (LAYOUT == LAY_STRIP && W == 16 && H <= 16 ? 16 : 8);
     // pass 1 on two adjacent columns per thread (8-byte loads): strip layout
     static constexpr bool PAIR1 = LAYOUT == LAY_STRIP && W >= 16;
     // warps: every thread has at least one line (or column pair) in each pass
@@ -64,19 +65,18 @@ struct FusedCfg {
     static constexpr int THREADS = 32 * NW;
     static constexpr int P = HW + 4;       // slot pitch (floats)
     static constexpr int SP = G * W + 4;   // strip row pitch (floats)
-    static constexpr int RP = W + 4;       // padded row pitch (floats)
-    static constexpr int AP = H * RP;      // padded array pitch (floats)
     static constexpr int STAGE_FLOATS =
-        LAYOUT == LAY_ROWPAD ? G * AP : (LAYOUT == LAY_STRIP ? H * SP : G * P);
+        LAYOUT == LAY_STRIP ? H * SP : G * P;
     static constexpr int STAGE_BYTES = STAGE_FLOATS * 4;
-    static constexpr int ST_RAW = (LAYOUT == LAY_ROWPAD ? 72 * 1024 : 32 * 1024) / STAGE_BYTES;
+    static constexpr int ST_RAW = (32 * 1024) / STAGE_BYTES;
     static constexpr int STAGES = ST_RAW < 2 ? 2 : (ST_RAW > 4 ? 4 : ST_RAW);
     static constexpr int J1 = G * W / (PAIR1 ? 2 * THREADS : THREADS);  // column steps per thread (pass 1)
     static constexpr int J2 = G * H / THREADS;  // rows per thread (pass 2)
     static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + STAGES * 8;
     static_assert(J1 >= 1 && J2 >= 1 && J1 * THREADS * (PAIR1 ? 2 : 1) == G * W && J2 * THREADS == G * H,
                   "lane mapping");
-    static_assert((P % 8) == 4 && (SP % 8) == 4 && (RP % 8) == 4, "pitches must be 4 mod 8 floats");
+    static_assert((P % 8) == 4 && (SP % 8) == 4, "pitches must be 4 mod 8 floats");
+    static_assert(H <= 32 && W <= 32, "sides 64 and 128 use the ring kernels");
 };
 
 // Element (a, r, c) of a stage: array/tile a, row r, column c.
@@ -84,8 +84,7 @@ template <int H, int W, bool TILED>
 __device__ __forceinline__ int elem(int a, int r, int c)
 {
     using C = FusedCfg<H, W, TILED>;
-    if constexpr (C::LAYOUT == LAY_ROWPAD) return a * C::AP + r * C::RP + c;
-    else if constexpr (C::LAYOUT == LAY_STRIP) return r * C::SP + a * W + c;
+    if constexpr (C::LAYOUT == LAY_STRIP) return r * C::SP + a * W + c;
     else return a * C::P + r * W + c;
 }
 
@@ -94,7 +93,7 @@ template <int H, int W, bool TILED>
 __device__ __forceinline__ constexpr int row_stride()
 {
     using C = FusedCfg<H, W, TILED>;
-    return C::LAYOUT == LAY_ROWPAD ? C::RP : (C::LAYOUT == LAY_STRIP ? C::SP : W);
+    return C::LAYOUT == LAY_STRIP ? C::SP : W;
 }
 
 // Pass 1 line j of this thread -> (array, column).
@@ -107,7 +106,7 @@ __device__ __forceinline__ void map_col(int j, int warp, int lane, int &a, int &
         a = (lane & 7) + 8 * (combo % (C::G / 8));
         col = (lane >> 3) + 4 * (combo / (C::G / 8));
     } else {
-        // 32 adjacent columns (of the strip, or of one padded array)
+        // 32 adjacent columns of the strip
         const int s = lane + 32 * (warp + C::NW * j);
         a = s / W;
         col = s % W;
@@ -123,15 +122,10 @@ __device__ __forceinline__ void map_row(int j, int warp, int lane, int &a, int &
         const int combo = warp + C::NW * j;
         a = (lane & 7) + 8 * (combo % (C::G / 8));
         r = (lane >> 3) + 4 * (combo / (C::G / 8));
-    } else if constexpr (C::LAYOUT == LAY_STRIP) {
+    } else {
         const int u = (lane >> 3) + 4 * (warp + C::NW * j);
         a = u % C::G;
         r = (lane & 7) + 8 * (u / C::G);
-    } else {
-        // 32 adjacent rows of one padded array
-        const int s = lane + 32 * (warp + C::NW * j);
-        a = s / H;
-        r = s % H;
     }
 }
 
@@ -199,18 +193,10 @@ __device__ __forceinline__ void issue_fill(const FusedParams &p, const ChunkGeom
     if constexpr (C::LAYOUT == LAY_SLOT) {
         for (int a = lane; a < g.n; a += 32)
             bulk_load(stage + a * C::P, arr_in(p, g.first + a, C::HW), C::HW * 4, bar);
-    } else if constexpr (C::LAYOUT == LAY_STRIP) {
+    } else {
         for (int r = lane; r < H; r += 32) {
             const float *src = p.in + (g.brow * H + r) * p.ld_in + (long long)g.t0 * W;
             bulk_load(stage + r * C::SP, src, (uint32_t)(g.n * W * 4), bar);
-        }
-    } else {
-        for (int q = lane; q < g.n * H; q += 32) {
-            const int a = q / H, r = q % H;
-            const float *src;
-            if constexpr (TILED) src = p.in + (g.brow * H + r) * p.ld_in + (long long)(g.t0 + a) * W;
-            else src = arr_in(p, g.first + a, C::HW) + (long long)r * W;
-            bulk_load(stage + a * C::AP + r * C::RP, src, W * 4, bar);
         }
     }
 }
@@ -222,18 +208,10 @@ __device__ __forceinline__ void issue_drain(const FusedParams &p, const ChunkGeo
     using C = FusedCfg<H, W, TILED>;
     if constexpr (C::LAYOUT == LAY_SLOT) {
         for (int a = lane; a < g.n; a += 32) bulk_store(arr_out(p, g.first + a, C::HW), stage + a * C::P, C::HW * 4);
-    } else if constexpr (C::LAYOUT == LAY_STRIP) {
+    } else {
         for (int r = lane; r < H; r += 32) {
             float *dst = p.out + (g.brow * H + r) * p.ld_out + (long long)g.t0 * W;
             bulk_store(dst, stage + r * C::SP, (uint32_t)(g.n * W * 4));
-        }
-    } else {
-        for (int q = lane; q < g.n * H; q += 32) {
-            const int a = q / H, r = q % H;
-            float *dst;
-            if constexpr (TILED) dst = p.out + (g.brow * H + r) * p.ld_out + (long long)(g.t0 + a) * W;
-            else dst = arr_out(p, g.first + a, C::HW) + (long long)r * W;
-            bulk_store(dst, stage + a * C::AP + r * C::RP, W * 4);
         }
     }
 }
@@ -401,6 +379,7 @@ cudaError_t fused_init_device(int device)
     e = cudaGetLastError();
     if (e == cudaSuccess) e = init_cos_table(tmp);
     if (e == cudaSuccess) e = lines_init_table(tmp);
+    if (e == cudaSuccess) e = ring_init_table(tmp);
     if (e == cudaSuccess) {
         k_gen_cos_table3<<<(769 + 255) / 256, 256>>>(tmp);
         e = cudaGetLastError();
@@ -416,7 +395,7 @@ cudaError_t fused_init_device(int device)
 bool fused_supported(int rows, int cols)
 {
     auto ok = [](int n) { return n == 8 || n == 16 || n == 32; };
-    return (ok(rows) && ok(cols)) || (rows == 64 && cols == 64);
+    return (ok(rows) && ok(cols)) || ring_supported(rows, cols);
 }
 
 template <int H, int W, int DIR, bool TILED>
@@ -507,7 +486,7 @@ static cudaError_t launch_h(int cols, Dir dir, const DirScales &sc, const ExecGe
 cudaError_t fused_launch(int rows, int cols, Dir dir, const DirScales &sc, const ExecGeom &g,
                          unsigned int *status, cudaStream_t stream)
 {
-    if (rows == 64 && cols == 64) return launch_hw<64, 64>(dir, sc, g, status, stream);
+    if (ring_supported(rows, cols)) return ring_launch(rows, cols, dir, sc, g, status, stream);
     switch (rows) {
         case 8: return launch_h<8>(cols, dir, sc, g, status, stream);
         case 16: return launch_h<16>(cols, dir, sc, g, status, stream);

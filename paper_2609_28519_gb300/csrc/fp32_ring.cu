@@ -1,0 +1,653 @@
+// FP32 ring kernels for sides 64 and 128: 64x64, 64x128, 128x64, 128x128.
+//
+// What is computed: Eq. 2 of the BRiDCT paper, C(X) = Q_h X Q_w^T (forward,
+// DCT-II), C^{-1}(Y) = Q_h^T Y Q_w (inverse, DCT-III) and the normalized
+// round trip (Prop. 1: forward core, E_n^2, adjoint core per axis), one read
+// and one write of every element, both passes on chip.
+//
+// Organization (warp-specialized, one persistent CTA per SM):
+//  * one producer warp keeps a ring of S shared-memory slots full, one array
+//    per slot.  Contiguous batches and image tiles move by TMA tensor copies
+//    (boxes of 32 columns x all rows, 128-byte swizzle), completing on the
+//    slot's mbarrier, and leave by TMA tensor stores; the producer refills a
+//    slot with the array S positions ahead once its stores have read it.
+//    Indexed batches (ragged classes, arrays at arbitrary offsets) move by
+//    16-byte cp.async copies placed at the same swizzled positions and leave
+//    by vector stores;
+//  * NG consumer groups (named barriers, no CTA-wide synchronization) take
+//    the slots round robin, about three slots per group, so each group's next
+//    arrays are in flight while it computes; a group transforms every row of
+//    its array, then every column, in place.
+//
+// Slot layout (the GPU counterpart of the paper's padded stride, Section
+// 3.2): columns 32b .. 32b+31 of all rows form box b; row r of a box is 128
+// bytes, whose 16-byte chunk k sits at chunk position k XOR (r mod 8).  Eight
+// consecutive rows at one logical chunk, and 32 consecutive columns of one
+// row, then fall into distinct banks, so the row pass (one row per thread,
+// 16-byte accesses) and the column pass (one column per thread) are both
+// free of bank conflicts.
+//
+// 1D lines of 64 points run whole in one thread (dct_cores.cuh).  Lines of
+// 128 points are shared by two threads of different warps through the first
+// even/odd split of the DCT-II: role 0 evaluates the even outputs as a
+// 64-point DCT-II of the sums x_j + x_{127-j}, role 1 the odd outputs as a
+// 64-point DCT-IV of the differences.  The inverse runs the split backwards:
+// role 0 a 64-point DCT-III of the even inputs (a), role 1 a 64-point DCT-IV
+// of the odd inputs (b), then x_j = a_j + b_j and x_{127-j} = a_j - b_j.
+// After a 128-point row pass the row is left in a permuted order that the
+// column pass undoes when it writes back:
+//  * forward: Y_{2m} at position m, Y_{2m+1} at 64 + ((m + 16) mod 64);
+//  * inverse and round trip: x_j at j, x_{127-j} at 64 + j (j < 64);
+// either way the 32 columns a warp takes in the column pass occupy 32
+// distinct banks of every row.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdio>
+
+#include "bdct_internal.h"
+#include "dct_cores.cuh"
+#include "ptx.cuh"
+
+namespace bdct {
+
+cudaError_t ring_init_table(const float *d_table) { return init_cos_table(d_table); }
+
+bool ring_supported(int rows, int cols)
+{
+    return (rows == 64 || rows == 128) && (cols == 64 || cols == 128);
+}
+
+constexpr int kRingMaxSmem = 232448;  // 227 KiB, the opt-in limit per CTA
+
+template <int H, int W>
+struct RingCfg {
+    static constexpr int TR = W / 64;   // threads per row line
+    static constexpr int TC = H / 64;   // threads per column line
+    static constexpr int GT = H * TR;   // threads per consumer group
+    static constexpr int GW = GT / 32;  // warps per consumer group
+    static constexpr int SLOT_BYTES = H * W * 4;
+    static constexpr int SLOT_FLOATS = H * W;
+    static constexpr int BOX_BYTES = H * 128;  // 32 columns x H rows
+    static constexpr int S_MAX = (kRingMaxSmem - 2048) / SLOT_BYTES;
+    // about three slots per group, so that a group's next arrays load while
+    // it computes; the slot count is a multiple of the group count (a group
+    // always reuses slots it consumed itself)
+    static constexpr int NG = S_MAX / 3 < 1 ? 1 : S_MAX / 3;
+    static constexpr int S = (S_MAX / NG) * NG;
+    static constexpr int PROD_WARP = NG * GW;
+    static constexpr int THREADS = (NG * GW + 1) * 32;
+    // slots start 1024-byte aligned (128-byte swizzle atoms)
+    static constexpr size_t SMEM = 1024 + (size_t)S * SLOT_BYTES + (size_t)2 * S * 8;
+    static_assert(H * TR == W * TC, "both passes use the whole group");
+    static_assert(GT % 32 == 0 && S >= 2 && S % NG == 0, "ring shape");
+    static_assert(SMEM <= (size_t)kRingMaxSmem, "shared memory");
+    static_assert(BOX_BYTES % 1024 == 0, "swizzle atoms");
+};
+
+// Named barrier over the threads of one consumer group.
+__device__ __forceinline__ void group_sync(int id, int nthreads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Named barrier that also ANDs a predicate over the group.
+__device__ __forceinline__ bool group_and(int id, int nthreads, bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(id), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
+
+// Slot byte offset of 16-byte chunk k (k < W/4) of row r.
+template <int H>
+__device__ __forceinline__ uint32_t sw_chunk(int r, int k)
+{
+    return (uint32_t)((k >> 3) * (H * 128) + r * 128 + (((k & 7) ^ (r & 7)) << 4));
+}
+
+// Row view: chunk k of a fixed row r is at base + (k / 8) * BOX_BYTES + o[k % 8].
+struct RowView {
+    uint32_t o[8];
+    __device__ __forceinline__ explicit RowView(int r)
+    {
+#pragma unroll
+        for (int t = 0; t < 8; ++t) o[t] = (uint32_t)(r * 128 + ((t ^ (r & 7)) << 4));
+    }
+};
+
+// Column view: the float at slot position p of row i is at base + i * 128 + o[i % 8].
+template <int H>
+struct ColView {
+    uint32_t o[8];
+    __device__ __forceinline__ explicit ColView(int p)
+    {
+        const int pc = p >> 2;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) o[t] = (uint32_t)((pc >> 3) * (H * 128) + (((pc & 7) ^ t) << 4) + (p & 3) * 4);
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ T &at(char *base, uint32_t off)
+{
+    return *reinterpret_cast<T *>(base + off);
+}
+
+// Slot position of logical column c after the row pass (see the header).
+template <int W, int DIR>
+__device__ __forceinline__ int ring_colpos(int c)
+{
+    if constexpr (W == 64) return c;
+    else if constexpr (DIR == DIR_FWD) return (c & 1) ? 64 + (((c >> 1) + 16) & 63) : (c >> 1);
+    else return c < 64 ? c : 191 - c;
+}
+
+template <int N>
+__device__ __forceinline__ void scale_from(float (&x)[N], float first, float rest)
+{
+    x[0] *= first;
+#pragma unroll
+    for (int k = 1; k < N; ++k) x[k] *= rest;
+}
+
+// The 64-point core of one role of a 128-point line.  On entry v holds the
+// role's input (forward and round trip: sums or differences; inverse: the
+// even or odd coefficients, already scaled); on exit y holds the role's
+// output (forward: its coefficients, scaled; inverse and round trip: a or b).
+template <int DIR>
+__device__ __forceinline__ void role_core(int role, const float (&v)[64], float (&y)[64], AxisScale s)
+{
+    if constexpr (DIR == DIR_FWD) {
+        if (role == 0) DCT2<64>::run(v, y);
+        else DCT4<64>::run(v, y);
+        scale_from<64>(y, role ? s.s1 : s.s0, s.s1);
+    } else if constexpr (DIR == DIR_INV) {
+        if (role == 0) DCT3<64>::run(v, y);
+        else DCT4<64>::run(v, y);
+    } else {
+        float t[64];
+        if (role == 0) {
+            DCT2<64>::run(v, t);
+            scale_from<64>(t, s.s0, s.s1);
+            DCT3<64>::run(t, y);
+        } else {
+            DCT4<64>::run(v, t);
+            scale_from<64>(t, s.s1, s.s1);
+            DCT4<64>::run(t, y);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- row pass
+template <int H, int W, int DIR>
+__device__ __forceinline__ void ring_rows(char *slot, int gt, int bar, AxisScale s)
+{
+    using C = RingCfg<H, W>;
+    constexpr int BB = C::BOX_BYTES;
+    if constexpr (W == 64) {
+        // one thread per row, in place
+        const RowView rv(gt);
+        float x[64];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const float4 t = at<float4>(slot, (k >> 3) * BB + rv.o[k & 7]);
+            x[4 * k] = t.x; x[4 * k + 1] = t.y; x[4 * k + 2] = t.z; x[4 * k + 3] = t.w;
+        }
+        line_op<64, DIR>(x, s);
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            at<float4>(slot, (k >> 3) * BB + rv.o[k & 7]) = make_float4(x[4 * k], x[4 * k + 1], x[4 * k + 2], x[4 * k + 3]);
+    } else {
+        const int role = gt / H;  // warp-uniform
+        const int r = gt - role * H;
+        const RowView rv(r);
+        float v[64];
+        if constexpr (DIR == DIR_INV) {
+            // role 0: even coefficients, role 1: odd coefficients
+            if (role == 0) {
+#pragma unroll
+                for (int k = 0; k < 32; ++k) {
+                    const float4 t = at<float4>(slot, (k >> 3) * BB + rv.o[k & 7]);
+                    v[2 * k] = t.x; v[2 * k + 1] = t.z;
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 32; ++k) {
+                    const float4 t = at<float4>(slot, (k >> 3) * BB + rv.o[k & 7]);
+                    v[2 * k] = t.y; v[2 * k + 1] = t.w;
+                }
+            }
+            scale_from<64>(v, role ? s.s1 : s.s0, s.s1);
+        } else {
+            // sums (role 0) or differences (role 1) of x_j and x_{127-j}
+            const float sg = role ? -1.0f : 1.0f;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const float4 a = at<float4>(slot, (k >> 3) * BB + rv.o[k & 7]);
+                const float4 b = at<float4>(slot, ((31 - k) >> 3) * BB + rv.o[(31 - k) & 7]);
+                v[4 * k] = fmaf(sg, b.w, a.x);
+                v[4 * k + 1] = fmaf(sg, b.z, a.y);
+                v[4 * k + 2] = fmaf(sg, b.y, a.z);
+                v[4 * k + 3] = fmaf(sg, b.x, a.w);
+            }
+        }
+        group_sync(bar, C::GT);  // every read of the row done before it is overwritten
+        float y[64];
+        role_core<DIR>(role, v, y, s);
+        if (role == 0) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+                at<float4>(slot, (k >> 3) * BB + rv.o[k & 7]) = make_float4(y[4 * k], y[4 * k + 1], y[4 * k + 2], y[4 * k + 3]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                // forward: Y_{2m+1} at 64 + ((m + 16) mod 64); inverse / round trip: b_j at 64 + j
+                const int kk = 16 + (DIR == DIR_FWD ? ((k + 4) & 15) : k);
+                at<float4>(slot, (kk >> 3) * BB + rv.o[kk & 7]) = make_float4(y[4 * k], y[4 * k + 1], y[4 * k + 2], y[4 * k + 3]);
+            }
+        }
+        if constexpr (DIR != DIR_FWD) {
+            // x_j = a_j + b_j (position j), x_{127-j} = a_j - b_j (position 64 + j)
+            group_sync(bar, C::GT);
+            constexpr int TASKS = H * 16;  // (row, 4 consecutive j)
+#pragma unroll
+            for (int t = gt; t < TASKS; t += C::GT) {
+                const int rr = t >> 4, k = t & 15;
+                const uint32_t oa = sw_chunk<H>(rr, k), ob = sw_chunk<H>(rr, 16 + k);
+                const float4 a = at<float4>(slot, oa), b = at<float4>(slot, ob);
+                at<float4>(slot, oa) = make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+                at<float4>(slot, ob) = make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- column pass
+template <int H, int W, int DIR>
+__device__ __forceinline__ void ring_cols(char *slot, int gt, int bar, AxisScale s)
+{
+    using C = RingCfg<H, W>;
+    if constexpr (H == 64) {
+        // one thread per column; reads at the permuted position, writes at the natural one
+        const int c = gt;
+        const ColView<H> src(ring_colpos<W, DIR>(c));
+        float x[64];
+#pragma unroll
+        for (int i = 0; i < 64; ++i) x[i] = at<float>(slot, i * 128 + src.o[i & 7]);
+        if constexpr (W == 128) group_sync(bar, C::GT);
+        line_op<64, DIR>(x, s);
+        const ColView<H> dst(c);
+#pragma unroll
+        for (int i = 0; i < 64; ++i) at<float>(slot, i * 128 + dst.o[i & 7]) = x[i];
+    } else {
+        const int role = gt / W;  // warp-uniform
+        const int c = gt - role * W;
+        const ColView<H> src(ring_colpos<W, DIR>(c));
+        float v[64];
+        if constexpr (DIR == DIR_INV) {
+            // even rows (role 0) or odd rows (role 1)
+            if (role == 0) {
+#pragma unroll
+                for (int m = 0; m < 64; ++m) v[m] = at<float>(slot, 2 * m * 128 + src.o[(2 * m) & 7]);
+            } else {
+#pragma unroll
+                for (int m = 0; m < 64; ++m) v[m] = at<float>(slot, (2 * m + 1) * 128 + src.o[(2 * m + 1) & 7]);
+            }
+            scale_from<64>(v, role ? s.s1 : s.s0, s.s1);
+        } else {
+            const float sg = role ? -1.0f : 1.0f;
+#pragma unroll
+            for (int i = 0; i < 64; ++i)
+                v[i] = fmaf(sg, at<float>(slot, (127 - i) * 128 + src.o[(127 - i) & 7]),
+                            at<float>(slot, i * 128 + src.o[i & 7]));
+        }
+        group_sync(bar, C::GT);  // all reads done: writes go to natural positions
+        float y[64];
+        role_core<DIR>(role, v, y, s);
+        const ColView<H> dst(c);
+        if constexpr (DIR == DIR_FWD) {
+            // rows 2m (role 0) or 2m + 1 (role 1)
+            if (role == 0) {
+#pragma unroll
+                for (int m = 0; m < 64; ++m) at<float>(slot, 2 * m * 128 + dst.o[(2 * m) & 7]) = y[m];
+            } else {
+#pragma unroll
+                for (int m = 0; m < 64; ++m) at<float>(slot, (2 * m + 1) * 128 + dst.o[(2 * m + 1) & 7]) = y[m];
+            }
+        } else {
+            if (role == 0) {
+#pragma unroll
+                for (int j = 0; j < 64; ++j) at<float>(slot, j * 128 + dst.o[j & 7]) = y[j];  // a_j at row j
+            } else {
+#pragma unroll
+                for (int j = 0; j < 64; ++j)
+                    at<float>(slot, (127 - j) * 128 + dst.o[(127 - j) & 7]) = y[j];  // b_j at row 127 - j
+            }
+            group_sync(bar, C::GT);
+            // x_j = a_j + b_j, x_{127-j} = a_j - b_j; two threads per column, 32 pairs each
+            auto comb = [&](int j) {
+                const uint32_t oa = j * 128 + dst.o[j & 7], ob = (127 - j) * 128 + dst.o[(127 - j) & 7];
+                const float a = at<float>(slot, oa), b = at<float>(slot, ob);
+                at<float>(slot, oa) = a + b;
+                at<float>(slot, ob) = a - b;
+            };
+            if (role == 0) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) comb(j);
+            } else {
+#pragma unroll
+                for (int j = 32; j < 64; ++j) comb(j);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- kernel
+struct RingParams {
+    CUtensorMap map_in, map_out;  // contiguous and tiled batches (TMA)
+    const float *in;
+    float *out;
+    long long count;          // arrays or tiles
+    int tiles_per_row;        // tiled only
+    int tiled;
+    int indexed;              // arrays at in + in_off[a], out + out_off[a] (cp.async path)
+    long long ld_in, ld_out;  // tiled only (floats)
+    DirScales sc;
+    unsigned int *status;
+    const long long *in_off, *out_off;
+};
+
+// TMA coordinates (x: column, y: row) of the first element of array or tile a.
+template <int H, int W>
+__device__ __forceinline__ void ring_coords(const RingParams &p, long long a, int &x, int &y)
+{
+    if (p.tiled) {
+        const long long br = a / p.tiles_per_row, bc = a - br * p.tiles_per_row;
+        x = (int)(bc * W);
+        y = (int)(br * H);
+    } else {
+        x = 0;
+        y = (int)(a * H);
+    }
+}
+
+template <int H, int W, int DIR>
+__global__ void __launch_bounds__(RingCfg<H, W>::THREADS, 1) k_ring(const __grid_constant__ RingParams p)
+{
+    using C = RingCfg<H, W>;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte aligned slots
+    const uint32_t raw = smem_u32(smem_raw);
+    char *smem = reinterpret_cast<char *>(smem_raw) + (((raw + 1023u) & ~1023u) - raw);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + C::S * C::SLOT_BYTES);
+    uint64_t *done = full + C::S;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long grid = gridDim.x;
+    const long long first = blockIdx.x;
+    const int n = first < p.count ? (int)((p.count - first + grid - 1) / grid) : 0;
+
+    if (tid == 0) {
+        for (int s = 0; s < C::S; ++s) {
+            mbar_init(&full[s], p.indexed ? 32 : 1);  // 32 lane arrivals (cp.async) or one expect_tx
+            mbar_init(&done[s], 1);
+        }
+        fence_mbar_init();
+    }
+    pdl_launch_dependents();
+    pdl_wait_prerequisites();
+    __syncthreads();
+
+    if (warp == C::PROD_WARP) {
+        // ---------------- producer
+        bool ok = true;
+        int filled = 0, consumed = 0;
+        if (!p.indexed) {
+            // TMA tensor copies issued by lane 0
+            auto fill = [&](int j) {
+                const int s = j % C::S;
+                char *slot = smem + s * C::SLOT_BYTES;
+                int x, y;
+                ring_coords<H, W>(p, first + (long long)j * grid, x, y);
+                mbar_arrive_expect_tx(&full[s], (uint32_t)C::SLOT_BYTES);
+#pragma unroll
+                for (int b = 0; b < W / 32; ++b) tensor_load_2d(slot + b * C::BOX_BYTES, &p.map_in, x + 32 * b, y, &full[s]);
+            };
+            if (lane == 0) {
+                const int pro = n < C::S ? n : C::S;
+                for (int j = 0; j < pro; ++j) fill(j);
+                filled = pro;
+                for (int j = 0; j < n; ++j) {
+                    const int s = j % C::S;
+                    if (!mbar_wait_bounded(&done[s], (uint32_t)((j / C::S) & 1))) {
+                        record_timeout(p.status);
+                        ok = false;
+                        break;
+                    }
+                    consumed = j + 1;
+                    const char *slot = smem + s * C::SLOT_BYTES;
+                    int x, y;
+                    ring_coords<H, W>(p, first + (long long)j * grid, x, y);
+#pragma unroll
+                    for (int b = 0; b < W / 32; ++b) tensor_store_2d(&p.map_out, x + 32 * b, y, slot + b * C::BOX_BYTES);
+                    bulk_commit();
+                    // refill the slot stored one step earlier once its stores have read it
+                    if (j >= 1 && j - 1 + C::S < n) {
+                        bulk_wait_read<1>();
+                        fill(j - 1 + C::S);
+                        filled = j + C::S;
+                    }
+                }
+                bulk_wait<0>();
+            }
+        } else {
+            // 16-byte cp.async copies by all lanes, at the swizzled positions
+            constexpr int Q = W / 4;  // chunks per row
+            auto fill = [&](int j) {
+                const long long a = first + (long long)j * grid;
+                const int s = j % C::S;
+                char *slot = smem + s * C::SLOT_BYTES;
+                const float *src = p.in + p.in_off[a];
+#pragma unroll 8
+                for (int t = lane; t < H * Q; t += 32) {
+                    const int r = t / Q, k = t - r * Q;
+                    cp_async16(slot + sw_chunk<H>(r, k), src + r * W + 4 * k);
+                }
+                cp_async_mbar_arrive(&full[s]);
+            };
+            const int pro = n < C::S ? n : C::S;
+            for (int j = 0; j < pro; ++j) fill(j);
+            filled = pro;
+            for (int j = 0; j < n; ++j) {
+                const int s = j % C::S;
+                ok = __all_sync(0xffffffffu, mbar_wait_bounded(&done[s], (uint32_t)((j / C::S) & 1)));
+                if (!ok) {
+                    if (lane == 0) record_timeout(p.status);
+                    break;
+                }
+                consumed = j + 1;
+                const long long a = first + (long long)j * grid;
+                float *dst = p.out + p.out_off[a];
+                const char *slot = smem + s * C::SLOT_BYTES;
+#pragma unroll 8
+                for (int t = lane; t < H * Q; t += 32) {
+                    const int r = t / Q, k = t - r * Q;
+                    *reinterpret_cast<float4 *>(dst + r * W + 4 * k) =
+                        *reinterpret_cast<const float4 *>(slot + sw_chunk<H>(r, k));
+                }
+                __syncwarp();  // every lane's reads of the slot done before any lane refills it
+                if (j + C::S < n) {
+                    fill(j + C::S);
+                    filled = j + C::S + 1;
+                }
+            }
+            cp_async_wait_all();
+        }
+        if (!__all_sync(0xffffffffu, ok)) {
+            // loads issued for arrays never consumed land (bounded) before the CTA exits
+            if (lane == 0)
+                for (int j = consumed; j < filled; ++j)
+                    if (!mbar_wait_bounded(&full[j % C::S], (uint32_t)((j / C::S) & 1))) break;
+        }
+        return;
+    }
+
+    // ---------------- consumers
+    const int g = warp / C::GW;
+    const int gt = tid - g * C::GT;
+    const int bar = 1 + g;
+    for (int j = g; j < n; j += C::NG) {
+        const int s = j % C::S;
+        bool ok = mbar_wait_bounded(&full[s], (uint32_t)((j / C::S) & 1));
+        ok = group_and(bar, C::GT, ok);
+        if (!ok) {
+            if (gt == 0) record_timeout(p.status);
+            break;
+        }
+        char *slot = smem + s * C::SLOT_BYTES;
+        ring_rows<H, W, DIR>(slot, gt, bar, p.sc.w);
+        group_sync(bar, C::GT);
+        ring_cols<H, W, DIR>(slot, gt, bar, p.sc.h);
+        fence_proxy_async_smem();  // the TMA store reads the slot through the async proxy
+        group_sync(bar, C::GT);
+        if (gt == 0) mbar_arrive(&done[s]);
+    }
+}
+
+// ---------------------------------------------------------------- host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(f);
+    }
+    return fn;
+}
+
+// A row-major float matrix of `rows` x `cols` with row stride `ld` floats,
+// read and written in boxes of 32 columns x `box_rows` rows, 128-byte swizzle.
+static cudaError_t make_map(CUtensorMap *m, const float *base, unsigned long long rows, unsigned long long cols,
+                            unsigned long long ld, int box_rows)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    if (rows > 0xffffffffull || cols > 0xffffffffull) return cudaErrorInvalidValue;
+    const cuuint64_t dims[2] = {cols, rows};
+    const cuuint64_t strides[1] = {ld * sizeof(float)};
+    const cuuint32_t box[2] = {32, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <int H, int W, int DIR>
+static cudaError_t ring_launch_one(const DirScales &sc, const ExecGeom &g, unsigned int *status,
+                                   cudaStream_t stream)
+{
+    using C = RingCfg<H, W>;
+    auto kern = k_ring<H, W, DIR>;
+    static int num_sms[64];
+    static bool ready[64];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!ready[dev]) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        if (e != cudaSuccess) return e;
+        int bps = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, C::THREADS, C::SMEM);
+        if (e != cudaSuccess) return e;
+        if (bps < 1) return cudaErrorInvalidConfiguration;
+        e = cudaDeviceGetAttribute(&num_sms[dev], cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        if (debug_enabled())
+            fprintf(stderr, "[bdct] k_ring<%d,%d,%d>: %d slots of %d B, %d groups x %d warps + producer, smem %zu B\n",
+                    H, W, DIR, C::S, C::SLOT_BYTES, C::NG, C::GW, C::SMEM);
+        ready[dev] = true;
+    }
+    if (g.count <= 0) return cudaSuccess;
+    RingParams p{};
+    p.in = g.in;
+    p.out = g.out;
+    p.count = g.count;
+    p.tiled = g.tiled;
+    p.tiles_per_row = g.tiles_per_row;
+    p.ld_in = g.ld_in;
+    p.ld_out = g.ld_out;
+    p.sc = sc;
+    p.status = status;
+    p.in_off = g.in_off;
+    p.out_off = g.out_off;
+    p.indexed = (g.in_off != nullptr || g.out_off != nullptr) ? 1 : 0;
+    if (p.indexed) {
+        if (!g.in_off || !g.out_off) return cudaErrorInvalidValue;
+    } else if (g.tiled) {
+        const unsigned long long rows = (unsigned long long)(g.count / g.tiles_per_row) * H;
+        const unsigned long long cols = (unsigned long long)g.tiles_per_row * W;
+        e = make_map(&p.map_in, g.in, rows, cols, (unsigned long long)g.ld_in, H);
+        if (e == cudaSuccess) e = make_map(&p.map_out, g.out, rows, cols, (unsigned long long)g.ld_out, H);
+        if (e != cudaSuccess) return e;
+    } else {
+        const unsigned long long rows = (unsigned long long)g.count * H;
+        e = make_map(&p.map_in, g.in, rows, W, W, H);
+        if (e == cudaSuccess) e = make_map(&p.map_out, g.out, rows, W, W, H);
+        if (e != cudaSuccess) return e;
+    }
+    long long grid = num_sms[dev];
+    if (grid > g.count) grid = g.count;
+    if ((g.count + grid - 1) / grid > 0x7fffff00LL) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(C::THREADS);
+    cfg.dynamicSmemBytes = C::SMEM;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, p);
+}
+
+template <int H, int W>
+static cudaError_t ring_dir(Dir dir, const DirScales &sc, const ExecGeom &g, unsigned int *st, cudaStream_t s)
+{
+    switch (dir) {
+        case DIR_FWD: return ring_launch_one<H, W, DIR_FWD>(sc, g, st, s);
+        case DIR_INV: return ring_launch_one<H, W, DIR_INV>(sc, g, st, s);
+        default: return ring_launch_one<H, W, DIR_RT>(sc, g, st, s);
+    }
+}
+
+cudaError_t ring_launch(int rows, int cols, Dir dir, const DirScales &sc, const ExecGeom &g, unsigned int *status,
+                        cudaStream_t stream)
+{
+    if (rows == 64 && cols == 64) return ring_dir<64, 64>(dir, sc, g, status, stream);
+    if (rows == 64 && cols == 128) return ring_dir<64, 128>(dir, sc, g, status, stream);
+    if (rows == 128 && cols == 64) return ring_dir<128, 64>(dir, sc, g, status, stream);
+    if (rows == 128 && cols == 128) return ring_dir<128, 128>(dir, sc, g, status, stream);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace bdct

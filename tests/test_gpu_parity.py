@@ -13,7 +13,8 @@ from paper_2609_28519_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 FUSED_SHAPES = [(h, w) for h in (8, 16, 32) for w in (8, 16, 32)] + [(64, 64)]
-SEPARABLE_SHAPES = [(128, 128), (256, 256), (64, 256), (128, 512), (1024, 1024), (2048, 64),
+RING_SHAPES = [(64, 64), (64, 128), (128, 64), (128, 128)]
+SEPARABLE_SHAPES = [(256, 256), (64, 256), (256, 128), (128, 512), (1024, 1024), (2048, 64),
                     (512, 2048), (24, 40), (12, 8), (768, 64)]
 KINDS = ["forward", "inverse", "roundtrip"]
 
@@ -55,6 +56,47 @@ def test_fused_shapes_all_kinds(oracle_mod, cuda_dev, h, w, norm):
     for kind in KINDS:
         y = _run(plan, kind, x, cuda_dev)
         _assert_parity(oracle_mod, y, _ref(oracle_mod, kind, x, norm), x, norm, kind, (h, w, norm, kind))
+
+
+@pytest.mark.parametrize("h,w", RING_SHAPES)
+@pytest.mark.parametrize("norm", [0, 1])
+def test_ring_shapes_all_kinds(oracle_mod, cuda_dev, h, w, norm):
+    """Sides 64 and 128 (the warp-specialized ring kernels, 128-point lines
+    split over two threads): a few arrays, fewer than the CTAs."""
+    from paper_2609_28519_gb300 import Plan
+    plan = Plan(h, w, norm=norm, path="fp32")
+    assert plan.info().variant == 1
+    x = inputs.gaussian(1500 + h + 3 * w, 7, h, w)
+    for kind in KINDS:
+        y = _run(plan, kind, x, cuda_dev)
+        _assert_parity(oracle_mod, y, _ref(oracle_mod, kind, x, norm), x, norm, kind, (h, w, norm, kind))
+
+
+@pytest.mark.parametrize("h,w", RING_SHAPES)
+def test_ring_wraparound_replicated(oracle_mod, cuda_dev, h, w):
+    """Enough arrays that every CTA goes around its slot ring several times
+    (every slot and barrier phase in use), plus a ragged tail: the batch
+    repeats 5 distinct arrays, so every copy must give the same bits, and the
+    distinct ones must match the oracle."""
+    import torch
+    from paper_2609_28519_gb300 import Plan
+    sms = torch.cuda.get_device_properties(cuda_dev).multi_processor_count
+    ring = 12 if (h, w) == (64, 64) else (3 if (h, w) == (128, 128) else 6)
+    batch = sms * (3 * ring + 1) + 11
+    base = inputs.uniform(1700 + h + w, 5, h, w)
+    plan = Plan(h, w, path="fp32")
+    x = torch.from_numpy(base).to(cuda_dev).repeat(batch // 5 + 1, 1, 1)[:batch].contiguous()
+    for kind in KINDS:
+        y = plan.execute(kind, x)
+        torch.cuda.synchronize()
+        first = y[:5].cpu().numpy()
+        _assert_parity(oracle_mod, first, _ref(oracle_mod, kind, base, 0), base, 0, kind, (h, w, kind))
+        ref_bits = torch.from_numpy(first).to(cuda_dev)
+        idx = torch.arange(batch, device=cuda_dev) % 5
+        assert torch.equal(y, ref_bits[idx]), (h, w, kind)
+        del y
+    del x
+    torch.cuda.empty_cache()
 
 
 @pytest.mark.parametrize("h,w", SEPARABLE_SHAPES)
@@ -175,18 +217,21 @@ def test_sweep_distributions(oracle_mod, cuda_dev, n):
     assert np.all(np.isfinite(weak_rel))  # reported, not accepted
 
 
-def test_fused_64_tiled_image(oracle_mod, cuda_dev):
-    """64x64 blocks of a 1024x512 image through the padded-row layout."""
+@pytest.mark.parametrize("h,w", RING_SHAPES)
+def test_ring_tiled_image(oracle_mod, cuda_dev, h, w):
+    """Blocks of a 1024x512 image read and written in place in the image
+    (one bulk copy per block row), all three directions."""
     import torch
     from paper_2609_28519_gb300 import Plan
     img = inputs.ramp_image(9, 1024, 512)
-    blocks = inputs.image_to_blocks(img, 64, 64)
-    plan = Plan(64, 64)
+    blocks = inputs.image_to_blocks(img, h, w)
+    plan = Plan(h, w)
     d = torch.from_numpy(img).to(cuda_dev)
-    spec = plan.execute_tiled("forward", d)
-    torch.cuda.synchronize()
-    got = inputs.image_to_blocks(spec.cpu().numpy(), 64, 64)
-    _assert_parity(oracle_mod, got, oracle_mod.forward(blocks, 0), blocks, 0, "forward", "tiled64")
+    for kind in KINDS:
+        out = plan.execute_tiled(kind, d)
+        torch.cuda.synchronize()
+        got = inputs.image_to_blocks(out.cpu().numpy(), h, w)
+        _assert_parity(oracle_mod, got, _ref(oracle_mod, kind, blocks, 0), blocks, 0, kind, ("tiled", h, w, kind))
 
 
 def test_inplace_and_tail_and_guards(oracle_mod, cuda_dev):
@@ -303,7 +348,9 @@ def test_auto_path_choice(cuda_dev):
     from paper_2609_28519_gb300 import Plan
     assert Plan(64, 64).info().variant == 1
     assert Plan(16, 16).info().variant == 1
-    assert Plan(128, 128).info().variant == 2
+    assert Plan(128, 128).info().variant == 1
+    assert Plan(64, 128).info().variant == 1
+    assert Plan(256, 256).info().variant == 2
     assert Plan(64, 64, path="split_tc").info().variant == 3
 
 
