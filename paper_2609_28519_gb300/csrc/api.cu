@@ -160,13 +160,13 @@ extern "C" int bdct_plan_create(bdct_plan **plan, int rows, int cols, unsigned k
         p->work_bytes = (size_t)chunk * arr_bytes;
         e = cudaMalloc(&p->work, p->work_bytes);
         if (e != cudaSuccess) { plan_free(p); t_last_cuda_error = (int)e; return BDCT_ERR_NO_MEMORY; }
-        p->line_tw_h = (size_t)cols + 1;
-        e = cudaMalloc(&p->line_tw, ((size_t)cols + 1 + (size_t)rows + 1) * sizeof(float2));
+        p->line_tw_h = lines_table_elems(cols);
+        e = cudaMalloc(&p->line_tw, (lines_table_elems(cols) + lines_table_elems(rows)) * sizeof(float2));
         if (e != cudaSuccess) { plan_free(p); t_last_cuda_error = (int)e; return BDCT_ERR_NO_MEMORY; }
         e = lines_gen_table(p->line_tw, cols, 0);
         if (e == cudaSuccess) e = lines_gen_table(p->line_tw + p->line_tw_h, rows, 0);
         if (e != cudaSuccess) { plan_free(p); return cuda_fail(e); }
-        p->table_bytes = ((size_t)cols + 1 + (size_t)rows + 1) * sizeof(float2);
+        p->table_bytes = (lines_table_elems(cols) + lines_table_elems(rows)) * sizeof(float2);
     } else {
         p->variant = 2;
         // operator matrices: forward and inverse in the plan's norm, and the

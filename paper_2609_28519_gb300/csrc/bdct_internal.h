@@ -74,8 +74,9 @@ cudaError_t lines_init_table(const float *d_table);
 cudaError_t lines_init_table3(const float *d_table);
 // True if n has an FFT-based line engine (powers of two 64..4096, and 768).
 bool lines_supported(int n);
-// The line engine's twiddle table for length n: exp(-i pi r / (2n)), r = 0..n,
-// generated in FP64 (n + 1 float2 entries).
+// The line engine's twiddle tables for length n (lines_table_elems(n)
+// float2 entries), generated in FP64.
+size_t lines_table_elems(int n);
 cudaError_t lines_gen_table(float2 *dst, int n, cudaStream_t s);
 // One separable pass over `count` arrays of rows x n: every row (length n)
 // gets the 1D transform of `dir` with per-index scales `sc` (forward: output

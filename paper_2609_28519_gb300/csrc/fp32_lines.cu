@@ -1,5 +1,5 @@
 // FFT-based FP32 line engine: one separable pass of the 2D DCT for long
-// lines (64 .. 4096 points, powers of two, and 768 = 2 * 3 * 2^7).
+// lines (64 .. 4096 points, powers of two, and 768 = 3 * 2^8).
 //
 // What is computed: the 1D factor of Eq. 2 of the BRiDCT paper along every
 // row of a batch of arrays -- y_k = s_k sum_j x_j cos(pi (2j+1) k / (2N))
@@ -17,9 +17,15 @@
 //   O_k = (Z_k - conj Z_{L-k}) / (2i), V_k = E_k + exp(-2 pi i k / N) O_k:
 //   y_k = Re(exp(-i pi k / (2N)) V_k), y_{N-k} = -Im(exp(-i pi k / (2N)) V_k).
 // The DCT-III runs the same steps backwards (its 1/L folded into a factor 2
-// on y_0).  Sub-FFTs (radix 2 and 3, up to 64 points) run in registers
-// (dct_cores.cuh); a warp transforms one to four lines; the FFT stays within
-// FP32 rounding of the exact sums (error grows like log N).
+// on y_0).
+//
+// GPU organization: T threads share a line, T dividing L1 and L2, so that in
+// both FFT steps every thread runs whole register-resident sub-FFTs (radix 2
+// and 3, dct_cores.cuh); the step-C results stay in registers and the split
+// partner Z_{L-k}, held by thread T - t of the same line, arrives by warp
+// shuffle.  All twiddles come from per-plan tables generated in FP64 and
+// staged in shared memory.  The FFT stays within FP32 rounding of the exact
+// sums (error grows like log N).
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -37,67 +43,79 @@ bool lines_supported(int n)
     return n == 64 || n == 128 || n == 256 || n == 512 || n == 1024 || n == 2048 || n == 4096 || n == 768;
 }
 
+// Four-step split L = N/2 = L1 * L2 (step A: L2 FFTs of length L1, step C:
+// L1 FFTs of length L2) and the threads that share one line: T divides both
+// L1 and L2, so in both steps every thread has whole sub-FFTs.
 template <int N>
 struct LineCfg {
     static constexpr int L = N / 2;
-    // four-step split L = L1 * L2 (step A: FFTs of L1, step C: FFTs of L2)
-    static constexpr int L1 = (N == 64) ? 4 : (N == 128) ? 8 : (N == 256) ? 8 : (N == 512) ? 16 : (N == 1024) ? 16
-                            : (N == 768) ? 12 : 32;
+    static constexpr int L1 = N == 64 ? 4 : N == 128 ? 8 : N == 256 ? 8 : N == 512 ? 16 : N == 1024 ? 16
+                            : N == 768 ? 24 : 32;
     static constexpr int L2 = L / L1;
-    static constexpr int TPL_RAW = L1 > L2 ? L1 : L2;
-    static constexpr int TPL = TPL_RAW > 32 ? 32 : TPL_RAW;  // threads per line
-    static constexpr int LPW = 32 / TPL;                     // lines per warp at once
-    static constexpr int NW = N >= 4096 ? 4 : 8;             // warps per CTA
+    static constexpr int T = N == 64 ? 4 : (N == 128 || N == 256 || N == 768) ? 8 : (N == 512 || N == 1024) ? 16 : 32;
+    static constexpr int JA = L2 / T;  // step-A sub-FFTs per thread
+    static constexpr int JC = L1 / T;  // step-C sub-FFTs per thread
+    static constexpr int LPW = 32 / T;  // lines per warp
+    static constexpr int NW = (N == 1024 || N == 2048 || N == 4096) ? 4 : 8;  // warps per CTA
     static constexpr int THREADS = 32 * NW;
-    static constexpr int PR = N <= 512 ? 32 : (N <= 1024 ? 16 : (N == 2048 ? 8 : 4));  // rows per panel
-    static constexpr int PP = N + 2 * L1 + 2;                // panel row pitch (floats)
-    static constexpr int A_FLOATS = 2 * L1 * (L2 + 1);       // step-A output, padded
-    static constexpr int SCR = A_FLOATS > N ? A_FLOATS : N;  // per-line scratch (floats)
-    static constexpr int ROUNDS = PR / (NW * LPW);
-    static constexpr int DELTA = 16 / LPW;                   // row distance of a warp's lines
-    static constexpr int SEG = PR < 16 ? PR : 16;            // rows per transposed-store segment
-    static constexpr int PAIRS = (L / 2 + 1 + TPL - 1) / TPL;  // split tasks per lane
-    static constexpr int TWN = N + 1;                        // quarter-wave twiddles
-    static constexpr size_t SMEM = (size_t)PR * PP * 4 + (size_t)NW * LPW * SCR * 4 + (size_t)TWN * 8;
-    static_assert(L1 * L2 == L && L1 <= 32, "split");
-    static_assert(ROUNDS >= 1 && ROUNDS * NW * LPW == PR, "panel");
-    static_assert(LPW == 1 || PR % 16 == 0, "line groups");
-    static_assert((PP % 4) == 2, "row pitch 2 mod 4 floats");
+    static constexpr int LPR = NW * LPW;  // lines per round
+    // Rows per panel.  For T < 16 a half-warp holds several lines; they sit T
+    // rows apart (rows 32 b + w + T sub of a 32-row block, w < T), which with a
+    // row pitch of 2 mod 32 floats puts them 2T banks apart.
+    static constexpr int PR = T < 16 ? (N == 768 ? 32 : 64) : (N <= 1024 ? 16 : (N == 2048 ? 8 : 4));
+    static constexpr int ROUNDS = PR / LPR;
+    static constexpr int A_FLOATS = 2 * L1 * (L2 + 1);  // step-A output, row pitch L2 + 1 complex
+    static constexpr int pitch(int need, int mod)
+    {
+        int p = need;
+        while (p % 32 != mod) ++p;
+        return p;
+    }
+    // line pitch: room for the step-A output of the inverse; 2 mod 32 floats so
+    // that the transposed store (16 rows x 2 columns per warp) is conflict-free
+    static constexpr int PP = pitch(A_FLOATS > N ? A_FLOATS : N, 2);
+    // per-line scratch: the lines of one warp 2T banks apart
+    static constexpr int SCR = pitch(A_FLOATS > N ? A_FLOATS : N, (2 * T) % 32);
+    static constexpr int SEG = PR < 16 ? PR : 16;  // rows per transposed-store segment
+    static constexpr int TAB_F2 = 3 * L;           // L step-A twiddles, then L float4 split twiddles
+    static constexpr size_t SMEM = (size_t)PR * PP * 4 + (size_t)LPR * SCR * 4 + (size_t)TAB_F2 * 8;
+    static_assert(L1 * L2 == L && L1 % T == 0 && L2 % T == 0 && 32 % T == 0, "split");
+    static_assert(ROUNDS >= 1 && ROUNDS * LPR == PR, "panel");
+    static_assert(T >= 16 || PR % 32 == 0, "line spacing");
+    static_assert(JC * L2 <= 64, "registers held through the split");
+    static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
-// exp(-i pi r / (2N)) for any r, from the quarter table tw[0..N] (angles 0..pi/2).
+// Panel row of line `sub` of warp-slot `slot` (slot = round * NW + warp).
 template <int N>
-__device__ __forceinline__ float2 twq(const float2 *tw, int r)
+__device__ __forceinline__ int line_row(int slot, int sub)
 {
-    r %= 4 * N;
-    if (r < 0) r += 4 * N;
-    bool conj = false;
-    if (r > 2 * N) { r = 4 * N - r; conj = true; }  // exp(-i(2pi - a)) = conj(exp(-i a))
-    float2 v;
-    if (r <= N) v = tw[r];
-    else {  // a = pi/2 + b: exp(-i a) = -i exp(-i b)
-        const float2 t = tw[r - N];
-        v = make_float2(t.y, -t.x);
-    }
-    return conj ? make_float2(v.x, -v.y) : v;
+    using C = LineCfg<N>;
+    if constexpr (C::T < 16) return 32 * (slot / C::T) + (slot % C::T) + C::T * sub;
+    else return slot * C::LPW + sub;
 }
+
+size_t lines_table_elems(int n) { return (size_t)3 * (n / 2); }
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b)
 {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 
-__device__ __forceinline__ float2 conjf2(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b)  // a * conj(b)
+{
+    return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
 
-// Step A of the four-step FFT: for every task m2 of this lane, the FFT of
-// length L1 of src[L2*m1 + m2] (m1 < L1), times exp(-2 pi i m2 k1 / L),
-// written to A[k1][m2] of dst (pitch L2 + 1).  src and dst are distinct.
+// Step A for this thread: for m2 = t + T j, the length-L1 FFT of
+// src[L2 m1 + m2] (m1 < L1) times exp(-2 pi i m2 k1 / L), to A[k1][m2].
 template <int N>
-__device__ __forceinline__ void step_a(const float2 *src, float2 *dst, const float2 *tw, int t)
+__device__ __forceinline__ void four_step_a(const float2 *src, float2 *A, const float2 *ta, int t)
 {
     using C = LineCfg<N>;
-#pragma unroll 1
-    for (int m2 = t; m2 < C::L2; m2 += C::TPL) {
+#pragma unroll
+    for (int j = 0; j < C::JA; ++j) {
+        const int m2 = t + C::T * j;
         float re[C::L1], im[C::L1];
 #pragma unroll
         for (int m1 = 0; m1 < C::L1; ++m1) {
@@ -106,80 +124,84 @@ __device__ __forceinline__ void step_a(const float2 *src, float2 *dst, const flo
             im[m1] = v.y;
         }
         FFT<C::L1>::run(re, im);
+        A[m2] = make_float2(re[0], im[0]);
 #pragma unroll
-        for (int k1 = 0; k1 < C::L1; ++k1) {
-            // exp(-2 pi i m2 k1 / L) = exp(-i pi (8 m2 k1) / (2N))
-            const float2 t1 = k1 == 0 ? make_float2(1.f, 0.f) : twq<N>(tw, 8 * m2 * k1);
-            dst[k1 * (C::L2 + 1) + m2] = cmul(make_float2(re[k1], im[k1]), t1);
-        }
+        for (int k1 = 1; k1 < C::L1; ++k1)
+            A[k1 * (C::L2 + 1) + m2] = cmul(make_float2(re[k1], im[k1]), ta[k1 * C::L2 + m2]);
     }
 }
 
-// Step C for task k1: FFT of length L2 of A[k1][*]; Z_{k1 + L1 k2} in re/im.
+// Step C for this thread: for k1 = t + T j, the length-L2 FFT of A[k1][*];
+// Z_{k1 + L1 k2} lands in zr[j][k2], zi[j][k2].
 template <int N>
-__device__ __forceinline__ void step_c(const float2 *A, int k1, float (&re)[LineCfg<N>::L2], float (&im)[LineCfg<N>::L2])
+__device__ __forceinline__ void four_step_c(const float2 *A, int t, float (&zr)[LineCfg<N>::JC][LineCfg<N>::L2],
+                                            float (&zi)[LineCfg<N>::JC][LineCfg<N>::L2])
 {
     using C = LineCfg<N>;
 #pragma unroll
-    for (int m2 = 0; m2 < C::L2; ++m2) {
-        const float2 v = A[k1 * (C::L2 + 1) + m2];
-        re[m2] = v.x;
-        im[m2] = v.y;
+    for (int j = 0; j < C::JC; ++j) {
+        const int k1 = t + C::T * j;
+#pragma unroll
+        for (int m2 = 0; m2 < C::L2; ++m2) {
+            const float2 v = A[k1 * (C::L2 + 1) + m2];
+            zr[j][m2] = v.x;
+            zi[j][m2] = v.y;
+        }
+        FFT<C::L2>::run(zr[j], zi[j]);
     }
-    FFT<C::L2>::run(re, im);
 }
 
 // Forward DCT-II of one line.  On entry `line` holds z (Makhoul order, as
-// float2); on exit y_k * s_k in natural order.
+// float2); on exit y_k * s_k in natural order.  Z_k and its split partner
+// Z_{L-k} sit in registers of threads t and T - t of the line (the same
+// warp), so the partner comes by shuffle.
 template <int N>
-__device__ __forceinline__ void line_forward(float *line, float *scr, const float2 *tw, int t, AxisScale s)
+__device__ __forceinline__ void line_forward(float *line, float *scr, const float2 *ta, const float4 *ts, int t,
+                                             int lane, AxisScale s)
 {
     using C = LineCfg<N>;
     float2 *z = reinterpret_cast<float2 *>(line);
     float2 *A = reinterpret_cast<float2 *>(scr);
-    step_a<N>(z, A, tw, t);  // line -> scratch
+    four_step_a<N>(z, A, ta, t);
     __syncwarp();
-    if (t < C::L1) {  // scratch -> Z (line, natural order)
-        float re[C::L2], im[C::L2];
-        step_c<N>(A, t, re, im);
+    float zr[C::JC][C::L2], zi[C::JC][C::L2];
+    four_step_c<N>(A, t, zr, zi);
+    // the line buffer is free (z was consumed by step A before the barrier)
+    const int src = lane - t + (C::T - t) % C::T;
 #pragma unroll
-        for (int k2 = 0; k2 < C::L2; ++k2) z[t + C::L1 * k2] = make_float2(re[k2], im[k2]);
-    }
-    __syncwarp();
-    // split: every lane reads its pairs (Z_k, Z_{L-k}) first, then writes y over them
-    float2 za[C::PAIRS], zb[C::PAIRS];
+    for (int j = 0; j < C::JC; ++j) {
 #pragma unroll
-    for (int q = 0; q < C::PAIRS; ++q) {
-        const int k = t + q * C::TPL;
-        if (k <= C::L / 2) {
-            za[q] = z[k];
-            zb[q] = z[k == 0 ? 0 : C::L - k];
-        }
-    }
-    __syncwarp();
-#pragma unroll
-    for (int q = 0; q < C::PAIRS; ++q) {
-        const int k = t + q * C::TPL;
-        if (k > C::L / 2) continue;
-        if (k == 0) {
-            const float2 z0 = za[q];
-            line[0] = (z0.x + z0.y) * s.s0;
-            line[C::L] = (z0.x - z0.y) * 0.70710678118654752f * s.s1;
-            continue;
-        }
-        const float2 a = za[q], c = zb[q];
-        const float2 E = make_float2(0.5f * (a.x + c.x), 0.5f * (a.y - c.y));
-        const float2 O = make_float2(0.5f * (a.y + c.y), 0.5f * (c.x - a.x));
-        const float2 P = cmul(twq<N>(tw, 4 * k), O);  // exp(-2 pi i k / N) O_k
-        const float2 V = make_float2(E.x + P.x, E.y + P.y);
-        const float2 WV = cmul(twq<N>(tw, k), V);      // exp(-i pi k / (2N)) V_k
-        line[k] = WV.x * s.s1;
-        line[N - k] = -WV.y * s.s1;
-        if (k != C::L - k) {
-            const float2 V2 = make_float2(E.x - P.x, -(E.y - P.y));  // V_{L-k} = conj(E - P)
-            const float2 WV2 = cmul(twq<N>(tw, C::L - k), V2);
-            line[C::L - k] = WV2.x * s.s1;
-            line[C::L + k] = -WV2.y * s.s1;
+        for (int k2 = 0; k2 < C::L2; ++k2) {
+            // partner Z_{L-k}: thread T - t, slot (JC - 1 - j, L2 - 1 - k2); for
+            // t = 0 the partner is this thread's own (JC - j) % JC or, for j = 0,
+            // slot (0, (L2 - k2) % L2)
+            float cr = __shfl_sync(0xffffffffu, zr[C::JC - 1 - j][C::L2 - 1 - k2], src);
+            float ci = __shfl_sync(0xffffffffu, zi[C::JC - 1 - j][C::L2 - 1 - k2], src);
+            constexpr int j0 = 0;
+            if (t == 0) {
+                if (j == 0) {
+                    cr = zr[j0][(C::L2 - k2) % C::L2];
+                    ci = zi[j0][(C::L2 - k2) % C::L2];
+                } else {
+                    cr = zr[(C::JC - j) % C::JC][C::L2 - 1 - k2];
+                    ci = zi[(C::JC - j) % C::JC][C::L2 - 1 - k2];
+                }
+            }
+            const int k = t + C::T * j + C::L1 * k2;
+            const float ar = zr[j][k2], ai = zi[j][k2];
+            if (k == 0) {
+                line[0] = (ar + ai) * s.s0;
+                line[C::L] = (ar - ai) * 0.70710678118654752f * s.s1;
+            } else {
+                const float4 w = ts[k];  // (exp(-2 pi i k / N), exp(-i pi k / (2N)))
+                const float2 E = make_float2(0.5f * (ar + cr), 0.5f * (ai - ci));
+                const float2 O = make_float2(0.5f * (ai + ci), 0.5f * (cr - ar));
+                const float2 P = cmul(make_float2(w.x, w.y), O);
+                const float2 V = make_float2(E.x + P.x, E.y + P.y);
+                const float2 WV = cmul(make_float2(w.z, w.w), V);
+                line[k] = WV.x * s.s1;
+                line[N - k] = -WV.y * s.s1;
+            }
         }
     }
     __syncwarp();
@@ -188,51 +210,49 @@ __device__ __forceinline__ void line_forward(float *line, float *scr, const floa
 // Inverse DCT-III of one line.  On entry `line` holds y in natural order; on
 // exit x (natural order).  Input scales s_k applied on entry.
 template <int N>
-__device__ __forceinline__ void line_inverse(float *line, float *scr, const float2 *tw, int t, AxisScale s)
+__device__ __forceinline__ void line_inverse(float *line, float *scr, const float2 *ta, const float4 *ts, int t,
+                                             AxisScale s)
 {
     using C = LineCfg<N>;
     float2 *Zc = reinterpret_cast<float2 *>(scr);  // conj(Z), natural order
-    // y -> conj(Z) (scratch)
-    for (int k = t; k <= C::L / 2; k += C::TPL) {
-        if (k == 0) {
-            const float v0 = 2.0f * line[0] * s.s0;  // factor 2 carries 1/L
-            const float vl = 1.41421356237309505f * line[C::L] * s.s1;
-            const float E0 = 0.5f * (v0 + vl), O0 = 0.5f * (v0 - vl);
-            Zc[0] = make_float2(E0, -O0);  // Z_0 = E0 + i O0
-            continue;
-        }
-        const float yk = line[k] * s.s1, ynk = line[N - k] * s.s1;
-        const float ylk = line[C::L - k] * s.s1, ylpk = line[C::L + k] * s.s1;
-        // V_k = conj(W_k) (y_k - i y_{N-k}),  V_{L-k} likewise
-        const float2 Vk = cmul(conjf2(twq<N>(tw, k)), make_float2(yk, -ynk));
-        const float2 Vl = cmul(conjf2(twq<N>(tw, C::L - k)), make_float2(ylk, -ylpk));
-        const float2 E = make_float2(0.5f * (Vk.x + Vl.x), 0.5f * (Vk.y - Vl.y));  // (V_k + conj V_{L-k}) / 2
-        const float2 D = make_float2(0.5f * (Vk.x - Vl.x), 0.5f * (Vk.y + Vl.y));  // (V_k - conj V_{L-k}) / 2
-        const float2 O = cmul(conjf2(twq<N>(tw, 4 * k)), D);                        // / exp(-2 pi i k / N)
-        // Z_k = E + i O;  Z_{L-k} = conj(E) + i conj(O)
-        const float2 Zk = make_float2(E.x - O.y, E.y + O.x);
-        Zc[k] = conjf2(Zk);
-        if (k != C::L - k) {
-            const float2 Zl = make_float2(E.x + O.y, -E.y + O.x);
-            Zc[C::L - k] = conjf2(Zl);
-        }
-    }
-    __syncwarp();
-    // forward four-step FFT of conj(Z): step A scratch -> line (padded)
-    float2 *A = reinterpret_cast<float2 *>(line);
-    step_a<N>(Zc, A, tw, t);
-    __syncwarp();
-    // step C: conj of the result is z = IFFT(Z) (unnormalized); then v from z, x from v
-    float re[C::L2], im[C::L2];
-    const bool act = t < C::L1;
-    if (act) step_c<N>(A, t, re, im);
-    __syncwarp();  // all of A read before x overwrites the line
-    if (act) {
+    // y -> conj(Z): each k from y_k, y_{N-k}, y_{L-k}, y_{L+k}
+#pragma unroll
+    for (int j = 0; j < C::JC; ++j) {
 #pragma unroll
         for (int k2 = 0; k2 < C::L2; ++k2) {
-            const int m = t + C::L1 * k2;
+            const int k = t + C::T * j + C::L1 * k2;
+            if (k == 0) {
+                const float v0 = 2.0f * line[0] * s.s0;  // factor 2 carries 1/L
+                const float vl = 1.41421356237309505f * line[C::L] * s.s1;
+                Zc[0] = make_float2(0.5f * (v0 + vl), -0.5f * (v0 - vl));
+            } else {
+                const float yk = line[k] * s.s1, ynk = line[N - k] * s.s1;
+                const float ylk = line[C::L - k] * s.s1, ylpk = line[C::L + k] * s.s1;
+                const float4 w = ts[k], wl = ts[C::L - k];
+                // V_k = conj(W_k) (y_k - i y_{N-k}), V_{L-k} likewise
+                const float2 Vk = cmulc(make_float2(yk, -ynk), make_float2(w.z, w.w));
+                const float2 Vl = cmulc(make_float2(ylk, -ylpk), make_float2(wl.z, wl.w));
+                const float2 E = make_float2(0.5f * (Vk.x + Vl.x), 0.5f * (Vk.y - Vl.y));
+                const float2 D = make_float2(0.5f * (Vk.x - Vl.x), 0.5f * (Vk.y + Vl.y));
+                const float2 O = cmulc(D, make_float2(w.x, w.y));  // / exp(-2 pi i k / N)
+                Zc[k] = make_float2(E.x - O.y, -(E.y + O.x));      // conj(E + i O)
+            }
+        }
+    }
+    __syncwarp();  // every read of y done before A overwrites the line
+    float2 *A = reinterpret_cast<float2 *>(line);
+    four_step_a<N>(Zc, A, ta, t);
+    __syncwarp();
+    float rr[C::JC][C::L2], ri[C::JC][C::L2];
+    four_step_c<N>(A, t, rr, ri);
+    __syncwarp();  // all of A read before x overwrites the line
+#pragma unroll
+    for (int j = 0; j < C::JC; ++j) {
+#pragma unroll
+        for (int k2 = 0; k2 < C::L2; ++k2) {
+            const int m = t + C::T * j + C::L1 * k2;
             // z_m = conj(result); v_{2m} = Re z_m, v_{2m+1} = Im z_m
-            const float v_even = re[k2], v_odd = -im[k2];
+            const float v_even = rr[j][k2], v_odd = -ri[j][k2];
             // x_{2i} = v_i (i < L), x_{2i+1} = v_{N-1-i}
             const int i0 = 2 * m, i1 = 2 * m + 1;
             if (i0 < C::L) line[2 * i0] = v_even; else line[2 * (N - 1 - i0) + 1] = v_even;
@@ -250,7 +270,7 @@ struct LinesParams {
     int npanels;
     AxisScale sc;        // forward: output scales; inverse: input scales; round trip: E^2
     const long long *src_off, *dst_off;  // indexed arrays (element offsets), or null
-    const float2 *tw;    // exp(-i pi r / (2N)), r = 0..N, generated in FP64 at plan time
+    const float2 *tw;    // the plan's tables for N (lines_gen_table), generated in FP64
 };
 
 template <int N, int DIR>
@@ -260,14 +280,15 @@ __global__ void __launch_bounds__(LineCfg<N>::THREADS) k_lines(const LinesParams
     extern __shared__ __align__(16) float lsm[];
     float *panel = lsm;
     float *scr_all = panel + C::PR * C::PP;
-    float2 *tw = reinterpret_cast<float2 *>(scr_all + C::NW * C::LPW * C::SCR);
+    float2 *ta = reinterpret_cast<float2 *>(scr_all + C::LPR * C::SCR);
+    const float4 *ts = reinterpret_cast<const float4 *>(ta + C::L);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int sub = lane / C::TPL, t = lane % C::TPL;
+    const int sub = lane / C::T, t = lane % C::T;
 
     pdl_launch_dependents();
     pdl_wait_prerequisites();
-    // quarter-wave twiddles exp(-i pi r / (2N)), r = 0 .. N, from the plan's table
-    for (int r = tid; r < C::TWN; r += C::THREADS) tw[r] = p.tw[r];
+    // the plan's twiddle tables (FP64-generated): step A, then the split
+    for (int r = tid; r < C::TAB_F2; r += C::THREADS) ta[r] = p.tw[r];
     __syncthreads();
 
     for (int pn = blockIdx.x; pn < p.npanels; pn += gridDim.x) {
@@ -295,29 +316,24 @@ __global__ void __launch_bounds__(LineCfg<N>::THREADS) k_lines(const LinesParams
         // ---- transform every line of the panel
 #pragma unroll 1
         for (int rd = 0; rd < C::ROUNDS; ++rd) {
-            // The LPW lines a warp transforms together sit DELTA = 16 / LPW rows
-            // apart: with a row pitch of 2 mod 4 floats their shared-memory
-            // accesses then fall into disjoint banks.
-            const int grp = rd * C::NW + warp;
-            const int l = (C::LPW == 1) ? grp : (grp / C::DELTA) * 16 + (grp % C::DELTA) + sub * C::DELTA;
-            float *line = panel + l * C::PP;
+            float *line = panel + line_row<N>(rd * C::NW + warp, sub) * C::PP;
             float *scr = scr_all + (warp * C::LPW + sub) * C::SCR;
             if constexpr (DIR == DIR_FWD) {
-                line_forward<N>(line, scr, tw, t, p.sc);
+                line_forward<N>(line, scr, ta, ts, t, lane, p.sc);
             } else if constexpr (DIR == DIR_INV) {
-                line_inverse<N>(line, scr, tw, t, p.sc);
+                line_inverse<N>(line, scr, ta, ts, t, p.sc);
             } else {
                 // round trip: forward core, E^2 correction, adjoint core
                 const AxisScale one = {1.0f, 1.0f};
-                line_forward<N>(line, scr, tw, t, p.sc);
-                line_inverse<N>(line, scr, tw, t, one);
+                line_forward<N>(line, scr, ta, ts, t, lane, p.sc);
+                line_inverse<N>(line, scr, ta, ts, t, one);
             }
         }
         __syncthreads();
         // ---- transposed store: dst[b][k][r] with rows r0.. (same array b)
         float *dstb = p.dst_off ? p.dst + p.dst_off[b] : p.dst + b * (long long)N * p.rows;
         // a warp instruction covers SEG rows x (32 / SEG) columns; with a row
-        // pitch of 2 mod 4 floats, 16 rows x 2 columns touch all 32 banks
+        // pitch of 2 mod 32 floats they touch all 32 banks
         for (int i = tid; i < C::PR * N; i += C::THREADS) {
             const int l = i % C::SEG, cj = i / C::SEG;
             const int k = cj % N, lb = (cj / N) * C::SEG;
@@ -380,19 +396,52 @@ static cudaError_t lines_dir(Dir dir, const LinesParams &p, cudaStream_t s)
     }
 }
 
-__global__ void k_gen_line_tw(float2 *t, int n)
+// The line engine's tables for length n (L = n / 2 = L1 * L2), in FP64 with
+// the angle reduced exactly in integers:
+//  [0, L):   exp(-2 pi i m2 k1 / L) at index k1 * L2 + m2 (step A);
+//  [L, 3L):  for k < L the float4 (exp(-2 pi i k / n), exp(-i pi k / (2n)))
+//            (the split between the half-length FFT and the DCT).
+__global__ void k_gen_line_tw(float2 *t, int n, int l1)
 {
+    const int L = n / 2, l2 = L / l1;
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r > n) return;
-    // angle pi r / (2n) in [0, pi/2], evaluated in FP64
-    const double a = (double)r / (2.0 * (double)n);
-    t[r] = make_float2((float)cospi(a), (float)(r == n ? -1.0 : -sinpi(a)));
-    if (r == n) t[r].x = 0.0f;
+    if (r < L) {
+        const int k1 = r / l2, m2 = r % l2;
+        const long long m = ((long long)m2 * k1) % L;  // angle -2 pi m / L
+        double sn, cs;
+        sincospi(-2.0 * (double)m / (double)L, &sn, &cs);
+        t[r] = make_float2((float)cs, (float)sn);
+    } else if (r < 2 * L) {
+        const int k = r - L;
+        double s1, c1, s2, c2;
+        sincospi(-2.0 * (double)k / (double)n, &s1, &c1);
+        sincospi(-(double)k / (2.0 * (double)n), &s2, &c2);
+        float4 *q = reinterpret_cast<float4 *>(t + L);
+        q[k] = make_float4((float)c1, (float)s1, (float)c2, (float)s2);
+    }
+}
+
+static int line_l1(int n)
+{
+    switch (n) {
+        case 64: return LineCfg<64>::L1;
+        case 128: return LineCfg<128>::L1;
+        case 256: return LineCfg<256>::L1;
+        case 512: return LineCfg<512>::L1;
+        case 1024: return LineCfg<1024>::L1;
+        case 2048: return LineCfg<2048>::L1;
+        case 4096: return LineCfg<4096>::L1;
+        case 768: return LineCfg<768>::L1;
+        default: return 0;
+    }
 }
 
 cudaError_t lines_gen_table(float2 *dst, int n, cudaStream_t s)
 {
-    k_gen_line_tw<<<(n + 1 + 255) / 256, 256, 0, s>>>(dst, n);
+    const int l1 = line_l1(n);
+    if (l1 == 0) return cudaErrorInvalidValue;
+    const int total = n;  // L step-A entries + L split entries (float4, two float2 each)
+    k_gen_line_tw<<<(total + 255) / 256, 256, 0, s>>>(dst, n, l1);
     return cudaGetLastError();
 }
 
