@@ -76,13 +76,14 @@ struct LineCfg {
     static constexpr int PP = pitch(A_FLOATS > N ? A_FLOATS : N, 2);
     // per-line scratch: the lines of one warp 2T banks apart
     static constexpr int SCR = pitch(A_FLOATS > N ? A_FLOATS : N, (2 * T) % 32);
-    static constexpr int SEG = PR < 16 ? PR : 16;  // rows per transposed-store segment
+    static constexpr int SEG = PR < 16 ? PR : 16;  // rows per transposed-store segment (a multiple of 4)
     static constexpr int TAB_F2 = 3 * L;           // L step-A twiddles, then L float4 split twiddles
     static constexpr size_t SMEM = (size_t)PR * PP * 4 + (size_t)LPR * SCR * 4 + (size_t)TAB_F2 * 8;
     static_assert(L1 * L2 == L && L1 % T == 0 && L2 % T == 0 && 32 % T == 0, "split");
     static_assert(ROUNDS >= 1 && ROUNDS * LPR == PR, "panel");
     static_assert(T >= 16 || PR % 32 == 0, "line spacing");
     static_assert(JC * L2 <= 64, "registers held through the split");
+    static_assert(SEG % 4 == 0 && THREADS % (SEG / 4) == 0 && N % (THREADS / (SEG / 4)) == 0, "store mapping");
     static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
@@ -296,20 +297,35 @@ __global__ void __launch_bounds__(LineCfg<N>::THREADS) k_lines(const LinesParams
         const long long b = r0 / p.rows;             // its array (panels never straddle two)
         const int rr = (int)(r0 - b * p.rows);
         const float *srcb = p.src_off ? p.src + p.src_off[b] : p.src + b * (long long)N * p.rows;
-        // ---- load the panel (rows r0 .. r0+PR-1), coalesced 16-byte reads
-        constexpr int V4 = N / 4;
-        for (int i = tid; i < C::PR * V4; i += C::THREADS) {
-            const int l = i / V4, q = i % V4;
-            const float4 v = __ldg(reinterpret_cast<const float4 *>(srcb + (long long)(rr + l) * N) + q);
-            float *row = panel + l * C::PP;
-            if constexpr (DIR == DIR_INV) {
-                reinterpret_cast<float2 *>(row)[2 * q] = make_float2(v.x, v.y);
-                reinterpret_cast<float2 *>(row)[2 * q + 1] = make_float2(v.z, v.w);
-            } else {
-                // Makhoul order: (v_{2q}, v_{2q+1}) = (x_{4q}, x_{4q+2}),
-                // (v_{N-2-2q}, v_{N-1-2q}) = (x_{4q+3}, x_{4q+1})
-                reinterpret_cast<float2 *>(row)[q] = make_float2(v.x, v.z);
-                reinterpret_cast<float2 *>(row)[N / 2 - 1 - q] = make_float2(v.w, v.y);
+        // ---- load the panel (rows r0 .. r0+PR-1), coalesced 16-byte reads,
+        // in batches of up to 8 per thread so that many loads are in flight
+        // before the first shared-memory write
+        {
+            constexpr int V4 = N / 4;
+            constexpr int ITER = C::PR * V4 / C::THREADS;
+            constexpr int NB = ITER < 8 ? ITER : 8;
+            static_assert(ITER % NB == 0, "load batches");
+            const float4 *src4 = reinterpret_cast<const float4 *>(srcb + (long long)rr * N);
+#pragma unroll 1
+            for (int i0 = 0; i0 < ITER; i0 += NB) {
+                float4 v[NB];
+#pragma unroll
+                for (int u = 0; u < NB; ++u) v[u] = __ldg(src4 + tid + (i0 + u) * C::THREADS);
+#pragma unroll
+                for (int u = 0; u < NB; ++u) {
+                    const int i = tid + (i0 + u) * C::THREADS;
+                    const int l = i / V4, q = i - l * V4;
+                    float2 *row = reinterpret_cast<float2 *>(panel + l * C::PP);
+                    if constexpr (DIR == DIR_INV) {
+                        row[2 * q] = make_float2(v[u].x, v[u].y);
+                        row[2 * q + 1] = make_float2(v[u].z, v[u].w);
+                    } else {
+                        // Makhoul order: (v_{2q}, v_{2q+1}) = (x_{4q}, x_{4q+2}),
+                        // (v_{N-2-2q}, v_{N-1-2q}) = (x_{4q+3}, x_{4q+1})
+                        row[q] = make_float2(v[u].x, v[u].z);
+                        row[N / 2 - 1 - q] = make_float2(v[u].w, v[u].y);
+                    }
+                }
             }
         }
         __syncthreads();
@@ -330,14 +346,29 @@ __global__ void __launch_bounds__(LineCfg<N>::THREADS) k_lines(const LinesParams
             }
         }
         __syncthreads();
-        // ---- transposed store: dst[b][k][r] with rows r0.. (same array b)
-        float *dstb = p.dst_off ? p.dst + p.dst_off[b] : p.dst + b * (long long)N * p.rows;
-        // a warp instruction covers SEG rows x (32 / SEG) columns; with a row
-        // pitch of 2 mod 32 floats they touch all 32 banks
-        for (int i = tid; i < C::PR * N; i += C::THREADS) {
-            const int l = i % C::SEG, cj = i / C::SEG;
-            const int k = cj % N, lb = (cj / N) * C::SEG;
-            dstb[(long long)k * p.rows + rr + lb + l] = panel[(lb + l) * C::PP + k];
+        // ---- transposed store: dst[b][k][r] with rows r0.. (same array b).
+        // A thread writes 4 consecutive rows of one column k as one 16-byte
+        // store; a warp instruction covers SEG rows x (128 / SEG) columns, and
+        // with a row pitch of 2 mod 32 floats its shared-memory reads touch
+        // all 32 banks.
+        {
+            float *dstb = p.dst_off ? p.dst + p.dst_off[b] : p.dst + b * (long long)N * p.rows;
+            constexpr int SQ = C::SEG / 4;          // row quads per segment
+            constexpr int KPI = C::THREADS / SQ;    // columns per step
+            const int qd = tid % SQ, kk = tid / SQ;
+            float *g = dstb + (long long)kk * p.rows + rr + 4 * qd;
+            const long long gstep = (long long)KPI * p.rows;
+#pragma unroll 1
+            for (int lb = 0; lb < C::PR; lb += C::SEG) {
+                const float *sp = panel + (lb + 4 * qd) * C::PP + kk;
+                float *gp = g + lb;
+#pragma unroll 4
+                for (int k = kk; k < N; k += KPI) {
+                    *reinterpret_cast<float4 *>(gp) = make_float4(sp[0], sp[C::PP], sp[2 * C::PP], sp[3 * C::PP]);
+                    sp += KPI;
+                    gp += gstep;
+                }
+            }
         }
         __syncthreads();
     }
