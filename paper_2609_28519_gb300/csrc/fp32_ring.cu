@@ -350,6 +350,168 @@ __device__ __forceinline__ void ring_cols(char *slot, int gt, int bar, AxisScale
     }
 }
 
+// ---------------------------------------------------------------- square arrays
+// For h = w the two passes run in one loop, so that the 1D cores (the largest
+// part of the code) exist once: pass 0 takes rows, pass 1 columns.  Same
+// arithmetic, layouts and barriers as ring_rows / ring_cols.
+template <int N, int DIR>
+__device__ __forceinline__ void ring_square(char *slot, int gt, int bar, const DirScales &sc)
+{
+    using C = RingCfg<N, N>;
+    constexpr int BB = C::BOX_BYTES;
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+        const AxisScale s = pass ? sc.h : sc.w;
+        if constexpr (N == 64) {
+            // one thread per line; row r (pass 0) or column c (pass 1), in place
+            float x[64];
+            if (pass == 0) {
+                const RowView rv(gt);
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    const float4 t = at<float4>(slot, (k >> 3) * BB + rv.o[k & 7]);
+                    x[4 * k] = t.x; x[4 * k + 1] = t.y; x[4 * k + 2] = t.z; x[4 * k + 3] = t.w;
+                }
+            } else {
+                const ColView<N> cv(gt);
+#pragma unroll
+                for (int i = 0; i < 64; ++i) x[i] = at<float>(slot, i * 128 + cv.o[i & 7]);
+            }
+            line_op<64, DIR>(x, s);
+            if (pass == 0) {
+                const RowView rv(gt);
+#pragma unroll
+                for (int k = 0; k < 16; ++k)
+                    at<float4>(slot, (k >> 3) * BB + rv.o[k & 7]) =
+                        make_float4(x[4 * k], x[4 * k + 1], x[4 * k + 2], x[4 * k + 3]);
+            } else {
+                const ColView<N> cv(gt);
+#pragma unroll
+                for (int i = 0; i < 64; ++i) at<float>(slot, i * 128 + cv.o[i & 7]) = x[i];
+            }
+        } else {
+            // two threads (roles) per 128-point line
+            const int role = gt / N;  // warp-uniform
+            const int r = gt - role * N;  // row (pass 0) or logical column (pass 1)
+            float v[64];
+            if (pass == 0) {
+                const RowView rv(r);
+                if constexpr (DIR == DIR_INV) {
+                    if (role == 0) {
+#pragma unroll
+                        for (int k = 0; k < 32; ++k) {
+                            const float4 t = at<float4>(slot, (k >> 3) * BB + rv.o[k & 7]);
+                            v[2 * k] = t.x; v[2 * k + 1] = t.z;
+                        }
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 32; ++k) {
+                            const float4 t = at<float4>(slot, (k >> 3) * BB + rv.o[k & 7]);
+                            v[2 * k] = t.y; v[2 * k + 1] = t.w;
+                        }
+                    }
+                } else {
+                    const float sg = role ? -1.0f : 1.0f;
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        const float4 a = at<float4>(slot, (k >> 3) * BB + rv.o[k & 7]);
+                        const float4 b = at<float4>(slot, ((31 - k) >> 3) * BB + rv.o[(31 - k) & 7]);
+                        v[4 * k] = fmaf(sg, b.w, a.x);
+                        v[4 * k + 1] = fmaf(sg, b.z, a.y);
+                        v[4 * k + 2] = fmaf(sg, b.y, a.z);
+                        v[4 * k + 3] = fmaf(sg, b.x, a.w);
+                    }
+                }
+            } else {
+                const ColView<N> src(ring_colpos<N, DIR>(r));
+                if constexpr (DIR == DIR_INV) {
+                    if (role == 0) {
+#pragma unroll
+                        for (int m = 0; m < 64; ++m) v[m] = at<float>(slot, 2 * m * 128 + src.o[(2 * m) & 7]);
+                    } else {
+#pragma unroll
+                        for (int m = 0; m < 64; ++m)
+                            v[m] = at<float>(slot, (2 * m + 1) * 128 + src.o[(2 * m + 1) & 7]);
+                    }
+                } else {
+                    const float sg = role ? -1.0f : 1.0f;
+#pragma unroll
+                    for (int i = 0; i < 64; ++i)
+                        v[i] = fmaf(sg, at<float>(slot, (127 - i) * 128 + src.o[(127 - i) & 7]),
+                                    at<float>(slot, i * 128 + src.o[i & 7]));
+                }
+            }
+            if constexpr (DIR == DIR_INV) scale_from<64>(v, role ? s.s1 : s.s0, s.s1);
+            group_sync(bar, C::GT);  // every read of the pass done before anything is overwritten
+            float y[64];
+            role_core<DIR>(role, v, y, s);
+            if (pass == 0) {
+                const RowView rv(r);
+                if (role == 0) {
+#pragma unroll
+                    for (int k = 0; k < 16; ++k)
+                        at<float4>(slot, (k >> 3) * BB + rv.o[k & 7]) =
+                            make_float4(y[4 * k], y[4 * k + 1], y[4 * k + 2], y[4 * k + 3]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        const int kk = 16 + (DIR == DIR_FWD ? ((k + 4) & 15) : k);
+                        at<float4>(slot, (kk >> 3) * BB + rv.o[kk & 7]) =
+                            make_float4(y[4 * k], y[4 * k + 1], y[4 * k + 2], y[4 * k + 3]);
+                    }
+                }
+                if constexpr (DIR != DIR_FWD) {
+                    group_sync(bar, C::GT);
+                    constexpr int TASKS = N * 16;
+#pragma unroll
+                    for (int t = gt; t < TASKS; t += C::GT) {
+                        const int rr = t >> 4, k = t & 15;
+                        const uint32_t oa = sw_chunk<N>(rr, k), ob = sw_chunk<N>(rr, 16 + k);
+                        const float4 a = at<float4>(slot, oa), b = at<float4>(slot, ob);
+                        at<float4>(slot, oa) = make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+                        at<float4>(slot, ob) = make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+                    }
+                }
+            } else {
+                const ColView<N> dst(r);
+                if constexpr (DIR == DIR_FWD) {
+                    if (role == 0) {
+#pragma unroll
+                        for (int m = 0; m < 64; ++m) at<float>(slot, 2 * m * 128 + dst.o[(2 * m) & 7]) = y[m];
+                    } else {
+#pragma unroll
+                        for (int m = 0; m < 64; ++m)
+                            at<float>(slot, (2 * m + 1) * 128 + dst.o[(2 * m + 1) & 7]) = y[m];
+                    }
+                } else {
+                    if (role == 0) {
+#pragma unroll
+                        for (int j = 0; j < 64; ++j) at<float>(slot, j * 128 + dst.o[j & 7]) = y[j];
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 64; ++j) at<float>(slot, (127 - j) * 128 + dst.o[(127 - j) & 7]) = y[j];
+                    }
+                    group_sync(bar, C::GT);
+                    auto comb = [&](int j) {
+                        const uint32_t oa = j * 128 + dst.o[j & 7], ob = (127 - j) * 128 + dst.o[(127 - j) & 7];
+                        const float a = at<float>(slot, oa), b = at<float>(slot, ob);
+                        at<float>(slot, oa) = a + b;
+                        at<float>(slot, ob) = a - b;
+                    };
+                    if (role == 0) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) comb(j);
+                    } else {
+#pragma unroll
+                        for (int j = 32; j < 64; ++j) comb(j);
+                    }
+                }
+            }
+        }
+        group_sync(bar, C::GT);
+    }
+}
+
 // ---------------------------------------------------------------- kernel
 struct RingParams {
     CUtensorMap map_in, map_out;  // contiguous and tiled batches (TMA)
@@ -512,11 +674,17 @@ __global__ void __launch_bounds__(RingCfg<H, W>::THREADS, 1) k_ring(const __grid
             break;
         }
         char *slot = smem + s * C::SLOT_BYTES;
-        ring_rows<H, W, DIR>(slot, gt, bar, p.sc.w);
-        group_sync(bar, C::GT);
-        ring_cols<H, W, DIR>(slot, gt, bar, p.sc.h);
-        fence_proxy_async_smem();  // the TMA store reads the slot through the async proxy
-        group_sync(bar, C::GT);
+        if constexpr (H == W) {
+            ring_square<H, DIR>(slot, gt, bar, p.sc);  // ends with a group barrier
+            fence_proxy_async_smem();  // the TMA store reads the slot through the async proxy
+            group_sync(bar, C::GT);
+        } else {
+            ring_rows<H, W, DIR>(slot, gt, bar, p.sc.w);
+            group_sync(bar, C::GT);
+            ring_cols<H, W, DIR>(slot, gt, bar, p.sc.h);
+            fence_proxy_async_smem();  // the TMA store reads the slot through the async proxy
+            group_sync(bar, C::GT);
+        }
         if (gt == 0) mbar_arrive(&done[s]);
     }
 }
