@@ -158,6 +158,13 @@ __device__ __forceinline__ void scale_from(float (&x)[N], float first, float res
     for (int k = 1; k < N; ++k) x[k] *= rest;
 }
 
+// Role and line of a group thread when 128-point lines are shared by two
+// threads: warps alternate roles, so that each SM sub-partition (warps are
+// dealt to the four sub-partitions round robin) runs one role's code only,
+// and the 32 lanes of a warp take 32 consecutive lines.
+__device__ __forceinline__ int role_of(int gt) { return (gt >> 5) & 1; }
+__device__ __forceinline__ int line_of(int gt) { return ((gt >> 6) << 5) | (gt & 31); }
+
 // The 64-point core of one role of a 128-point line.  On entry v holds the
 // role's input (forward and round trip: sums or differences; inverse: the
 // even or odd coefficients, already scaled); on exit y holds the role's
@@ -206,8 +213,8 @@ __device__ __forceinline__ void ring_rows(char *slot, int gt, int bar, AxisScale
         for (int k = 0; k < 16; ++k)
             at<float4>(slot, (k >> 3) * BB + rv.o[k & 7]) = make_float4(x[4 * k], x[4 * k + 1], x[4 * k + 2], x[4 * k + 3]);
     } else {
-        const int role = gt / H;  // warp-uniform
-        const int r = gt - role * H;
+        const int role = role_of(gt);
+        const int r = line_of(gt);
         const RowView rv(r);
         float v[64];
         if constexpr (DIR == DIR_INV) {
@@ -288,8 +295,8 @@ __device__ __forceinline__ void ring_cols(char *slot, int gt, int bar, AxisScale
 #pragma unroll
         for (int i = 0; i < 64; ++i) at<float>(slot, i * 128 + dst.o[i & 7]) = x[i];
     } else {
-        const int role = gt / W;  // warp-uniform
-        const int c = gt - role * W;
+        const int role = role_of(gt);
+        const int c = line_of(gt);
         const ColView<H> src(ring_colpos<W, DIR>(c));
         float v[64];
         if constexpr (DIR == DIR_INV) {
@@ -391,8 +398,8 @@ __device__ __forceinline__ void ring_square(char *slot, int gt, int bar, const D
             }
         } else {
             // two threads (roles) per 128-point line
-            const int role = gt / N;  // warp-uniform
-            const int r = gt - role * N;  // row (pass 0) or logical column (pass 1)
+            const int role = role_of(gt);
+            const int r = line_of(gt);  // row (pass 0) or logical column (pass 1)
             float v[64];
             if (pass == 0) {
                 const RowView rv(r);
