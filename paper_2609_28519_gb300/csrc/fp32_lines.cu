@@ -292,43 +292,73 @@ __global__ void __launch_bounds__(LineCfg<N>::THREADS) k_lines(const LinesParams
     for (int r = tid; r < C::TAB_F2; r += C::THREADS) ta[r] = p.tw[r];
     __syncthreads();
 
-    for (int pn = blockIdx.x; pn < p.npanels; pn += gridDim.x) {
+    // The panel's 16-byte chunks, ITER per thread; for lines up to 2048 points
+    // the next panel's chunks are loaded into registers while the current
+    // panel is transformed, so the global-load latency overlaps the work.
+    constexpr int V4 = N / 4;
+    constexpr int ITER = C::PR * V4 / C::THREADS;
+    constexpr bool PREFETCH = N <= 2048;
+    constexpr int NB = PREFETCH ? ITER : (ITER < 8 ? ITER : 8);
+    static_assert(ITER * C::THREADS == C::PR * V4 && ITER % NB == 0, "load batches");
+    auto panel_src = [&](int pn, long long &b, int &rr) -> const float4 * {
         const long long r0 = (long long)pn * C::PR;  // first global row of the panel
-        const long long b = r0 / p.rows;             // its array (panels never straddle two)
-        const int rr = (int)(r0 - b * p.rows);
+        b = r0 / p.rows;                             // its array (panels never straddle two)
+        rr = (int)(r0 - b * p.rows);
         const float *srcb = p.src_off ? p.src + p.src_off[b] : p.src + b * (long long)N * p.rows;
-        // ---- load the panel (rows r0 .. r0+PR-1), coalesced 16-byte reads,
-        // in batches of up to 8 per thread so that many loads are in flight
-        // before the first shared-memory write
-        {
-            constexpr int V4 = N / 4;
-            constexpr int ITER = C::PR * V4 / C::THREADS;
-            constexpr int NB = ITER < 8 ? ITER : 8;
-            static_assert(ITER % NB == 0, "load batches");
-            const float4 *src4 = reinterpret_cast<const float4 *>(srcb + (long long)rr * N);
+        return reinterpret_cast<const float4 *>(srcb + (long long)rr * N);
+    };
+    // chunk u of this thread -> the panel row (Makhoul order for the forward)
+    auto put = [&](int i, const float4 v) {
+        const int l = i / V4, q = i - l * V4;
+        float2 *row = reinterpret_cast<float2 *>(panel + l * C::PP);
+        if constexpr (DIR == DIR_INV) {
+            row[2 * q] = make_float2(v.x, v.y);
+            row[2 * q + 1] = make_float2(v.z, v.w);
+        } else {
+            // Makhoul order: (v_{2q}, v_{2q+1}) = (x_{4q}, x_{4q+2}),
+            // (v_{N-2-2q}, v_{N-1-2q}) = (x_{4q+3}, x_{4q+1})
+            row[q] = make_float2(v.x, v.z);
+            row[N / 2 - 1 - q] = make_float2(v.w, v.y);
+        }
+    };
+    float4 pre[NB];
+    if constexpr (PREFETCH) {
+        if (blockIdx.x < (unsigned)p.npanels) {
+            long long b0;
+            int r00;
+            const float4 *src4 = panel_src(blockIdx.x, b0, r00);
+#pragma unroll
+            for (int u = 0; u < NB; ++u) pre[u] = __ldg(src4 + tid + u * C::THREADS);
+        }
+    }
+
+    for (int pn = blockIdx.x; pn < p.npanels; pn += gridDim.x) {
+        long long b;
+        int rr;
+        const float4 *src4 = panel_src(pn, b, rr);
+        // ---- the panel (rows of this array), coalesced 16-byte reads
+        if constexpr (PREFETCH) {
+#pragma unroll
+            for (int u = 0; u < NB; ++u) put(tid + u * C::THREADS, pre[u]);
+            __syncthreads();
+            const int nx = pn + (int)gridDim.x;
+            if (nx < p.npanels) {
+                long long b1;
+                int r1;
+                const float4 *n4 = panel_src(nx, b1, r1);
+#pragma unroll
+                for (int u = 0; u < NB; ++u) pre[u] = __ldg(n4 + tid + u * C::THREADS);
+            }
+        } else {
 #pragma unroll 1
             for (int i0 = 0; i0 < ITER; i0 += NB) {
-                float4 v[NB];
 #pragma unroll
-                for (int u = 0; u < NB; ++u) v[u] = __ldg(src4 + tid + (i0 + u) * C::THREADS);
+                for (int u = 0; u < NB; ++u) pre[u] = __ldg(src4 + tid + (i0 + u) * C::THREADS);
 #pragma unroll
-                for (int u = 0; u < NB; ++u) {
-                    const int i = tid + (i0 + u) * C::THREADS;
-                    const int l = i / V4, q = i - l * V4;
-                    float2 *row = reinterpret_cast<float2 *>(panel + l * C::PP);
-                    if constexpr (DIR == DIR_INV) {
-                        row[2 * q] = make_float2(v[u].x, v[u].y);
-                        row[2 * q + 1] = make_float2(v[u].z, v[u].w);
-                    } else {
-                        // Makhoul order: (v_{2q}, v_{2q+1}) = (x_{4q}, x_{4q+2}),
-                        // (v_{N-2-2q}, v_{N-1-2q}) = (x_{4q+3}, x_{4q+1})
-                        row[q] = make_float2(v[u].x, v[u].z);
-                        row[N / 2 - 1 - q] = make_float2(v[u].w, v[u].y);
-                    }
-                }
+                for (int u = 0; u < NB; ++u) put(tid + (i0 + u) * C::THREADS, pre[u]);
             }
+            __syncthreads();
         }
-        __syncthreads();
         // ---- transform every line of the panel
 #pragma unroll 1
         for (int rd = 0; rd < C::ROUNDS; ++rd) {
