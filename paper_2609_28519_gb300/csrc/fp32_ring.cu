@@ -193,167 +193,156 @@ __device__ __forceinline__ void role_core(int role, const float (&v)[64], float 
     }
 }
 
-// ---------------------------------------------------------------- row pass
+// ---------------------------------------------------------------- rectangles
+// 64 x 128 and 128 x 64: the 128 side's lines are shared by two threads
+// (roles), the 64 side's lines take one thread each; both passes (rows, then
+// columns) run in one loop body around a single call of role_core (role 0 is
+// the whole 64-point transform), so the 1D cores exist once in the code.
 template <int H, int W, int DIR>
-__device__ __forceinline__ void ring_rows(char *slot, int gt, int bar, AxisScale s)
+__device__ __forceinline__ void ring_rect(char *slot, int gt, int bar, const DirScales &sc)
 {
     using C = RingCfg<H, W>;
     constexpr int BB = C::BOX_BYTES;
-    if constexpr (W == 64) {
-        // one thread per row, in place
-        const RowView rv(gt);
-        float x[64];
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            const float4 t = at<float4>(slot, (k >> 3) * BB + rv.o[k & 7]);
-            x[4 * k] = t.x; x[4 * k + 1] = t.y; x[4 * k + 2] = t.z; x[4 * k + 3] = t.w;
-        }
-        line_op<64, DIR>(x, s);
-#pragma unroll
-        for (int k = 0; k < 16; ++k)
-            at<float4>(slot, (k >> 3) * BB + rv.o[k & 7]) = make_float4(x[4 * k], x[4 * k + 1], x[4 * k + 2], x[4 * k + 3]);
-    } else {
-        const int role = role_of(gt);
-        const int r = line_of(gt);
-        const RowView rv(r);
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+        const AxisScale s = pass ? sc.h : sc.w;
+        const bool split = pass == 0 ? W == 128 : H == 128;  // this pass's lines have 128 points
+        const int role = split ? role_of(gt) : 0;
+        const int ln = split ? line_of(gt) : gt;  // row (pass 0) or logical column (pass 1)
         float v[64];
-        if constexpr (DIR == DIR_INV) {
-            // role 0: even coefficients, role 1: odd coefficients
-            if (role == 0) {
+        if (pass == 0) {
+            const RowView rv(ln);
+            if (!split) {
 #pragma unroll
-                for (int k = 0; k < 32; ++k) {
+                for (int k = 0; k < 16; ++k) {
                     const float4 t = at<float4>(slot, (k >> 3) * BB + rv.o[k & 7]);
-                    v[2 * k] = t.x; v[2 * k + 1] = t.z;
+                    v[4 * k] = t.x; v[4 * k + 1] = t.y; v[4 * k + 2] = t.z; v[4 * k + 3] = t.w;
+                }
+            } else if (DIR == DIR_INV) {
+                // role 0: even coefficients, role 1: odd coefficients
+                if (role == 0) {
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) {
+                        const float4 t = at<float4>(slot, (k >> 3) * BB + rv.o[k & 7]);
+                        v[2 * k] = t.x; v[2 * k + 1] = t.z;
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) {
+                        const float4 t = at<float4>(slot, (k >> 3) * BB + rv.o[k & 7]);
+                        v[2 * k] = t.y; v[2 * k + 1] = t.w;
+                    }
                 }
             } else {
+                // sums (role 0) or differences (role 1) of x_j and x_{127-j}
+                const float sg = role ? -1.0f : 1.0f;
 #pragma unroll
-                for (int k = 0; k < 32; ++k) {
-                    const float4 t = at<float4>(slot, (k >> 3) * BB + rv.o[k & 7]);
-                    v[2 * k] = t.y; v[2 * k + 1] = t.w;
+                for (int k = 0; k < 16; ++k) {
+                    const float4 a = at<float4>(slot, (k >> 3) * BB + rv.o[k & 7]);
+                    const float4 b = at<float4>(slot, ((31 - k) >> 3) * BB + rv.o[(31 - k) & 7]);
+                    v[4 * k] = fmaf(sg, b.w, a.x);
+                    v[4 * k + 1] = fmaf(sg, b.z, a.y);
+                    v[4 * k + 2] = fmaf(sg, b.y, a.z);
+                    v[4 * k + 3] = fmaf(sg, b.x, a.w);
                 }
             }
-            scale_from<64>(v, role ? s.s1 : s.s0, s.s1);
         } else {
-            // sums (role 0) or differences (role 1) of x_j and x_{127-j}
-            const float sg = role ? -1.0f : 1.0f;
+            const ColView<H> src(ring_colpos<W, DIR>(ln));
+            if (!split) {
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const float4 a = at<float4>(slot, (k >> 3) * BB + rv.o[k & 7]);
-                const float4 b = at<float4>(slot, ((31 - k) >> 3) * BB + rv.o[(31 - k) & 7]);
-                v[4 * k] = fmaf(sg, b.w, a.x);
-                v[4 * k + 1] = fmaf(sg, b.z, a.y);
-                v[4 * k + 2] = fmaf(sg, b.y, a.z);
-                v[4 * k + 3] = fmaf(sg, b.x, a.w);
+                for (int i = 0; i < 64; ++i) v[i] = at<float>(slot, i * 128 + src.o[i & 7]);
+            } else if (DIR == DIR_INV) {
+                // even rows (role 0) or odd rows (role 1)
+                if (role == 0) {
+#pragma unroll
+                    for (int m = 0; m < 64; ++m) v[m] = at<float>(slot, 2 * m * 128 + src.o[(2 * m) & 7]);
+                } else {
+#pragma unroll
+                    for (int m = 0; m < 64; ++m) v[m] = at<float>(slot, (2 * m + 1) * 128 + src.o[(2 * m + 1) & 7]);
+                }
+            } else {
+                const float sg = role ? -1.0f : 1.0f;
+#pragma unroll
+                for (int i = 0; i < 64; ++i)
+                    v[i] = fmaf(sg, at<float>(slot, (127 - i) * 128 + src.o[(127 - i) & 7]),
+                                at<float>(slot, i * 128 + src.o[i & 7]));
             }
         }
-        group_sync(bar, C::GT);  // every read of the row done before it is overwritten
+        if constexpr (DIR == DIR_INV) scale_from<64>(v, role ? s.s1 : s.s0, s.s1);
+        // every read of the pass done before anything is overwritten (the split
+        // lines' two threads share positions; the column pass of a 128-wide
+        // array writes natural positions over permuted ones)
+        if (split || (pass == 1 && W == 128)) group_sync(bar, C::GT);
         float y[64];
         role_core<DIR>(role, v, y, s);
-        if (role == 0) {
+        if (pass == 0) {
+            const RowView rv(ln);
+            if (!split || role == 0) {
 #pragma unroll
-            for (int k = 0; k < 16; ++k)
-                at<float4>(slot, (k >> 3) * BB + rv.o[k & 7]) = make_float4(y[4 * k], y[4 * k + 1], y[4 * k + 2], y[4 * k + 3]);
-        } else {
-#pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                // forward: Y_{2m+1} at 64 + ((m + 16) mod 64); inverse / round trip: b_j at 64 + j
-                const int kk = 16 + (DIR == DIR_FWD ? ((k + 4) & 15) : k);
-                at<float4>(slot, (kk >> 3) * BB + rv.o[kk & 7]) = make_float4(y[4 * k], y[4 * k + 1], y[4 * k + 2], y[4 * k + 3]);
-            }
-        }
-        if constexpr (DIR != DIR_FWD) {
-            // x_j = a_j + b_j (position j), x_{127-j} = a_j - b_j (position 64 + j)
-            group_sync(bar, C::GT);
-            constexpr int TASKS = H * 16;  // (row, 4 consecutive j)
-#pragma unroll
-            for (int t = gt; t < TASKS; t += C::GT) {
-                const int rr = t >> 4, k = t & 15;
-                const uint32_t oa = sw_chunk<H>(rr, k), ob = sw_chunk<H>(rr, 16 + k);
-                const float4 a = at<float4>(slot, oa), b = at<float4>(slot, ob);
-                at<float4>(slot, oa) = make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
-                at<float4>(slot, ob) = make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
-            }
-        }
-    }
-}
-
-// ---------------------------------------------------------------- column pass
-template <int H, int W, int DIR>
-__device__ __forceinline__ void ring_cols(char *slot, int gt, int bar, AxisScale s)
-{
-    using C = RingCfg<H, W>;
-    if constexpr (H == 64) {
-        // one thread per column; reads at the permuted position, writes at the natural one
-        const int c = gt;
-        const ColView<H> src(ring_colpos<W, DIR>(c));
-        float x[64];
-#pragma unroll
-        for (int i = 0; i < 64; ++i) x[i] = at<float>(slot, i * 128 + src.o[i & 7]);
-        if constexpr (W == 128) group_sync(bar, C::GT);
-        line_op<64, DIR>(x, s);
-        const ColView<H> dst(c);
-#pragma unroll
-        for (int i = 0; i < 64; ++i) at<float>(slot, i * 128 + dst.o[i & 7]) = x[i];
-    } else {
-        const int role = role_of(gt);
-        const int c = line_of(gt);
-        const ColView<H> src(ring_colpos<W, DIR>(c));
-        float v[64];
-        if constexpr (DIR == DIR_INV) {
-            // even rows (role 0) or odd rows (role 1)
-            if (role == 0) {
-#pragma unroll
-                for (int m = 0; m < 64; ++m) v[m] = at<float>(slot, 2 * m * 128 + src.o[(2 * m) & 7]);
+                for (int k = 0; k < 16; ++k)
+                    at<float4>(slot, (k >> 3) * BB + rv.o[k & 7]) = make_float4(y[4 * k], y[4 * k + 1], y[4 * k + 2], y[4 * k + 3]);
             } else {
 #pragma unroll
-                for (int m = 0; m < 64; ++m) v[m] = at<float>(slot, (2 * m + 1) * 128 + src.o[(2 * m + 1) & 7]);
+                for (int k = 0; k < 16; ++k) {
+                    // forward: Y_{2m+1} at 64 + ((m + 16) mod 64); inverse / round trip: b_j at 64 + j
+                    const int kk = 16 + (DIR == DIR_FWD ? ((k + 4) & 15) : k);
+                    at<float4>(slot, (kk >> 3) * BB + rv.o[kk & 7]) = make_float4(y[4 * k], y[4 * k + 1], y[4 * k + 2], y[4 * k + 3]);
+                }
             }
-            scale_from<64>(v, role ? s.s1 : s.s0, s.s1);
-        } else {
-            const float sg = role ? -1.0f : 1.0f;
+            if (DIR != DIR_FWD && split) {
+                // x_j = a_j + b_j (position j), x_{127-j} = a_j - b_j (position 64 + j)
+                group_sync(bar, C::GT);
+                constexpr int TASKS = H * 16;  // (row, 4 consecutive j)
 #pragma unroll
-            for (int i = 0; i < 64; ++i)
-                v[i] = fmaf(sg, at<float>(slot, (127 - i) * 128 + src.o[(127 - i) & 7]),
-                            at<float>(slot, i * 128 + src.o[i & 7]));
-        }
-        group_sync(bar, C::GT);  // all reads done: writes go to natural positions
-        float y[64];
-        role_core<DIR>(role, v, y, s);
-        const ColView<H> dst(c);
-        if constexpr (DIR == DIR_FWD) {
-            // rows 2m (role 0) or 2m + 1 (role 1)
-            if (role == 0) {
-#pragma unroll
-                for (int m = 0; m < 64; ++m) at<float>(slot, 2 * m * 128 + dst.o[(2 * m) & 7]) = y[m];
-            } else {
-#pragma unroll
-                for (int m = 0; m < 64; ++m) at<float>(slot, (2 * m + 1) * 128 + dst.o[(2 * m + 1) & 7]) = y[m];
+                for (int t = gt; t < TASKS; t += C::GT) {
+                    const int rr = t >> 4, k = t & 15;
+                    const uint32_t oa = sw_chunk<H>(rr, k), ob = sw_chunk<H>(rr, 16 + k);
+                    const float4 a = at<float4>(slot, oa), b = at<float4>(slot, ob);
+                    at<float4>(slot, oa) = make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+                    at<float4>(slot, ob) = make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+                }
             }
         } else {
-            if (role == 0) {
+            const ColView<H> dst(ln);
+            if (!split) {
 #pragma unroll
-                for (int j = 0; j < 64; ++j) at<float>(slot, j * 128 + dst.o[j & 7]) = y[j];  // a_j at row j
+                for (int i = 0; i < 64; ++i) at<float>(slot, i * 128 + dst.o[i & 7]) = y[i];
+            } else if (DIR == DIR_FWD) {
+                // rows 2m (role 0) or 2m + 1 (role 1)
+                if (role == 0) {
+#pragma unroll
+                    for (int m = 0; m < 64; ++m) at<float>(slot, 2 * m * 128 + dst.o[(2 * m) & 7]) = y[m];
+                } else {
+#pragma unroll
+                    for (int m = 0; m < 64; ++m) at<float>(slot, (2 * m + 1) * 128 + dst.o[(2 * m + 1) & 7]) = y[m];
+                }
             } else {
+                if (role == 0) {
 #pragma unroll
-                for (int j = 0; j < 64; ++j)
-                    at<float>(slot, (127 - j) * 128 + dst.o[(127 - j) & 7]) = y[j];  // b_j at row 127 - j
-            }
-            group_sync(bar, C::GT);
-            // x_j = a_j + b_j, x_{127-j} = a_j - b_j; two threads per column, 32 pairs each
-            auto comb = [&](int j) {
-                const uint32_t oa = j * 128 + dst.o[j & 7], ob = (127 - j) * 128 + dst.o[(127 - j) & 7];
-                const float a = at<float>(slot, oa), b = at<float>(slot, ob);
-                at<float>(slot, oa) = a + b;
-                at<float>(slot, ob) = a - b;
-            };
-            if (role == 0) {
+                    for (int j = 0; j < 64; ++j) at<float>(slot, j * 128 + dst.o[j & 7]) = y[j];  // a_j at row j
+                } else {
 #pragma unroll
-                for (int j = 0; j < 32; ++j) comb(j);
-            } else {
+                    for (int j = 0; j < 64; ++j)
+                        at<float>(slot, (127 - j) * 128 + dst.o[(127 - j) & 7]) = y[j];  // b_j at row 127 - j
+                }
+                group_sync(bar, C::GT);
+                // x_j = a_j + b_j, x_{127-j} = a_j - b_j; two threads per column, 32 pairs each
+                auto comb = [&](int j) {
+                    const uint32_t oa = j * 128 + dst.o[j & 7], ob = (127 - j) * 128 + dst.o[(127 - j) & 7];
+                    const float a = at<float>(slot, oa), b = at<float>(slot, ob);
+                    at<float>(slot, oa) = a + b;
+                    at<float>(slot, ob) = a - b;
+                };
+                if (role == 0) {
 #pragma unroll
-                for (int j = 32; j < 64; ++j) comb(j);
+                    for (int j = 0; j < 32; ++j) comb(j);
+                } else {
+#pragma unroll
+                    for (int j = 32; j < 64; ++j) comb(j);
+                }
             }
         }
+        group_sync(bar, C::GT);
     }
 }
 
@@ -681,17 +670,10 @@ __global__ void __launch_bounds__(RingCfg<H, W>::THREADS, 1) k_ring(const __grid
             break;
         }
         char *slot = smem + s * C::SLOT_BYTES;
-        if constexpr (H == W) {
-            ring_square<H, DIR>(slot, gt, bar, p.sc);  // ends with a group barrier
-            fence_proxy_async_smem();  // the TMA store reads the slot through the async proxy
-            group_sync(bar, C::GT);
-        } else {
-            ring_rows<H, W, DIR>(slot, gt, bar, p.sc.w);
-            group_sync(bar, C::GT);
-            ring_cols<H, W, DIR>(slot, gt, bar, p.sc.h);
-            fence_proxy_async_smem();  // the TMA store reads the slot through the async proxy
-            group_sync(bar, C::GT);
-        }
+        if constexpr (H == W) ring_square<H, DIR>(slot, gt, bar, p.sc);  // both end with a group barrier
+        else ring_rect<H, W, DIR>(slot, gt, bar, p.sc);
+        fence_proxy_async_smem();  // the TMA store reads the slot through the async proxy
+        group_sync(bar, C::GT);
         if (gt == 0) mbar_arrive(&done[s]);
     }
 }
