@@ -59,6 +59,13 @@ bool fused_supported(int rows, int cols);
 cudaError_t fused_launch(int rows, int cols, Dir dir, const DirScales &sc, const ExecGeom &g,
                          unsigned int *status, cudaStream_t stream);
 
+// ---- tma_host.cu
+// A 2D tensor map (TMA) of a row-major float matrix of rows x cols with row
+// stride ld floats: boxes of 32 columns x box_rows rows, 128-byte swizzle.
+// CUtensorMap comes from <cuda.h>; this header only forward-declares it.
+cudaError_t tma_map_2d(struct CUtensorMap_st *m, const float *base, unsigned long long rows,
+                       unsigned long long cols, unsigned long long ld, int box_rows);
+
 // ---- fp32_ring.cu
 // Warp-specialized ring kernels for sides 64 and 128 (all four combinations):
 // contiguous, indexed and tiled batches.

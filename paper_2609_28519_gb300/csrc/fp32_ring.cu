@@ -679,44 +679,6 @@ __global__ void __launch_bounds__(RingCfg<H, W>::THREADS, 1) k_ring(const __grid
 }
 
 // ---------------------------------------------------------------- host side
-typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-static EncodeTiledFn encode_fn()
-{
-    static EncodeTiledFn fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
-        void *f = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiledFn>(f);
-    }
-    return fn;
-}
-
-// A row-major float matrix of `rows` x `cols` with row stride `ld` floats,
-// read and written in boxes of 32 columns x `box_rows` rows, 128-byte swizzle.
-static cudaError_t make_map(CUtensorMap *m, const float *base, unsigned long long rows, unsigned long long cols,
-                            unsigned long long ld, int box_rows)
-{
-    EncodeTiledFn fn = encode_fn();
-    if (!fn) return cudaErrorNotSupported;
-    if (rows > 0xffffffffull || cols > 0xffffffffull) return cudaErrorInvalidValue;
-    const cuuint64_t dims[2] = {cols, rows};
-    const cuuint64_t strides[1] = {ld * sizeof(float)};
-    const cuuint32_t box[2] = {32, (cuuint32_t)box_rows};
-    const cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
-}
-
 template <int H, int W, int DIR>
 static cudaError_t ring_launch_one(const DirScales &sc, const ExecGeom &g, unsigned int *status,
                                    cudaStream_t stream)
@@ -762,13 +724,13 @@ static cudaError_t ring_launch_one(const DirScales &sc, const ExecGeom &g, unsig
     } else if (g.tiled) {
         const unsigned long long rows = (unsigned long long)(g.count / g.tiles_per_row) * H;
         const unsigned long long cols = (unsigned long long)g.tiles_per_row * W;
-        e = make_map(&p.map_in, g.in, rows, cols, (unsigned long long)g.ld_in, H);
-        if (e == cudaSuccess) e = make_map(&p.map_out, g.out, rows, cols, (unsigned long long)g.ld_out, H);
+        e = tma_map_2d(&p.map_in, g.in, rows, cols, (unsigned long long)g.ld_in, H);
+        if (e == cudaSuccess) e = tma_map_2d(&p.map_out, g.out, rows, cols, (unsigned long long)g.ld_out, H);
         if (e != cudaSuccess) return e;
     } else {
         const unsigned long long rows = (unsigned long long)g.count * H;
-        e = make_map(&p.map_in, g.in, rows, W, W, H);
-        if (e == cudaSuccess) e = make_map(&p.map_out, g.out, rows, W, W, H);
+        e = tma_map_2d(&p.map_in, g.in, rows, W, W, H);
+        if (e == cudaSuccess) e = tma_map_2d(&p.map_out, g.out, rows, W, W, H);
         if (e != cudaSuccess) return e;
     }
     long long grid = num_sms[dev];
