@@ -111,8 +111,14 @@ struct FFT {
                 re[k + M] = mr + sr; im[k + M] = mi + si;
                 re[k + 2 * M] = mr - sr; im[k + 2 * M] = mi - si;
             }
-            return;
+        } else {
+            radix2(re, im);
         }
+    }
+
+    // radix-2 decimation in time: two interleaved FFTs of L/2, then butterflies
+    static __device__ __forceinline__ void radix2(float (&re)[L], float (&im)[L])
+    {
         float er[L / 2], ei[L / 2], orr[L / 2], oi[L / 2];
 #pragma unroll
         for (int j = 0; j < L / 2; ++j) {

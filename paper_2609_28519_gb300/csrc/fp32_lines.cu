@@ -56,13 +56,13 @@ struct LineCfg {
     static constexpr int JA = L2 / T;  // step-A sub-FFTs per thread
     static constexpr int JC = L1 / T;  // step-C sub-FFTs per thread
     static constexpr int LPW = 32 / T;  // lines per warp
-    static constexpr int NW = (N == 1024 || N == 2048 || N == 4096) ? 4 : 8;  // warps per CTA
+    static constexpr int NW = N == 4096 ? 4 : 8;  // warps per CTA
     static constexpr int THREADS = 32 * NW;
     static constexpr int LPR = NW * LPW;  // lines per round
     // Rows per panel.  For T < 16 a half-warp holds several lines; they sit T
     // rows apart (rows 32 b + w + T sub of a 32-row block, w < T), which with a
     // row pitch of 2 mod 32 floats puts them 2T banks apart.
-    static constexpr int PR = T < 16 ? (N == 768 ? 32 : 64) : (N <= 1024 ? 16 : (N == 2048 ? 8 : 4));
+    static constexpr int PR = T < 16 ? (T == 4 ? 64 : 32) : (N <= 1024 ? 16 : (N == 2048 ? 8 : 4));
     static constexpr int ROUNDS = PR / LPR;
     static constexpr int A_FLOATS = 2 * L1 * (L2 + 1);  // step-A output, row pitch L2 + 1 complex
     static constexpr int pitch(int need, int mod)
