@@ -260,14 +260,15 @@ __global__ void __launch_bounds__(128) k_tc_split(const TcParams p)
     uint32_t mma_phase = 0;
 
     const int b_local = tid / N, r_local = tid % N;  // this thread's stack row: array, row
-    float v[N];
-    for (int tile = blockIdx.x; ok && tile < p.ntiles; tile += gridDim.x) {
+    // this thread's input row of a tile (zeros for arrays beyond the batch);
+    // for n <= 32 the next tile's row is loaded while the current tile's
+    // contractions run, so the global-load latency overlaps them
+    constexpr bool PREFETCH = N <= 32;
+    auto load_row = [&](int tile, float (&dstv)[N]) {
         long long first, brow;
         int n, t0;
         tile_geom<N, TILED>(p, tile, first, n, brow, t0);
-        const bool active = b_local < n;
-        // ---- load this thread's input row (zeros for absent arrays)
-        if (active) {
+        if (b_local < n) {
             const float *src;
             if constexpr (!TILED)
                 src = (p.in_off ? p.in + p.in_off[first + b_local] : p.in + (first + b_local) * (long long)(N * N)) +
@@ -276,11 +277,30 @@ __global__ void __launch_bounds__(128) k_tc_split(const TcParams p)
 #pragma unroll
             for (int q = 0; q < N / 4; ++q) {
                 const float4 t = __ldg(reinterpret_cast<const float4 *>(src) + q);
-                v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
+                dstv[4 * q] = t.x; dstv[4 * q + 1] = t.y; dstv[4 * q + 2] = t.z; dstv[4 * q + 3] = t.w;
             }
         } else {
 #pragma unroll
-            for (int j = 0; j < N; ++j) v[j] = 0.0f;
+            for (int j = 0; j < N; ++j) dstv[j] = 0.0f;
+        }
+    };
+    float v[N];
+    float nxt[PREFETCH ? N : 1];
+    if constexpr (PREFETCH) {
+        if (blockIdx.x < (unsigned)p.ntiles) load_row(blockIdx.x, nxt);
+    }
+    for (int tile = blockIdx.x; ok && tile < p.ntiles; tile += gridDim.x) {
+        long long first, brow;
+        int n, t0;
+        tile_geom<N, TILED>(p, tile, first, n, brow, t0);
+        const bool active = b_local < n;
+        if constexpr (PREFETCH) {
+#pragma unroll
+            for (int j = 0; j < N; ++j) v[j] = nxt[j];
+            const int nx = tile + (int)gridDim.x;
+            if (nx < p.ntiles) load_row(nx, nxt);
+        } else {
+            load_row(tile, v);
         }
 #pragma unroll 1
         for (int pass = 0; pass < NPASS; ++pass) {
