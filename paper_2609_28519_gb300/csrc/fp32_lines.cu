@@ -64,7 +64,12 @@ struct LineCfg {
     // row pitch of 2 mod 32 floats puts them 2T banks apart.
     static constexpr int PR = T < 16 ? (T == 4 ? 64 : 32) : (N <= 1024 ? 16 : (N == 2048 ? 8 : 4));
     static constexpr int ROUNDS = PR / LPR;
-    static constexpr int A_FLOATS = 2 * L1 * (L2 + 1);  // step-A output, row pitch L2 + 1 complex
+    // With L2 >= 16 both FFT steps run in place in the line buffer: step A's
+    // results are held in registers across a warp barrier and written back
+    // with a 16-periodic XOR swizzle that keeps step C conflict-free, so no
+    // per-line scratch is needed.  Shorter lines use a padded scratch.
+    static constexpr bool INPLACE = L2 >= 16;
+    static constexpr int A_FLOATS = INPLACE ? N : 2 * L1 * (L2 + 1);  // step-A output
     static constexpr int pitch(int need, int mod)
     {
         int p = need;
@@ -75,7 +80,7 @@ struct LineCfg {
     // that the transposed store (16 rows x 2 columns per warp) is conflict-free
     static constexpr int PP = pitch(A_FLOATS > N ? A_FLOATS : N, 2);
     // per-line scratch: the lines of one warp 2T banks apart
-    static constexpr int SCR = pitch(A_FLOATS > N ? A_FLOATS : N, (2 * T) % 32);
+    static constexpr int SCR = INPLACE ? 0 : pitch(A_FLOATS > N ? A_FLOATS : N, (2 * T) % 32);
     static constexpr int SEG = PR < 16 ? PR : 16;  // rows per transposed-store segment (a multiple of 4)
     static constexpr int TAB_F2 = 3 * L;           // L step-A twiddles, then L float4 split twiddles
     static constexpr size_t SMEM = (size_t)PR * PP * 4 + (size_t)LPR * SCR * 4 + (size_t)TAB_F2 * 8;
@@ -152,6 +157,61 @@ __device__ __forceinline__ void four_step_c(const float2 *A, int t, float (&zr)[
     }
 }
 
+// In-place variants (L2 >= 16).  A[k1][m2] sits at k1 L2 + (m2 XOR (k1 mod 16)).
+template <int N>
+__device__ __forceinline__ void four_step_a_inplace(float2 *buf, const float2 *ta, int t)
+{
+    using C = LineCfg<N>;
+    float hr[C::JA][C::L1], hi[C::JA][C::L1];
+#pragma unroll
+    for (int j = 0; j < C::JA; ++j) {
+        const int m2 = t + C::T * j;
+#pragma unroll
+        for (int m1 = 0; m1 < C::L1; ++m1) {
+            const float2 v = buf[C::L2 * m1 + m2];
+            hr[j][m1] = v.x;
+            hi[j][m1] = v.y;
+        }
+        FFT<C::L1>::run(hr[j], hi[j]);
+#pragma unroll
+        for (int k1 = 1; k1 < C::L1; ++k1) {
+            const float2 w = cmul(make_float2(hr[j][k1], hi[j][k1]), ta[k1 * C::L2 + m2]);
+            hr[j][k1] = w.x;
+            hi[j][k1] = w.y;
+        }
+    }
+    __syncwarp();  // every read of the line done before A overwrites it
+#pragma unroll
+    for (int j = 0; j < C::JA; ++j) {
+        const int m2 = t + C::T * j;
+#pragma unroll
+        for (int k1 = 0; k1 < C::L1; ++k1) buf[k1 * C::L2 + (m2 ^ (k1 & 15))] = make_float2(hr[j][k1], hi[j][k1]);
+    }
+    __syncwarp();
+}
+
+template <int N>
+__device__ __forceinline__ void four_step_c_inplace(const float2 *buf, int t,
+                                                    float (&zr)[LineCfg<N>::JC][LineCfg<N>::L2],
+                                                    float (&zi)[LineCfg<N>::JC][LineCfg<N>::L2])
+{
+    using C = LineCfg<N>;
+#pragma unroll
+    for (int j = 0; j < C::JC; ++j) {
+        const int k1 = t + C::T * j;
+        const float2 *row = buf + k1 * C::L2;
+        const int x = k1 & 15;
+#pragma unroll
+        for (int m2 = 0; m2 < C::L2; ++m2) {
+            const float2 v = row[(m2 & ~15) + ((m2 & 15) ^ x)];
+            zr[j][m2] = v.x;
+            zi[j][m2] = v.y;
+        }
+        FFT<C::L2>::run(zr[j], zi[j]);
+    }
+    __syncwarp();  // every read of A done before the line is overwritten
+}
+
 // Forward DCT-II of one line.  On entry `line` holds z (Makhoul order, as
 // float2); on exit y_k * s_k in natural order.  Z_k and its split partner
 // Z_{L-k} sit in registers of threads t and T - t of the line (the same
@@ -162,12 +222,17 @@ __device__ __forceinline__ void line_forward(float *line, float *scr, const floa
 {
     using C = LineCfg<N>;
     float2 *z = reinterpret_cast<float2 *>(line);
-    float2 *A = reinterpret_cast<float2 *>(scr);
-    four_step_a<N>(z, A, ta, t);
-    __syncwarp();
     float zr[C::JC][C::L2], zi[C::JC][C::L2];
-    four_step_c<N>(A, t, zr, zi);
-    // the line buffer is free (z was consumed by step A before the barrier)
+    if constexpr (C::INPLACE) {
+        four_step_a_inplace<N>(z, ta, t);
+        four_step_c_inplace<N>(z, t, zr, zi);
+    } else {
+        float2 *A = reinterpret_cast<float2 *>(scr);
+        four_step_a<N>(z, A, ta, t);
+        __syncwarp();
+        four_step_c<N>(A, t, zr, zi);
+    }
+    // the line buffer is free (its last reader passed a warp barrier)
     const int src = lane - t + (C::T - t) % C::T;
 #pragma unroll
     for (int j = 0; j < C::JC; ++j) {
@@ -215,17 +280,21 @@ __device__ __forceinline__ void line_inverse(float *line, float *scr, const floa
                                              AxisScale s)
 {
     using C = LineCfg<N>;
-    float2 *Zc = reinterpret_cast<float2 *>(scr);  // conj(Z), natural order
+    // conj(Z) in natural order: a scratch buffer, or (in place) registers
+    // written over the line once every y has been read
+    float2 *Zc = reinterpret_cast<float2 *>(C::INPLACE ? line : scr);
+    float qr[C::JC][C::L2], qi[C::JC][C::L2];
     // y -> conj(Z): each k from y_k, y_{N-k}, y_{L-k}, y_{L+k}
 #pragma unroll
     for (int j = 0; j < C::JC; ++j) {
 #pragma unroll
         for (int k2 = 0; k2 < C::L2; ++k2) {
             const int k = t + C::T * j + C::L1 * k2;
+            float2 zc;
             if (k == 0) {
                 const float v0 = 2.0f * line[0] * s.s0;  // factor 2 carries 1/L
                 const float vl = 1.41421356237309505f * line[C::L] * s.s1;
-                Zc[0] = make_float2(0.5f * (v0 + vl), -0.5f * (v0 - vl));
+                zc = make_float2(0.5f * (v0 + vl), -0.5f * (v0 - vl));
             } else {
                 const float yk = line[k] * s.s1, ynk = line[N - k] * s.s1;
                 const float ylk = line[C::L - k] * s.s1, ylpk = line[C::L + k] * s.s1;
@@ -236,16 +305,32 @@ __device__ __forceinline__ void line_inverse(float *line, float *scr, const floa
                 const float2 E = make_float2(0.5f * (Vk.x + Vl.x), 0.5f * (Vk.y - Vl.y));
                 const float2 D = make_float2(0.5f * (Vk.x - Vl.x), 0.5f * (Vk.y + Vl.y));
                 const float2 O = cmulc(D, make_float2(w.x, w.y));  // / exp(-2 pi i k / N)
-                Zc[k] = make_float2(E.x - O.y, -(E.y + O.x));      // conj(E + i O)
+                zc = make_float2(E.x - O.y, -(E.y + O.x));         // conj(E + i O)
+            }
+            if constexpr (C::INPLACE) {
+                qr[j][k2] = zc.x;
+                qi[j][k2] = zc.y;
+            } else {
+                Zc[k] = zc;
             }
         }
     }
-    __syncwarp();  // every read of y done before A overwrites the line
-    float2 *A = reinterpret_cast<float2 *>(line);
-    four_step_a<N>(Zc, A, ta, t);
-    __syncwarp();
+    __syncwarp();  // every read of y done before the line is overwritten
     float rr[C::JC][C::L2], ri[C::JC][C::L2];
-    four_step_c<N>(A, t, rr, ri);
+    if constexpr (C::INPLACE) {
+#pragma unroll
+        for (int j = 0; j < C::JC; ++j)
+#pragma unroll
+            for (int k2 = 0; k2 < C::L2; ++k2) Zc[t + C::T * j + C::L1 * k2] = make_float2(qr[j][k2], qi[j][k2]);
+        __syncwarp();
+        four_step_a_inplace<N>(Zc, ta, t);
+        four_step_c_inplace<N>(Zc, t, rr, ri);
+    } else {
+        float2 *A = reinterpret_cast<float2 *>(line);
+        four_step_a<N>(Zc, A, ta, t);
+        __syncwarp();
+        four_step_c<N>(A, t, rr, ri);
+    }
     __syncwarp();  // all of A read before x overwrites the line
 #pragma unroll
     for (int j = 0; j < C::JC; ++j) {
@@ -280,7 +365,7 @@ __global__ void __launch_bounds__(LineCfg<N>::THREADS) k_lines(const LinesParams
     using C = LineCfg<N>;
     extern __shared__ __align__(16) float lsm[];
     float *panel = lsm;
-    float *scr_all = panel + C::PR * C::PP;
+    float *scr_all = panel + C::PR * C::PP;  // per-line scratch (lines without the in-place steps)
     float2 *ta = reinterpret_cast<float2 *>(scr_all + C::LPR * C::SCR);
     const float4 *ts = reinterpret_cast<const float4 *>(ta + C::L);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -297,7 +382,8 @@ __global__ void __launch_bounds__(LineCfg<N>::THREADS) k_lines(const LinesParams
     // panel is transformed, so the global-load latency overlaps the work.
     constexpr int V4 = N / 4;
     constexpr int ITER = C::PR * V4 / C::THREADS;
-    constexpr bool PREFETCH = N <= 2048;
+    // (768-point inverse and round trip lines already hold 48 complex values)
+    constexpr bool PREFETCH = N <= 2048 && !(N == 768 && DIR != DIR_FWD);
     constexpr int NB = PREFETCH ? ITER : (ITER < 8 ? ITER : 8);
     static_assert(ITER * C::THREADS == C::PR * V4 && ITER % NB == 0, "load batches");
     auto panel_src = [&](int pn, long long &b, int &rr) -> const float4 * {
