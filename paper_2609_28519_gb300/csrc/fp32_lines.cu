@@ -216,7 +216,9 @@ __device__ __forceinline__ void four_step_c_inplace(const float2 *buf, int t,
 // float2); on exit y_k * s_k in natural order.  Z_k and its split partner
 // Z_{L-k} sit in registers of threads t and T - t of the line (the same
 // warp), so the partner comes by shuffle.
-template <int N>
+// With FOLD the table's exp(-i pi k / (2N)) carries the factor s_1 / 2
+// (folded in when the table is staged), saving the scalings below.
+template <int N, bool FOLD = false>
 __device__ __forceinline__ void line_forward(float *line, float *scr, const float2 *ta, const float4 *ts, int t,
                                              int lane, AxisScale s)
 {
@@ -260,13 +262,23 @@ __device__ __forceinline__ void line_forward(float *line, float *scr, const floa
                 line[C::L] = (ar - ai) * 0.70710678118654752f * s.s1;
             } else {
                 const float4 w = ts[k];  // (exp(-2 pi i k / N), exp(-i pi k / (2N)))
-                const float2 E = make_float2(0.5f * (ar + cr), 0.5f * (ai - ci));
-                const float2 O = make_float2(0.5f * (ai + ci), 0.5f * (cr - ar));
-                const float2 P = cmul(make_float2(w.x, w.y), O);
-                const float2 V = make_float2(E.x + P.x, E.y + P.y);
-                const float2 WV = cmul(make_float2(w.z, w.w), V);
-                line[k] = WV.x * s.s1;
-                line[N - k] = -WV.y * s.s1;
+                if constexpr (FOLD) {
+                    // 2E, 2O; the table's second factor carries s_1 / 2
+                    const float2 E = make_float2(ar + cr, ai - ci);
+                    const float2 O = make_float2(ai + ci, cr - ar);
+                    const float2 P = cmul(make_float2(w.x, w.y), O);
+                    const float2 WV = cmul(make_float2(w.z, w.w), make_float2(E.x + P.x, E.y + P.y));
+                    line[k] = WV.x;
+                    line[N - k] = -WV.y;
+                } else {
+                    const float2 E = make_float2(0.5f * (ar + cr), 0.5f * (ai - ci));
+                    const float2 O = make_float2(0.5f * (ai + ci), 0.5f * (cr - ar));
+                    const float2 P = cmul(make_float2(w.x, w.y), O);
+                    const float2 V = make_float2(E.x + P.x, E.y + P.y);
+                    const float2 WV = cmul(make_float2(w.z, w.w), V);
+                    line[k] = WV.x * s.s1;
+                    line[N - k] = -WV.y * s.s1;
+                }
             }
         }
     }
@@ -275,7 +287,7 @@ __device__ __forceinline__ void line_forward(float *line, float *scr, const floa
 
 // Inverse DCT-III of one line.  On entry `line` holds y in natural order; on
 // exit x (natural order).  Input scales s_k applied on entry.
-template <int N>
+template <int N, bool FOLD = false>
 __device__ __forceinline__ void line_inverse(float *line, float *scr, const float2 *ta, const float4 *ts, int t,
                                              AxisScale s)
 {
@@ -296,14 +308,16 @@ __device__ __forceinline__ void line_inverse(float *line, float *scr, const floa
                 const float vl = 1.41421356237309505f * line[C::L] * s.s1;
                 zc = make_float2(0.5f * (v0 + vl), -0.5f * (v0 - vl));
             } else {
-                const float yk = line[k] * s.s1, ynk = line[N - k] * s.s1;
-                const float ylk = line[C::L - k] * s.s1, ylpk = line[C::L + k] * s.s1;
+                const float sy = FOLD ? 1.0f : s.s1;  // with FOLD the table carries s_1 / 2
+                const float yk = line[k] * sy, ynk = line[N - k] * sy;
+                const float ylk = line[C::L - k] * sy, ylpk = line[C::L + k] * sy;
                 const float4 w = ts[k], wl = ts[C::L - k];
                 // V_k = conj(W_k) (y_k - i y_{N-k}), V_{L-k} likewise
                 const float2 Vk = cmulc(make_float2(yk, -ynk), make_float2(w.z, w.w));
                 const float2 Vl = cmulc(make_float2(ylk, -ylpk), make_float2(wl.z, wl.w));
-                const float2 E = make_float2(0.5f * (Vk.x + Vl.x), 0.5f * (Vk.y - Vl.y));
-                const float2 D = make_float2(0.5f * (Vk.x - Vl.x), 0.5f * (Vk.y + Vl.y));
+                const float hf = FOLD ? 1.0f : 0.5f;
+                const float2 E = make_float2(hf * (Vk.x + Vl.x), hf * (Vk.y - Vl.y));
+                const float2 D = make_float2(hf * (Vk.x - Vl.x), hf * (Vk.y + Vl.y));
                 const float2 O = cmulc(D, make_float2(w.x, w.y));  // / exp(-2 pi i k / N)
                 zc = make_float2(E.x - O.y, -(E.y + O.x));         // conj(E + i O)
             }
@@ -373,8 +387,15 @@ __global__ void __launch_bounds__(LineCfg<N>::THREADS) k_lines(const LinesParams
 
     pdl_launch_dependents();
     pdl_wait_prerequisites();
-    // the plan's twiddle tables (FP64-generated): step A, then the split
-    for (int r = tid; r < C::TAB_F2; r += C::THREADS) ta[r] = p.tw[r];
+    // the plan's twiddle tables (FP64-generated): step A, then the split;
+    // forward and inverse fold s_1 / 2 into exp(-i pi k / (2N)) here
+    constexpr bool FOLD = DIR != DIR_RT;
+    const float fold = 0.5f * p.sc.s1;
+    for (int r = tid; r < C::TAB_F2; r += C::THREADS) {
+        float2 v = p.tw[r];
+        if (FOLD && r >= C::L && ((r - C::L) & 1)) v = make_float2(v.x * fold, v.y * fold);
+        ta[r] = v;
+    }
     __syncthreads();
 
     // The panel's 16-byte chunks, ITER per thread; for lines up to 2048 points
@@ -451,9 +472,9 @@ __global__ void __launch_bounds__(LineCfg<N>::THREADS) k_lines(const LinesParams
             float *line = panel + line_row<N>(rd * C::NW + warp, sub) * C::PP;
             float *scr = scr_all + (warp * C::LPW + sub) * C::SCR;
             if constexpr (DIR == DIR_FWD) {
-                line_forward<N>(line, scr, ta, ts, t, lane, p.sc);
+                line_forward<N, true>(line, scr, ta, ts, t, lane, p.sc);
             } else if constexpr (DIR == DIR_INV) {
-                line_inverse<N>(line, scr, ta, ts, t, p.sc);
+                line_inverse<N, true>(line, scr, ta, ts, t, p.sc);
             } else {
                 // round trip: forward core, E^2 correction, adjoint core
                 const AxisScale one = {1.0f, 1.0f};
