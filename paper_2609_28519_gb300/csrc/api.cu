@@ -258,7 +258,7 @@ static int run_lines(const bdct_plan *p, Dir dir, const float *in, const long lo
                                    in_off ? in_off + b0 : nullptr, nullptr);
         if (e == cudaSuccess)
             e = lines_pass(p->work, dst, w, h, nb, dir, p->scales[dir].h, p->line_tw + p->line_tw_h, p->status, s,
-                           nullptr, out_off ? out_off + b0 : nullptr);
+                           nullptr, out_off ? out_off + b0 : nullptr, true);
         if (e != cudaSuccess) return cuda_fail(e);
     }
     return BDCT_OK;

@@ -92,7 +92,8 @@ cudaError_t lines_gen_table(float2 *dst, int n, cudaStream_t s);
 // n x rows.  Two such passes give the 2D transform in natural layout.
 cudaError_t lines_pass(const float *src, float *dst, int rows, int n, long long count, Dir dir,
                        AxisScale sc, const float2 *tw, unsigned int *status, cudaStream_t stream,
-                       const long long *src_off = nullptr, const long long *dst_off = nullptr);
+                       const long long *src_off = nullptr, const long long *dst_off = nullptr,
+                       bool reverse = false);
 
 // ---- tc_split.cu
 // Split-BF16 tcgen05 route for square sides 16, 32, 64.

@@ -371,6 +371,8 @@ struct LinesParams {
     AxisScale sc;        // forward: output scales; inverse: input scales; round trip: E^2
     const long long *src_off, *dst_off;  // indexed arrays (element offsets), or null
     const float2 *tw;    // the plan's tables for N (lines_gen_table), generated in FP64
+    int reverse;         // take panels last to first (the second pass reads the
+                         // intermediate the first pass wrote last, still in L2, first)
 };
 
 template <int N, int DIR>
@@ -408,6 +410,7 @@ __global__ void __launch_bounds__(LineCfg<N>::THREADS) k_lines(const LinesParams
     constexpr int NB = PREFETCH ? ITER : (ITER < 8 ? ITER : 8);
     static_assert(ITER * C::THREADS == C::PR * V4 && ITER % NB == 0, "load batches");
     auto panel_src = [&](int pn, long long &b, int &rr) -> const float4 * {
+        if (p.reverse) pn = p.npanels - 1 - pn;
         const long long r0 = (long long)pn * C::PR;  // first global row of the panel
         b = r0 / p.rows;                             // its array (panels never straddle two)
         rr = (int)(r0 - b * p.rows);
@@ -615,10 +618,11 @@ cudaError_t lines_gen_table(float2 *dst, int n, cudaStream_t s)
 
 cudaError_t lines_pass(const float *src, float *dst, int rows, int n, long long count, Dir dir, AxisScale sc,
                        const float2 *tw, unsigned int *status, cudaStream_t stream, const long long *src_off,
-                       const long long *dst_off)
+                       const long long *dst_off, bool reverse)
 {
     (void)status;
     LinesParams p{};
+    p.reverse = reverse ? 1 : 0;
     p.src = src;
     p.dst = dst;
     p.tw = tw;

@@ -257,6 +257,25 @@ def test_inplace_and_tail_and_guards(oracle_mod, cuda_dev):
     assert np.array_equal(x.cpu().numpy(), out.cpu().numpy())
 
 
+@pytest.mark.parametrize("h,w", [(64, 64), (128, 128), (64, 128), (256, 256), (768, 64)])
+def test_exact_inplace_large_sides(oracle_mod, cuda_dev, h, w):
+    """in == out on the ring kernels (TMA copies read and write the same
+    arrays) and on the line route (through the plan workspace): the result
+    equals the out-of-place one bit for bit and matches the oracle."""
+    import torch
+    from paper_2609_28519_gb300 import Plan
+    plan = Plan(h, w)
+    x_np = inputs.uniform(88 + h + w, 9, h, w)
+    x = torch.from_numpy(x_np).to(cuda_dev)
+    for kind in KINDS:
+        ref_gpu = plan.execute(kind, x)
+        y = x.clone()
+        plan.execute(kind, y, y)
+        torch.cuda.synchronize()
+        assert torch.equal(y, ref_gpu), (h, w, kind)
+        _assert_parity(oracle_mod, y.cpu().numpy(), _ref(oracle_mod, kind, x_np, 0), x_np, 0, kind, ("inplace", h, w, kind))
+
+
 def test_argument_errors_on_device(cuda_dev):
     import torch
     from paper_2609_28519_gb300 import Plan, BdctError, native
