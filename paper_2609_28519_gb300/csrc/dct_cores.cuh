@@ -37,17 +37,48 @@ __device__ __forceinline__ float cospi_md(int m, int d)
 // sin(pi m / d) = cos(pi (d/2 - m) / d)
 __device__ __forceinline__ float sinpi_md(int m, int d) { return cospi_md(d / 2 - m, d); }
 
+// ------------------------------------------------------------ value types
+// Every core runs on one line (V = float) or on two lines at once (V =
+// float2): the packed FP32 instructions of sm_100-family GPUs apply one
+// add, multiply or fused multiply-add to both halves of a register pair, so
+// two lines cost the instructions of one.  Each packed operation rounds each
+// half exactly as the scalar operation does.
+template <typename V>
+struct VOps;
+template <>
+struct VOps<float> {
+    static __device__ __forceinline__ float add(float a, float b) { return a + b; }
+    static __device__ __forceinline__ float sub(float a, float b) { return a - b; }
+    static __device__ __forceinline__ float mul(float a, float c) { return a * c; }
+    static __device__ __forceinline__ float fma(float a, float c, float b) { return fmaf(a, c, b); }
+    static __device__ __forceinline__ float neg(float a) { return -a; }
+};
+template <>
+struct VOps<float2> {
+    static __device__ __forceinline__ float2 dup(float c) { return make_float2(c, c); }
+    static __device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+    // a - b as a + (-1) b: one rounding, the value of the subtraction
+    static __device__ __forceinline__ float2 sub(float2 a, float2 b) { return __ffma2_rn(b, dup(-1.0f), a); }
+    static __device__ __forceinline__ float2 mul(float2 a, float c) { return __fmul2_rn(a, dup(c)); }
+    static __device__ __forceinline__ float2 fma(float2 a, float c, float2 b) { return __ffma2_rn(a, dup(c), b); }
+    static __device__ __forceinline__ float2 neg(float2 a) { return __fmul2_rn(a, dup(-1.0f)); }
+};
+template <typename V>
+inline constexpr bool kPacked = sizeof(V) == 8;
+
 // (ar + i ai) * exp(-i pi m / d), with the trivial angles resolved at compile time.
-__device__ __forceinline__ void rot(float ar, float ai, int m, int d, float &rr, float &ri)
+template <typename V>
+__device__ __forceinline__ void rot(V ar, V ai, int m, int d, V &rr, V &ri)
 {
+    using O = VOps<V>;
     int r = (m * (8192 / d)) & 16383;
     if (r == 0) { rr = ar; ri = ai; return; }
-    if (r == 8192) { rr = -ar; ri = -ai; return; }
-    if (r == 4096) { rr = ai; ri = -ar; return; }
-    if (r == 12288) { rr = -ai; ri = ar; return; }
+    if (r == 8192) { rr = O::neg(ar); ri = O::neg(ai); return; }
+    if (r == 4096) { rr = ai; ri = O::neg(ar); return; }
+    if (r == 12288) { rr = O::neg(ai); ri = ar; return; }
     float c = cospi_md(m, d), s = sinpi_md(m, d);
-    rr = fmaf(ar, c, ai * s);
-    ri = fmaf(ai, c, -(ar * s));
+    rr = O::fma(ar, c, O::mul(ai, s));
+    ri = O::fma(ai, c, O::mul(ar, -s));
 }
 
 // ------------------------------------------------------------ 1D cores
@@ -70,46 +101,49 @@ __device__ __forceinline__ float cospi3_md(int m, int d)
 __device__ __forceinline__ float sinpi3_md(int m, int d) { return cospi3_md(d / 2 - m, d); }
 
 // (ar + i ai) * exp(-2 pi i k / L) for L = 3 * 2^j.
-__device__ __forceinline__ void rot3(float ar, float ai, int k, int L, float &rr, float &ri)
+template <typename V>
+__device__ __forceinline__ void rot3(V ar, V ai, int k, int L, V &rr, V &ri)
 {
+    using O = VOps<V>;
     if (k % L == 0) { rr = ar; ri = ai; return; }
     const float c = cospi3_md(2 * k, L), s = sinpi3_md(2 * k, L);
-    rr = fmaf(ar, c, ai * s);
-    ri = fmaf(ai, c, -(ar * s));
+    rr = O::fma(ar, c, O::mul(ai, s));
+    ri = O::fma(ai, c, O::mul(ar, -s));
 }
 
-template <int L>
+template <int L, typename V = float>
 struct FFT {
-    static __device__ __forceinline__ void run(float (&re)[L], float (&im)[L])
+    using O = VOps<V>;
+    static __device__ __forceinline__ void run(V (&re)[L], V (&im)[L])
     {
         if constexpr (L % 3 == 0) {
             // radix-3 decimation in time: three interleaved FFTs of L/3, then a
             // 3-point DFT of (E0_k, w^k E1_k, w^2k E2_k), w = exp(-2 pi i / L)
             constexpr int M = L / 3;
-            float r0[M], i0[M], r1[M], i1[M], r2[M], i2[M];
+            V r0[M], i0[M], r1[M], i1[M], r2[M], i2[M];
 #pragma unroll
             for (int j = 0; j < M; ++j) {
                 r0[j] = re[3 * j]; i0[j] = im[3 * j];
                 r1[j] = re[3 * j + 1]; i1[j] = im[3 * j + 1];
                 r2[j] = re[3 * j + 2]; i2[j] = im[3 * j + 2];
             }
-            FFT<M>::run(r0, i0);
-            FFT<M>::run(r1, i1);
-            FFT<M>::run(r2, i2);
+            FFT<M, V>::run(r0, i0);
+            FFT<M, V>::run(r1, i1);
+            FFT<M, V>::run(r2, i2);
             const float h = cospi3_md(256, 1536);  // cos(pi / 6) = sqrt(3) / 2
 #pragma unroll
             for (int k = 0; k < M; ++k) {
-                float br, bi, cr, ci;
+                V br, bi, cr, ci;
                 rot3(r1[k], i1[k], k, L, br, bi);
                 rot3(r2[k], i2[k], 2 * k, L, cr, ci);
-                const float tr = br + cr, ti = bi + ci;      // b + c
-                const float dr = br - cr, di = bi - ci;      // b - c
-                const float mr = r0[k] - 0.5f * tr, mi = i0[k] - 0.5f * ti;
+                const V tr = O::add(br, cr), ti = O::add(bi, ci);  // b + c
+                const V dr = O::sub(br, cr), di = O::sub(bi, ci);  // b - c
+                const V mr = O::fma(tr, -0.5f, r0[k]), mi = O::fma(ti, -0.5f, i0[k]);
                 // -i sqrt(3)/2 (b - c)
-                const float sr = h * di, si = -h * dr;
-                re[k] = r0[k] + tr; im[k] = i0[k] + ti;
-                re[k + M] = mr + sr; im[k + M] = mi + si;
-                re[k + 2 * M] = mr - sr; im[k + 2 * M] = mi - si;
+                const V sr = O::mul(di, h), si = O::mul(dr, -h);
+                re[k] = O::add(r0[k], tr); im[k] = O::add(i0[k], ti);
+                re[k + M] = O::add(mr, sr); im[k + M] = O::add(mi, si);
+                re[k + 2 * M] = O::sub(mr, sr); im[k + 2 * M] = O::sub(mi, si);
             }
         } else {
             radix2(re, im);
@@ -117,132 +151,151 @@ struct FFT {
     }
 
     // radix-2 decimation in time: two interleaved FFTs of L/2, then butterflies
-    static __device__ __forceinline__ void radix2(float (&re)[L], float (&im)[L])
+    static __device__ __forceinline__ void radix2(V (&re)[L], V (&im)[L])
     {
-        float er[L / 2], ei[L / 2], orr[L / 2], oi[L / 2];
+        V er[L / 2], ei[L / 2], orr[L / 2], oi[L / 2];
 #pragma unroll
         for (int j = 0; j < L / 2; ++j) {
             er[j] = re[2 * j]; ei[j] = im[2 * j];
             orr[j] = re[2 * j + 1]; oi[j] = im[2 * j + 1];
         }
-        FFT<L / 2>::run(er, ei);
-        FFT<L / 2>::run(orr, oi);
+        FFT<L / 2, V>::run(er, ei);
+        FFT<L / 2, V>::run(orr, oi);
 #pragma unroll
         for (int k = 0; k < L / 2; ++k) {
-            float tr, ti;
+            V tr, ti;
             rot(orr[k], oi[k], 2 * k, L, tr, ti);  // exp(-2 pi i k / L), L a power of two
-            re[k] = er[k] + tr; im[k] = ei[k] + ti;
-            re[k + L / 2] = er[k] - tr; im[k + L / 2] = ei[k] - ti;
+            re[k] = O::add(er[k], tr); im[k] = O::add(ei[k], ti);
+            re[k + L / 2] = O::sub(er[k], tr); im[k + L / 2] = O::sub(ei[k], ti);
         }
     }
 };
-template <>
-struct FFT<1> {
-    static __device__ __forceinline__ void run(float (&)[1], float (&)[1]) {}
+template <typename V>
+struct FFT<1, V> {
+    static __device__ __forceinline__ void run(V (&)[1], V (&)[1]) {}
 };
 
 // DCT-IV: z_k = sum_j v_j cos(pi (2j+1)(2k+1) / (4M)).  Symmetric matrix.
-template <int M>
+template <int M, typename V = float>
 struct DCT4 {
-    static __device__ __forceinline__ void run(const float (&v)[M], float (&z)[M])
+    using O = VOps<V>;
+    static __device__ __forceinline__ void run(const V (&v)[M], V (&z)[M])
     {
         if constexpr (M <= 4) {
 #pragma unroll
             for (int k = 0; k < M; ++k) {
-                float acc = v[0] * cospi_md(2 * k + 1, 4 * M);
+                V acc = O::mul(v[0], cospi_md(2 * k + 1, 4 * M));
 #pragma unroll
-                for (int j = 1; j < M; ++j) acc = fmaf(v[j], cospi_md((2 * j + 1) * (2 * k + 1), 4 * M), acc);
+                for (int j = 1; j < M; ++j) acc = O::fma(v[j], cospi_md((2 * j + 1) * (2 * k + 1), 4 * M), acc);
                 z[k] = acc;
             }
         } else {
             // u_j = (v_{2j} + i v_{M-1-2j}) exp(-i pi (4j+1) / (4M))
-            float ur[M / 2], ui[M / 2];
+            V ur[M / 2], ui[M / 2];
 #pragma unroll
             for (int j = 0; j < M / 2; ++j) rot(v[2 * j], v[M - 1 - 2 * j], 4 * j + 1, 4 * M, ur[j], ui[j]);
-            FFT<M / 2>::run(ur, ui);
+            FFT<M / 2, V>::run(ur, ui);
             // W_k = U_k exp(-i pi k / M); z_{2k} = Re W_k, z_{M-1-2k} = -Im W_k
 #pragma unroll
             for (int k = 0; k < M / 2; ++k) {
-                float wr, wi;
-                rot(ur[k], ui[k], k, M, wr, wi);
-                z[2 * k] = wr;
-                z[M - 1 - 2 * k] = -wi;
+                if constexpr (kPacked<V>) {
+                    // -Im W_k = Im U_k (-cos(pi k / M)) + Re U_k sin(pi k / M): the
+                    // negated rounding of the scalar form, with no packed negation
+                    // (k = 0: -Im U_0)
+                    if (k == 0) {
+                        z[0] = ur[0];
+                        z[M - 1] = O::neg(ui[0]);
+                    } else {
+                        const float c = cospi_md(k, M), s = sinpi_md(k, M);
+                        z[2 * k] = O::fma(ur[k], c, O::mul(ui[k], s));
+                        z[M - 1 - 2 * k] = O::fma(ui[k], -c, O::mul(ur[k], s));
+                    }
+                } else {
+                    V wr, wi;
+                    rot(ur[k], ui[k], k, M, wr, wi);
+                    z[2 * k] = wr;
+                    z[M - 1 - 2 * k] = -wi;
+                }
             }
         }
     }
 };
 
 // Unscaled DCT-II: y_k = sum_j x_j cos(pi (2j+1) k / (2N)).
-template <int N>
+template <int N, typename V = float>
 struct DCT2 {
-    static __device__ __forceinline__ void run(const float (&x)[N], float (&y)[N])
+    using O = VOps<V>;
+    static __device__ __forceinline__ void run(const V (&x)[N], V (&y)[N])
     {
-        float u[N / 2], v[N / 2], ye[N / 2], yo[N / 2];
+        V u[N / 2], v[N / 2], ye[N / 2], yo[N / 2];
 #pragma unroll
         for (int j = 0; j < N / 2; ++j) {
-            u[j] = x[j] + x[N - 1 - j];
-            v[j] = x[j] - x[N - 1 - j];
+            u[j] = O::add(x[j], x[N - 1 - j]);
+            v[j] = O::sub(x[j], x[N - 1 - j]);
         }
-        DCT2<N / 2>::run(u, ye);
-        DCT4<N / 2>::run(v, yo);
+        DCT2<N / 2, V>::run(u, ye);
+        DCT4<N / 2, V>::run(v, yo);
 #pragma unroll
         for (int m = 0; m < N / 2; ++m) { y[2 * m] = ye[m]; y[2 * m + 1] = yo[m]; }
     }
 };
-template <>
-struct DCT2<1> {
-    static __device__ __forceinline__ void run(const float (&x)[1], float (&y)[1]) { y[0] = x[0]; }
+template <typename V>
+struct DCT2<1, V> {
+    static __device__ __forceinline__ void run(const V (&x)[1], V (&y)[1]) { y[0] = x[0]; }
 };
 
 // Unscaled DCT-III (transpose of DCT2): x_j = sum_k y_k cos(pi (2j+1) k / (2N)).
-template <int N>
+template <int N, typename V = float>
 struct DCT3 {
-    static __device__ __forceinline__ void run(const float (&y)[N], float (&x)[N])
+    using O = VOps<V>;
+    static __device__ __forceinline__ void run(const V (&y)[N], V (&x)[N])
     {
-        float ye[N / 2], yo[N / 2], a[N / 2], b[N / 2];
+        V ye[N / 2], yo[N / 2], a[N / 2], b[N / 2];
 #pragma unroll
         for (int m = 0; m < N / 2; ++m) { ye[m] = y[2 * m]; yo[m] = y[2 * m + 1]; }
-        DCT3<N / 2>::run(ye, a);
-        DCT4<N / 2>::run(yo, b);
+        DCT3<N / 2, V>::run(ye, a);
+        DCT4<N / 2, V>::run(yo, b);
 #pragma unroll
         for (int j = 0; j < N / 2; ++j) {
-            x[j] = a[j] + b[j];
-            x[N - 1 - j] = a[j] - b[j];
+            x[j] = O::add(a[j], b[j]);
+            x[N - 1 - j] = O::sub(a[j], b[j]);
         }
     }
 };
-template <>
-struct DCT3<1> {
-    static __device__ __forceinline__ void run(const float (&y)[1], float (&x)[1]) { x[0] = y[0]; }
+template <typename V>
+struct DCT3<1, V> {
+    static __device__ __forceinline__ void run(const V (&y)[1], V (&x)[1]) { x[0] = y[0]; }
 };
 
-template <int N>
-__device__ __forceinline__ void scale_line(float (&x)[N], AxisScale s)
+template <int N, typename V = float>
+__device__ __forceinline__ void scale_line(V (&x)[N], AxisScale s)
 {
-    x[0] *= s.s0;
+    using O = VOps<V>;
+    x[0] = O::mul(x[0], s.s0);
 #pragma unroll
-    for (int k = 1; k < N; ++k) x[k] *= s.s1;
+    for (int k = 1; k < N; ++k) x[k] = O::mul(x[k], s.s1);
 }
 
-// One direction of the 2D transform along one axis of a line held in registers.
-template <int N, int DIR>
-__device__ __forceinline__ void line_op(float (&x)[N], AxisScale s)
+// One direction of the 2D transform along one axis of a line held in
+// registers (or of two lines, V = float2).
+template <int N, int DIR, typename V = float>
+__device__ __forceinline__ void line_op(V (&x)[N], AxisScale s)
 {
-    float y[N];
+    V y[N];
     if constexpr (DIR == DIR_FWD) {
-        DCT2<N>::run(x, y);
-        scale_line<N>(y, s);
+        DCT2<N, V>::run(x, y);
+        scale_line<N, V>(y, s);
 #pragma unroll
         for (int k = 0; k < N; ++k) x[k] = y[k];
     } else if constexpr (DIR == DIR_INV) {
-        scale_line<N>(x, s);
-        DCT3<N>::run(x, y);
+        scale_line<N, V>(x, s);
+        DCT3<N, V>::run(x, y);
 #pragma unroll
         for (int k = 0; k < N; ++k) x[k] = y[k];
     } else {
-        DCT2<N>::run(x, y);
-        scale_line<N>(y, s);
-        DCT3<N>::run(y, x);
+        DCT2<N, V>::run(x, y);
+        scale_line<N, V>(y, s);
+        DCT3<N, V>::run(y, x);
     }
 }
 

@@ -55,10 +55,13 @@ struct FusedCfg {
     // arrays per chunk (image strips of 16-wide tiles take 16 tiles so that
     // every thread gets a column pair in pass 1)
     static constexpr int G = (HW <= 64) ? 16 : (LAYOUT == LAY_STRIP && W == 16 && H <= 16 ? 16 : 8);
-    // pass 1 on two adjacent columns per thread (8-byte loads): strip layout
-    static constexpr bool PAIR1 = LAYOUT == LAY_STRIP && W >= 16;
+    // pass 1 on two adjacent columns per thread (8-byte loads), run as one
+    // packed line (float2 cores).  Pairing halves the warps of a CTA; measured
+    // on contiguous batches it pays for 32 x 32 only (other shapes lose more
+    // latency hiding than the packed instructions save)
+    static constexpr bool PAIR1 = LAYOUT == LAY_STRIP ? W >= 16 : (H == 32 && W == 32);
     // warps: every thread has at least one line (or column pair) in each pass
-    static constexpr int NW_P1 = G * W / ((W >= 16 && LAYOUT == LAY_STRIP) ? 64 : 32);
+    static constexpr int NW_P1 = G * W / (PAIR1 ? 64 : 32);
     static constexpr int NW_P2 = G * H / 32;
     static constexpr int NW_MAX = NW_P1 < NW_P2 ? NW_P1 : NW_P2;
     static constexpr int NW = NW_MAX > 8 ? 8 : NW_MAX;  // warps per CTA
@@ -271,22 +274,28 @@ __global__ void __launch_bounds__(FusedCfg<H, W, TILED>::THREADS) k_fused(const 
         if constexpr (C::PAIR1) {
 #pragma unroll
             for (int j = 0; j < C::J1; ++j) {
-                const int s2 = 2 * (lane + 32 * (warp + C::NW * j));  // even strip column
-                const int a = s2 / W, col = s2 % W;
+                int a, col;
+                if constexpr (C::LAYOUT == LAY_STRIP) {
+                    const int s2 = 2 * (lane + 32 * (warp + C::NW * j));  // even strip column
+                    a = s2 / W;
+                    col = s2 % W;
+                } else {
+                    // lanes: 8 arrays x 4 column pairs; with the 4-mod-8 slot pitch each
+                    // half-warp's 8-byte accesses cover the 32 banks once
+                    const int combo = warp + C::NW * j;
+                    a = (lane & 7) + 8 * (combo % (C::G / 8));
+                    col = 2 * ((lane >> 3) + 4 * (combo / (C::G / 8)));
+                }
                 if (a < n) {
+                    // the two columns run as one packed line (float2 cores)
                     float2 *q = reinterpret_cast<float2 *>(stage + elem<H, W, TILED>(a, 0, col));
-                    constexpr int RS2 = C::SP / 2;
-                    float x0[H], x1[H];
+                    constexpr int RS2 = row_stride<H, W, TILED>() / 2;
+                    float2 x[H];
 #pragma unroll
-                    for (int i = 0; i < H; ++i) {
-                        const float2 t = q[i * RS2];
-                        x0[i] = t.x;
-                        x1[i] = t.y;
-                    }
-                    line_op<H, DIR>(x0, p.sc.h);
-                    line_op<H, DIR>(x1, p.sc.h);
+                    for (int i = 0; i < H; ++i) x[i] = q[i * RS2];
+                    line_op<H, DIR, float2>(x, p.sc.h);
 #pragma unroll
-                    for (int i = 0; i < H; ++i) q[i * RS2] = make_float2(x0[i], x1[i]);
+                    for (int i = 0; i < H; ++i) q[i * RS2] = x[i];
                 }
             }
         } else

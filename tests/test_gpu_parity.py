@@ -163,11 +163,14 @@ def test_config_image_16x16_tiles(oracle_mod, cuda_dev):
     _assert_parity(oracle_mod, back_b, blocks.astype(np.float64), blocks, 0, "roundtrip", "f-then-i")
     rt_b = inputs.image_to_blocks(rt.cpu().numpy(), 16, 16)
     _assert_parity(oracle_mod, rt_b, blocks.astype(np.float64), blocks, 0, "roundtrip", "tiled-rt")
-    # the contiguous batch gives bit-identical results to the tiled view
+    # the contiguous batch (scalar cores) and the tiled view (packed cores for
+    # the column pass) agree up to rounding order (Section 2.1)
     db = torch.from_numpy(blocks).to(cuda_dev)
-    spec2 = plan.forward(db)
-    torch.cuda.synchronize()
-    assert np.array_equal(spec2.cpu().numpy(), spec_b)
+    spec2 = plan.forward(db).cpu().numpy()
+    _assert_parity(oracle_mod, spec2, ref, blocks, 0, "forward", "contiguous-forward")
+    scale = np.maximum(np.abs(blocks).max(axis=(1, 2), keepdims=True),
+                       np.abs(spec_b).max(axis=(1, 2), keepdims=True))
+    assert np.all(np.abs(spec2.astype(np.float64) - spec_b) <= 4e-6 * scale)
 
 
 @pytest.mark.parametrize("n", [8, 16, 32, 64, 128, 256])
