@@ -299,6 +299,61 @@ __device__ __forceinline__ void line_op(V (&x)[N], AxisScale s)
     }
 }
 
+// line_op on two lines a and b held as plain float arrays (for instance two
+// rows loaded with 16-byte accesses): the first and the last stage run in
+// scalar instructions that read or write the halves of packed pairs, so
+// packing and unpacking cost no moves; everything between runs packed.
+template <int N, int DIR>
+__device__ __forceinline__ void line_op2(float (&a)[N], float (&b)[N], AxisScale s)
+{
+    static_assert(N >= 4, "split of the first stage");
+    using O = VOps<float2>;
+    constexpr int H = N / 2;
+    float2 ye[H], yo[H];
+    if constexpr (DIR == DIR_FWD || DIR == DIR_RT) {
+        // even/odd split of the DCT-II: sums and differences, packed as they form
+        float2 u[H], v[H];
+#pragma unroll
+        for (int j = 0; j < H; ++j) {
+            u[j] = make_float2(a[j] + a[N - 1 - j], b[j] + b[N - 1 - j]);
+            v[j] = make_float2(a[j] - a[N - 1 - j], b[j] - b[N - 1 - j]);
+        }
+        DCT2<H, float2>::run(u, ye);
+        DCT4<H, float2>::run(v, yo);
+        if constexpr (DIR == DIR_FWD) {
+#pragma unroll
+            for (int m = 0; m < H; ++m) {
+                const float se = m == 0 ? s.s0 : s.s1;
+                a[2 * m] = ye[m].x * se; b[2 * m] = ye[m].y * se;
+                a[2 * m + 1] = yo[m].x * s.s1; b[2 * m + 1] = yo[m].y * s.s1;
+            }
+            return;
+        }
+        // round trip: E_n^2 between the core and its adjoint (even outputs ye,
+        // odd outputs yo are exactly the DCT-III's split inputs)
+        ye[0] = O::mul(ye[0], s.s0);
+#pragma unroll
+        for (int m = 1; m < H; ++m) ye[m] = O::mul(ye[m], s.s1);
+#pragma unroll
+        for (int m = 0; m < H; ++m) yo[m] = O::mul(yo[m], s.s1);
+    } else {
+        // scaled inputs of the DCT-III, split into even and odd, packed as they form
+#pragma unroll
+        for (int m = 0; m < H; ++m) {
+            const float se = m == 0 ? s.s0 : s.s1;
+            ye[m] = make_float2(a[2 * m] * se, b[2 * m] * se);
+            yo[m] = make_float2(a[2 * m + 1] * s.s1, b[2 * m + 1] * s.s1);
+        }
+    }
+    float2 ea[H], ob[H];
+    DCT3<H, float2>::run(ye, ea);
+    DCT4<H, float2>::run(yo, ob);
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+        a[j] = ea[j].x + ob[j].x; a[N - 1 - j] = ea[j].x - ob[j].x;
+        b[j] = ea[j].y + ob[j].y; b[N - 1 - j] = ea[j].y - ob[j].y;
+    }
+}
 
 // Fill this translation unit's constant table from a device buffer holding
 // cos(pi r / 8192), r = 0..4096.

