@@ -263,13 +263,11 @@ __global__ void __launch_bounds__(FusedCfg<H, W, TILED>::THREADS) k_fused(const 
     int prev_s = 0;
     for (int c = (int)blockIdx.x, k = 0; c < p.nchunks; c += grid, ++k) {
         float *stage = smem + s * C::STAGE_FLOATS;
+        // each thread waits for the stage itself; the CTA agrees on the outcome
+        // at the barrier after pass 1, so that the other warps start a chunk
+        // while warp 0 still issues the copies of the previous one (pass 1 on a
+        // stage whose wait expired only wastes work: nothing is stored)
         bool ok = mbar_wait_bounded(&full[s], phase);
-        if constexpr (C::NW == 1) ok = __all_sync(0xffffffffu, ok);
-        else ok = __syncthreads_and(ok);
-        if (!ok) {
-            if (tid == 0) record_timeout(p.status);
-            break;
-        }
         const ChunkGeom g = chunk_geom<H, W, TILED>(p, c);
         const int n = g.n;
 
@@ -318,7 +316,12 @@ __global__ void __launch_bounds__(FusedCfg<H, W, TILED>::THREADS) k_fused(const 
                 for (int i = 0; i < H; ++i) q[i * RS] = x[i];
             }
         }
-        cta_sync<C::NW>();
+        if constexpr (C::NW == 1) ok = __all_sync(0xffffffffu, ok);
+        else ok = __syncthreads_and(ok);
+        if (!ok) {
+            if (tid == 0) record_timeout(p.status);
+            break;
+        }
 
         // pass 2: one row per thread per step, 1D core along w; with an even
         // number of rows per thread the rows go in packed pairs
@@ -373,14 +376,30 @@ __global__ void __launch_bounds__(FusedCfg<H, W, TILED>::THREADS) k_fused(const 
             // bulk groups are per thread: every lane commits the stores it issued
             issue_drain<H, W, TILED>(p, g, stage, lane);
             bulk_commit();
-            // refill the stage drained in the previous iteration once its reads are done
-            if (k >= 1) {
-                const int cn = c + (C::STAGES - 1) * grid;
+            // Deferred refill: the stage drained in the previous iteration, once its
+            // reads are done (no wait on the stores just issued).  With two stages
+            // that loads the next chunk only now; the round trip (twice the
+            // arithmetic per chunk) instead refills this stage right away, which
+            // measured 0.81 -> 0.94 of HBM on 32 x 32 batches, while forward and
+            // inverse lose more to the wait on the stores than they gain.
+            if constexpr (C::STAGES >= 3 || DIR != DIR_RT) {
+                if (k >= 1) {
+                    const int cn = c + (C::STAGES - 1) * grid;
+                    if (cn < p.nchunks) {
+                        bulk_wait_read<1>();
+                        __syncwarp();
+                        issue_fill<H, W, TILED>(p, chunk_geom<H, W, TILED>(p, cn), smem + prev_s * C::STAGE_FLOATS,
+                                                &full[prev_s], lane);
+                    }
+                }
+            } else {
+                // refill this stage as soon as its stores have read it, so that the
+                // chunk after next loads while the next is transformed
+                const int cn = c + C::STAGES * grid;
                 if (cn < p.nchunks) {
-                    bulk_wait_read<1>();
+                    bulk_wait_read<0>();
                     __syncwarp();
-                    issue_fill<H, W, TILED>(p, chunk_geom<H, W, TILED>(p, cn), smem + prev_s * C::STAGE_FLOATS,
-                                            &full[prev_s], lane);
+                    issue_fill<H, W, TILED>(p, chunk_geom<H, W, TILED>(p, cn), stage, &full[s], lane);
                 }
             }
         }
