@@ -123,13 +123,13 @@ int bdct_execute_tiled(const bdct_plan *plan, unsigned kind, const float *in, fl
  * memory works but each copy then blocks the host).  The paper times complete
  * calls including input copies (Sections 4.1-4.2) and names streaming
  * workloads with data transfers as future work (Section 8).
- * bdct_plan_set_host_staging allocates the plan's device staging (two slots
+ * bdct_plan_set_host_staging allocates the plan's device staging (four slots
  * of two chunk_bytes buffers, rounded down to whole arrays, at least one) and
  * three private streams; call it once before the host entry points.
  * bdct_execute_host moves `batch` contiguous arrays from h_in through the
  * device and back to h_out in chunks: the host-to-device copy of one chunk,
- * the transforms of the previous chunk and the device-to-host copy of the one
- * before overlap.  kinds[0..nkinds-1] (1..8 directions, each planned) are
+ * the transforms of an earlier chunk and the device-to-host copy of one
+ * before it overlap.  kinds[0..nkinds-1] (1..8 directions, each planned) are
  * applied in order to every chunk on the device, so an intermediate spectrum
  * never crosses the host link.  bdct_execute_tiled_host does the same for an
  * img_rows x img_cols host image (leading dimension img_cols) in bands of

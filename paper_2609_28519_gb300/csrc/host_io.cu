@@ -3,9 +3,9 @@
 // The paper measures complete calls including input copies (Sections 4.1,
 // 4.2) and lists first-use and streaming workloads with data transfers as
 // future work (Section 8).  These entry points take HOST buffers: the data
-// moves in chunks through plan-owned device staging, double-buffered so that
-// the host-to-device copy of one chunk, the transforms of the previous chunk
-// and the device-to-host copy of the one before run at the same time on three
+// moves in chunks through plan-owned device staging (four slots) so that
+// the host-to-device copy of one chunk, the transforms of an earlier chunk
+// and the device-to-host copy of one before it run at the same time on three
 // streams (one per copy direction, one for the kernels).  A sequence of directions (for example forward
 // then inverse) is applied to each chunk on the device, so intermediates never
 // cross the host link.
@@ -40,7 +40,7 @@ int dir_of_kind(unsigned k, Dir *d)
 
 void bdct::host_staging_free(bdct_plan *p)
 {
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < kStageSlots; ++i) {
         for (int j = 0; j < 2; ++j)
             if (p->stage[i][j]) cudaFree(p->stage[i][j]);
         if (p->ev_in[i]) cudaEventDestroy(p->ev_in[i]);
@@ -69,10 +69,10 @@ extern "C" int bdct_plan_set_host_staging(bdct_plan *plan, size_t chunk_bytes)
     chunk_bytes = (chunk_bytes / arr) * arr;
     host_staging_free(plan);
     cudaError_t e = cudaSuccess;
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+    for (int i = 0; i < kStageSlots && e == cudaSuccess; ++i)
         for (int j = 0; j < 2 && e == cudaSuccess; ++j) e = cudaMalloc(&plan->stage[i][j], chunk_bytes);
     if (e != cudaSuccess) { host_staging_free(plan); return BDCT_ERR_NO_MEMORY; }
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    for (int i = 0; i < kStageSlots && e == cudaSuccess; ++i) {
         e = cudaEventCreateWithFlags(&plan->ev_in[i], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&plan->ev_done[i], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&plan->ev_out[i], cudaEventDisableTiming);
@@ -104,12 +104,12 @@ static int pipeline(const bdct_plan *p, const float *h_in, float *h_out, long lo
     if (e != cudaSuccess) return host_fail(e);
     const long long nch = (nunits + units_per_chunk - 1) / units_per_chunk;
     for (long long c = 0; c < nch; ++c) {
-        const int slot = (int)(c & 1);
+        const int slot = (int)(c % kStageSlots);
         const long long u0 = c * units_per_chunk;
         const long long nu = (nunits - u0) < units_per_chunk ? (nunits - u0) : units_per_chunk;
         const size_t bytes = (size_t)nu * unit_floats * sizeof(float);
         // copy in (after the slot's previous chunk has been copied out)
-        if (c >= 2) e = cudaStreamWaitEvent(p->copy_stream, p->ev_out[slot], 0);
+        if (c >= kStageSlots) e = cudaStreamWaitEvent(p->copy_stream, p->ev_out[slot], 0);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(p->stage[slot][0], h_in + (size_t)u0 * unit_floats, bytes, cudaMemcpyHostToDevice,
                                 p->copy_stream);

@@ -5,6 +5,10 @@
 
 #include "bdct_internal.h"
 
+// Staging slots of the host-buffer pipeline: with four, the copy-in of a
+// chunk never waits for the copy-out of an earlier chunk in a short sequence.
+constexpr int kStageSlots = 4;
+
 struct bdct_plan {
     int rows = 0, cols = 0;
     unsigned kind = 0;
@@ -28,13 +32,13 @@ struct bdct_plan {
     __nv_bfloat16 *tc_ops = nullptr;
     size_t tc_off[3] = {0, 0, 0};
     int tc_terms = 3;
-    // host-buffer execution (bdct_plan_set_host_staging): two slots of two
-    // device buffers, and streams/events of the copy-in / transform /
+    // host-buffer execution (bdct_plan_set_host_staging): kStageSlots slots of
+    // two device buffers, and streams/events of the copy-in / transform /
     // copy-out pipeline
-    float *stage[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    float *stage[kStageSlots][2] = {};
     size_t stage_bytes = 0;
     cudaStream_t copy_stream = nullptr, comp_stream = nullptr, d2h_stream = nullptr;
-    cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
+    cudaEvent_t ev_in[kStageSlots] = {}, ev_done[kStageSlots] = {}, ev_out[kStageSlots] = {};
     cudaEvent_t ev_start = nullptr, ev_end = nullptr;
 };
 
