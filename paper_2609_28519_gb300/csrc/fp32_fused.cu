@@ -53,8 +53,10 @@ struct FusedCfg {
     static constexpr int HW = H * W;
     static constexpr int LAYOUT = TILED ? LAY_STRIP : LAY_SLOT;
     // arrays per chunk (image strips of 16-wide tiles take 16 tiles so that
-    // every thread gets a column pair in pass 1)
-    static constexpr int G = (HW <= 64) ? 16 : (LAYOUT == LAY_STRIP && W == 16 && H <= 16 ? 16 : 8);
+    // every thread gets a column pair in pass 1; contiguous batches of
+    // 256-element arrays take 16, measured 0.82 -> 0.94 of HBM for 16 x 16)
+    static constexpr int G = (HW <= 64 || (LAYOUT == LAY_SLOT && HW == 256)) ? 16
+                             : (LAYOUT == LAY_STRIP && W == 16 && H <= 16 ? 16 : 8);
     // pass 1 on two adjacent columns per thread (8-byte loads), run as one
     // packed line (float2 cores).  Pairing halves the warps of a CTA; measured
     // on contiguous batches it pays for 32 x 32 only (other shapes lose more
@@ -83,6 +85,7 @@ struct FusedCfg {
     static_assert(J1 >= 1 && J2 >= 1 && J1 * THREADS * (PAIR1 ? 2 : 1) == G * W && J2 * THREADS == G * H,
                   "lane mapping");
     static_assert((P % 8) == 4 && (SP % 8) == 4, "pitches must be 4 mod 8 floats");
+    static_assert(LAYOUT == LAY_STRIP || G % 8 == 0, "slot-layout lanes span 8 arrays");
     static_assert(H <= 32 && W <= 32, "sides 64 and 128 use the ring kernels");
 };
 
