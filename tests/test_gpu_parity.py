@@ -50,12 +50,39 @@ def test_fused_shapes_all_kinds(oracle_mod, cuda_dev, h, w, norm):
     from paper_2609_28519_gb300 import Plan
     plan = Plan(h, w, norm=norm, path="fp32")
     assert plan.info().variant == 1
-    per_chunk = 16 if h * w <= 64 else (8 if max(h, w) <= 32 else 2)
+    per_chunk = 16 if (h * w <= 64 or h * w == 256) else (8 if max(h, w) <= 32 else 2)
     batch = 5 * per_chunk + 3  # several chunks and a ragged tail
     x = inputs.uniform(1000 + h * 7 + w, batch, h, w)
     for kind in KINDS:
         y = _run(plan, kind, x, cuda_dev)
         _assert_parity(oracle_mod, y, _ref(oracle_mod, kind, x, norm), x, norm, kind, (h, w, norm, kind))
+
+
+@pytest.mark.parametrize("h,w", FUSED_SHAPES[:9])
+def test_fused_tiled_all_shapes(oracle_mod, cuda_dev, h, w):
+    """Image strips for every fused shape: the column pass runs packed column
+    pairs for w >= 16 and the row pass packed row pairs where a thread has two
+    rows; every block row ends in a partial chunk of tiles, and input and
+    output sit in wider buffers (leading dimension > width) whose padding
+    must stay untouched."""
+    import torch
+    from paper_2609_28519_gb300 import Plan
+    g = 16 if (h * w <= 64 or (w == 16 and h <= 16)) else 8  # tiles per chunk of a strip
+    tpr = 2 * g + 3
+    rows, cols = 3 * h, tpr * w
+    img = inputs.gaussian(2500 + h + 5 * w, 1, rows, cols)[0]
+    blocks = inputs.image_to_blocks(img, h, w)
+    src = torch.zeros(rows, cols + 12, device=cuda_dev)
+    src[:, :cols] = torch.from_numpy(img).to(cuda_dev)
+    plan = Plan(h, w, path="fp32")
+    assert plan.info().variant == 1
+    for kind in KINDS:
+        dst = torch.full((rows, cols + 8), float("nan"), device=cuda_dev)
+        plan.execute_tiled(kind, src[:, :cols], dst[:, :cols])
+        torch.cuda.synchronize()
+        got = inputs.image_to_blocks(dst[:, :cols].cpu().numpy(), h, w)
+        _assert_parity(oracle_mod, got, _ref(oracle_mod, kind, blocks, 0), blocks, 0, kind, ("strip", h, w, kind))
+        assert torch.isnan(dst[:, cols:]).all(), (h, w, kind)
 
 
 @pytest.mark.parametrize("h,w", RING_SHAPES)
