@@ -82,6 +82,11 @@ struct FusedCfg {
     // 10% faster) and is mixed on contiguous batches
     static constexpr bool PAIR2 = LAYOUT == LAY_STRIP && J2 % 2 == 0 && W >= 4;
     static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + STAGES * 8;
+    // register-allocation hint (resident CTAs per SM; 0 = none).  Measured: the
+    // image strips and the 64-element batches run faster with the allocation
+    // the hint gives (16x16 image step 15.0 -> 14.65 us, 8x8 round trip 0.76
+    // -> 0.80 of HBM), the other batches without it (16x16 0.93 -> 0.86 with)
+    static constexpr int MIN_CTAS = TILED ? 2 : (HW <= 64 ? 1 : 0);
     static_assert(J1 >= 1 && J2 >= 1 && J1 * THREADS * (PAIR1 ? 2 : 1) == G * W && J2 * THREADS == G * H,
                   "lane mapping");
     static_assert((P % 8) == 4 && (SP % 8) == 4, "pitches must be 4 mod 8 floats");
@@ -226,6 +231,15 @@ __device__ __forceinline__ void issue_drain(const FusedParams &p, const ChunkGeo
     }
 }
 
+// Error path: the copies issued for chunks first .. filled - 1 of this CTA
+// (chunk i in stage i mod stages, phase (i / stages) mod 2) land, each wait
+// bounded, before the CTA exits.
+__device__ __forceinline__ void drain_fills(uint64_t *full, int stages, int first, int filled)
+{
+    for (int i = first; i < filled; ++i)
+        if (!mbar_wait_bounded(&full[i % stages], (uint32_t)((i / stages) & 1))) break;
+}
+
 template <int NW>
 __device__ __forceinline__ void cta_sync()
 {
@@ -234,7 +248,7 @@ __device__ __forceinline__ void cta_sync()
 }
 
 template <int H, int W, int DIR, bool TILED>
-__global__ void __launch_bounds__(FusedCfg<H, W, TILED>::THREADS) k_fused(const FusedParams p)
+__global__ void __launch_bounds__(FusedCfg<H, W, TILED>::THREADS, FusedCfg<H, W, TILED>::MIN_CTAS) k_fused(const FusedParams p)
 {
     using C = FusedCfg<H, W, TILED>;
     extern __shared__ __align__(128) float smem[];
@@ -252,7 +266,8 @@ __global__ void __launch_bounds__(FusedCfg<H, W, TILED>::THREADS) k_fused(const 
     pdl_wait_prerequisites();
     __syncthreads();
 
-    // prologue: fill every stage
+    // prologue: fill every stage (chunk k of this CTA uses stage k mod STAGES,
+    // phase (k / STAGES) mod 2)
     if (warp == 0) {
         for (int s = 0; s < C::STAGES; ++s) {
             const int c = (int)blockIdx.x + s * grid;
@@ -260,7 +275,9 @@ __global__ void __launch_bounds__(FusedCfg<H, W, TILED>::THREADS) k_fused(const 
                 issue_fill<H, W, TILED>(p, chunk_geom<H, W, TILED>(p, c), smem + s * C::STAGE_FLOATS, &full[s], lane);
         }
     }
+    constexpr bool DEFER = C::STAGES >= 3 || DIR != DIR_RT;  // refill policy (see the end of the loop)
 
+    int failed_at = -1;   // iteration whose stage wait expired, if any
     int s = 0;            // stage of the current chunk
     uint32_t phase = 0;   // parity of the stage's current use
     int prev_s = 0;
@@ -322,7 +339,7 @@ __global__ void __launch_bounds__(FusedCfg<H, W, TILED>::THREADS) k_fused(const 
         if constexpr (C::NW == 1) ok = __all_sync(0xffffffffu, ok);
         else ok = __syncthreads_and(ok);
         if (!ok) {
-            if (tid == 0) record_timeout(p.status);
+            failed_at = k;
             break;
         }
 
@@ -385,7 +402,7 @@ __global__ void __launch_bounds__(FusedCfg<H, W, TILED>::THREADS) k_fused(const 
             // arithmetic per chunk) instead refills this stage right away, which
             // measured 0.81 -> 0.94 of HBM on 32 x 32 batches, while forward and
             // inverse lose more to the wait on the stores than they gain.
-            if constexpr (C::STAGES >= 3 || DIR != DIR_RT) {
+            if constexpr (DEFER) {
                 if (k >= 1) {
                     const int cn = c + (C::STAGES - 1) * grid;
                     if (cn < p.nchunks) {
@@ -408,6 +425,16 @@ __global__ void __launch_bounds__(FusedCfg<H, W, TILED>::THREADS) k_fused(const 
         }
         prev_s = s;
         if (++s == C::STAGES) { s = 0; phase ^= 1u; }
+    }
+    if (failed_at >= 0 && tid == 0) {
+        record_timeout(p.status);
+        // chunks whose copies were issued by then: the prologue's, plus one
+        // refill per finished iteration (from the second on when deferred)
+        const int k = failed_at;
+        const int n_own = (p.nchunks - (int)blockIdx.x + grid - 1) / grid;
+        int issued = DEFER ? (k + C::STAGES - 1 > C::STAGES ? k + C::STAGES - 1 : C::STAGES) : k + C::STAGES;
+        if (issued > n_own) issued = n_own;
+        drain_fills(full, C::STAGES, k, issued);
     }
     if (warp == 0) bulk_wait<0>();
 }
