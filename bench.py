@@ -168,20 +168,39 @@ def run_reference(args):
     return 0
 
 
-def traffic_from_profiles(kernel_key: str):
-    """DRAM bytes per launch recorded by an ncu capture, if the kernel's source
-    file has not changed since (the summary stores the source hash)."""
+# Sources of each captured kernel's translation unit (the kernel file and the
+# headers it includes).
+KERNEL_SOURCES = {"k_fused": ["fp32_fused.cu", "dct_cores.cuh", "ptx.cuh", "bdct_internal.h"],
+                  "k_tc_split": ["tc_split.cu", "ptx.cuh", "bdct_internal.h"]}
+
+
+def source_key(kernel_key: str) -> str:
+    """sha256[:16] of the kernel's sources with // comments and blank lines
+    removed: an edit of the code invalidates a recorded capture, an edit of
+    the comments does not."""
     import hashlib
+    base = kernel_key.split("<")[0]
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES[base]:
+        path = os.path.join(ROOT, "paper_2609_28519_gb300", "csrc", name)
+        for ln in open(path, encoding="utf-8"):
+            code = ln.split("//")[0].rstrip()
+            if code:
+                h.update(code.encode() + b"\n")
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profiles(kernel_key: str):
+    """DRAM bytes per launch recorded by an ncu capture, if the kernel's
+    sources have not changed since (the record stores their source key)."""
     p = os.path.join(ROOT, "profiles", "traffic_per_launch.txt")
     if not os.path.exists(p):
         return None
-    fname = "tc_split.cu" if kernel_key.startswith("k_tc_split") else "fp32_fused.cu"
-    src = os.path.join(ROOT, "paper_2609_28519_gb300", "csrc", fname)
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    key = source_key(kernel_key)
     for ln in open(p):
         parts = ln.split()
         if len(parts) >= 3 and parts[0] == kernel_key and not ln.startswith("#"):
-            if parts[2] == h:
+            if parts[2] == key:
                 return float(parts[1])
     return None
 

@@ -14,8 +14,10 @@
 // On-chip organization (the GPU counterpart of the paper's Algorithm 1 and of
 // its Section 3.2 padded stride): arrays are staged in shared memory by TMA
 // bulk copies, one array per 16-byte-padded slot; pass 1 gives each thread one
-// column, pass 2 one row, and each line lives in registers while its 1D core
-// runs.  HBM traffic is one read and one write of every element.
+// column (or two adjacent columns), pass 2 one row (or two rows), and each
+// line lives in registers while its 1D core runs; two lines of a thread run
+// as one packed line (float2 cores: one packed FP32 instruction serves both).
+// HBM traffic is one read and one write of every element.
 #include <cuda_runtime.h>
 
 #include "bdct_internal.h"
@@ -32,19 +34,22 @@ namespace bdct {
 // image tiles).  Warp 0 fills stages ahead with TMA bulk copies completing on
 // the stage's mbarrier and drains finished stages with TMA bulk stores, so
 // HBM reads, the arithmetic and HBM writes of different chunks overlap; all
-// warps share the arithmetic of a chunk.
+// warps share the arithmetic of a chunk.  Every thread waits on the stage's
+// mbarrier itself; the CTA-wide agreement on that (bounded) wait comes at the
+// barrier after pass 1, so warp 0's copy issue for the previous chunk does
+// not hold the other warps back.
 //
 // Two shared-memory layouts, both bank-conflict-free for the column pass
-// (one column per thread, scalar loads) and the row pass (one row per
-// thread, 16-byte loads):
+// (one column per thread, scalar loads, or a column pair, 8-byte loads) and
+// the row pass (one row per thread, 16-byte loads):
 //  * contiguous batch -> "slots": array a at a*P, P = h*w + 4 floats, one bulk
 //    copy per array; a warp instruction touches 8 arrays at once (4 adjacent
 //    columns each in pass 1, one row each in pass 2), and the 16-byte gap
 //    between slots spreads them over all 32 banks;
 //  * tiled image -> "strip": the G tiles of a block row side by side, row r
 //    at r*SP, SP = G*w + 4 floats, one bulk copy per image row; pass 1 lanes
-//    take 32 adjacent strip columns, pass 2 lanes take 8 rows of one tile,
-//    which the odd 16-byte row pitch spreads over all banks.
+//    take 32 adjacent strip columns (or column pairs), pass 2 lanes take 8
+//    rows of one tile, which the odd 16-byte row pitch spreads over all banks.
 // Shared-memory layouts of a stage (see the comment above).
 enum Layout { LAY_SLOT = 0, LAY_STRIP = 1 };
 
