@@ -15,9 +15,10 @@
 //    16-byte cp.async copies placed at the same swizzled positions and leave
 //    by vector stores;
 //  * NG consumer groups (named barriers, no CTA-wide synchronization) take
-//    the slots round robin, about three slots per group, so each group's next
-//    arrays are in flight while it computes; a group transforms every row of
-//    its array, then every column, in place.
+//    the slots round robin, about three slots per group (two for the round
+//    trips, which run more groups), so each group's next arrays are in
+//    flight while it computes; a group transforms every row of its array,
+//    then every column, in place.
 //
 // Slot layout (the GPU counterpart of the paper's padded stride, Section
 // 3.2): columns 32b .. 32b+31 of all rows form box b; row r of a box is 128
@@ -75,7 +76,8 @@ struct RingCfg {
     static constexpr int S_MAX = (kRingMaxSmem - 2048) / SLOT_BYTES;
     // about three slots per group, so that a group's next arrays load while
     // it computes; the slot count is a multiple of the group count (a group
-    // always reuses slots it consumed itself)
+    // always reuses slots it consumed itself, which the slot barriers' parity
+    // tracking relies on)
     // (round trips, twice the arithmetic per array, run more groups over two
     // slots each: 64 x 64 seven groups, 0.67 -> 0.76 of HBM, while forward
     // and inverse measured 0.90 -> 0.81 that way; the rectangles three groups,
