@@ -346,17 +346,29 @@ __device__ __forceinline__ void line_inverse(float *line, float *scr, const floa
         four_step_c<N>(A, t, rr, ri);
     }
     __syncwarp();  // all of A read before x overwrites the line
+    // z_m = conj(result): v_{2m} = Re z_m, v_{2m+1} = -Im z_m, and x_{2i} = v_i
+    // (i < L), x_{2i+1} = v_{N-1-i}.  For m < L/2 the four outputs x_{4m} ..
+    // x_{4m+3} are v_{2m}, v_{2m'+1}, v_{2m+1}, v_{2m'} with m' = L-1-m, whose
+    // z sits in thread T-1-t at slot (JC-1-j, L2-1-k2) (k2 < L2/2 exactly when
+    // m < L/2): the partner's values arrive by shuffle and the four outputs
+    // leave as two 8-byte stores, taken in opposite order by the two halves of
+    // each 16-lane group so that one store instruction covers distinct banks.
+    const int lane = (int)(threadIdx.x & 31);
+    const int src = lane - t + (C::T - 1 - t);
+    const int swap = (lane >> 3) & 1;
+    float2 *x2 = reinterpret_cast<float2 *>(line);
 #pragma unroll
     for (int j = 0; j < C::JC; ++j) {
 #pragma unroll
-        for (int k2 = 0; k2 < C::L2; ++k2) {
+        for (int k2 = 0; k2 < C::L2 / 2; ++k2) {
+            // each lane sends its slot (JC-1-j, L2-1-k2) and receives the partner's
+            const float pe = __shfl_sync(0xffffffffu, rr[C::JC - 1 - j][C::L2 - 1 - k2], src);
+            const float po = __shfl_sync(0xffffffffu, ri[C::JC - 1 - j][C::L2 - 1 - k2], src);
             const int m = t + C::T * j + C::L1 * k2;
-            // z_m = conj(result); v_{2m} = Re z_m, v_{2m+1} = Im z_m
-            const float v_even = rr[j][k2], v_odd = -ri[j][k2];
-            // x_{2i} = v_i (i < L), x_{2i+1} = v_{N-1-i}
-            const int i0 = 2 * m, i1 = 2 * m + 1;
-            if (i0 < C::L) line[2 * i0] = v_even; else line[2 * (N - 1 - i0) + 1] = v_even;
-            if (i1 < C::L) line[2 * i1] = v_odd; else line[2 * (N - 1 - i1) + 1] = v_odd;
+            const float2 lo = make_float2(rr[j][k2], -po);  // x_{4m}, x_{4m+1}
+            const float2 hi = make_float2(-ri[j][k2], pe);  // x_{4m+2}, x_{4m+3}
+            x2[2 * m + swap] = swap ? hi : lo;
+            x2[2 * m + 1 - swap] = swap ? lo : hi;
         }
     }
     __syncwarp();
