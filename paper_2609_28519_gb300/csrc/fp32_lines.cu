@@ -296,36 +296,54 @@ __device__ __forceinline__ void line_inverse(float *line, float *scr, const floa
     // written over the line once every y has been read
     float2 *Zc = reinterpret_cast<float2 *>(C::INPLACE ? line : scr);
     float qr[C::JC][C::L2], qi[C::JC][C::L2];
-    // y -> conj(Z): each k from y_k, y_{N-k}, y_{L-k}, y_{L+k}
+    // y -> conj(Z): Z_k needs y_k, y_{N-k}, y_{L-k}, y_{L+k} and the table
+    // entries k and L-k, and Z_{L-k} needs the same, so one thread takes both:
+    // k runs over this thread's slots with k2 < L2/2 (k < L/2), and the second
+    // half of the slot array holds Z_{L-k} (for k = 0: Z_{L/2}, its own mirror)
+    const float sy = FOLD ? 1.0f : s.s1;  // with FOLD the table carries s_1 / 2
+    const float hf = FOLD ? 1.0f : 0.5f;
 #pragma unroll
     for (int j = 0; j < C::JC; ++j) {
 #pragma unroll
-        for (int k2 = 0; k2 < C::L2; ++k2) {
+        for (int k2 = 0; k2 < C::L2 / 2; ++k2) {
             const int k = t + C::T * j + C::L1 * k2;
-            float2 zc;
+            float2 za, zb;  // conj Z_k and conj Z_{L-k}
             if (k == 0) {
                 const float v0 = 2.0f * line[0] * s.s0;  // factor 2 carries 1/L
                 const float vl = 1.41421356237309505f * line[C::L] * s.s1;
-                zc = make_float2(0.5f * (v0 + vl), -0.5f * (v0 - vl));
+                za = make_float2(0.5f * (v0 + vl), -0.5f * (v0 - vl));
+                constexpr int H = C::L / 2;
+                const float yh = line[H] * sy, ynh = line[N - H] * sy;
+                const float4 w = ts[H];
+                const float2 V = cmulc(make_float2(yh, -ynh), make_float2(w.z, w.w));
+                const float2 E = make_float2(hf * (V.x + V.x), hf * (V.y - V.y));
+                const float2 D = make_float2(hf * (V.x - V.x), hf * (V.y + V.y));
+                const float2 O = cmulc(D, make_float2(w.x, w.y));
+                zb = make_float2(E.x - O.y, -(E.y + O.x));
             } else {
-                const float sy = FOLD ? 1.0f : s.s1;  // with FOLD the table carries s_1 / 2
                 const float yk = line[k] * sy, ynk = line[N - k] * sy;
                 const float ylk = line[C::L - k] * sy, ylpk = line[C::L + k] * sy;
                 const float4 w = ts[k], wl = ts[C::L - k];
                 // V_k = conj(W_k) (y_k - i y_{N-k}), V_{L-k} likewise
                 const float2 Vk = cmulc(make_float2(yk, -ynk), make_float2(w.z, w.w));
                 const float2 Vl = cmulc(make_float2(ylk, -ylpk), make_float2(wl.z, wl.w));
-                const float hf = FOLD ? 1.0f : 0.5f;
                 const float2 E = make_float2(hf * (Vk.x + Vl.x), hf * (Vk.y - Vl.y));
                 const float2 D = make_float2(hf * (Vk.x - Vl.x), hf * (Vk.y + Vl.y));
                 const float2 O = cmulc(D, make_float2(w.x, w.y));  // / exp(-2 pi i k / N)
-                zc = make_float2(E.x - O.y, -(E.y + O.x));         // conj(E + i O)
+                za = make_float2(E.x - O.y, -(E.y + O.x));         // conj(E + i O)
+                // for L-k the two V swap: E -> (E.x, -E.y), D -> (-D.x, D.y)
+                const float2 Ol = cmulc(make_float2(-D.x, D.y), make_float2(wl.x, wl.y));
+                zb = make_float2(E.x - Ol.y, -(Ol.x - E.y));
             }
+            const int km = k == 0 ? C::L / 2 : C::L - k;
             if constexpr (C::INPLACE) {
-                qr[j][k2] = zc.x;
-                qi[j][k2] = zc.y;
+                qr[j][k2] = za.x;
+                qi[j][k2] = za.y;
+                qr[j][k2 + C::L2 / 2] = zb.x;
+                qi[j][k2 + C::L2 / 2] = zb.y;
             } else {
-                Zc[k] = zc;
+                Zc[k] = za;
+                Zc[km] = zb;
             }
         }
     }
@@ -333,9 +351,14 @@ __device__ __forceinline__ void line_inverse(float *line, float *scr, const floa
     float rr[C::JC][C::L2], ri[C::JC][C::L2];
     if constexpr (C::INPLACE) {
 #pragma unroll
-        for (int j = 0; j < C::JC; ++j)
+        for (int j = 0; j < C::JC; ++j) {
 #pragma unroll
-            for (int k2 = 0; k2 < C::L2; ++k2) Zc[t + C::T * j + C::L1 * k2] = make_float2(qr[j][k2], qi[j][k2]);
+            for (int k2 = 0; k2 < C::L2 / 2; ++k2) {
+                const int k = t + C::T * j + C::L1 * k2;
+                Zc[k] = make_float2(qr[j][k2], qi[j][k2]);
+                Zc[k == 0 ? C::L / 2 : C::L - k] = make_float2(qr[j][k2 + C::L2 / 2], qi[j][k2 + C::L2 / 2]);
+            }
+        }
         __syncwarp();
         four_step_a_inplace<N>(Zc, ta, t);
         four_step_c_inplace<N>(Zc, t, rr, ri);
