@@ -234,12 +234,39 @@ __device__ __forceinline__ void line_forward(float *line, float *scr, const floa
         __syncwarp();
         four_step_c<N>(A, t, zr, zi);
     }
-    // the line buffer is free (its last reader passed a warp barrier)
+    // the line buffer is free (its last reader passed a warp barrier).
+    // The outputs k and L-k both come from Z_k and Z_{L-k} (the latter's E and O
+    // are the former's with the imaginary parts negated), so one thread takes
+    // both: k runs over this thread's slots with k2 < L2/2 (k < L/2); thread 0
+    // also takes k = L/2, its own mirror.
     const int src = lane - t + (C::T - t) % C::T;
+    // y_k and y_{N-k} of one index from its E and O and table entry
+    auto put = [&](int k, float2 E, float2 O, const float4 &w) {
+        const float2 P = cmul(make_float2(w.x, w.y), O);
+        const float2 WV = cmul(make_float2(w.z, w.w), make_float2(E.x + P.x, E.y + P.y));
+        if constexpr (FOLD) {
+            // the table's second factor carries s_1 / 2 (E and O are 2E, 2O)
+            line[k] = WV.x;
+            line[N - k] = -WV.y;
+        } else {
+            line[k] = WV.x * s.s1;
+            line[N - k] = -WV.y * s.s1;
+        }
+    };
+    // E, O of index k from Z_k = (ar, ai) and its partner Z_{L-k} = (cr, ci)
+    auto eo = [&](float ar, float ai, float cr, float ci, float2 &E, float2 &O) {
+        if constexpr (FOLD) {
+            E = make_float2(ar + cr, ai - ci);
+            O = make_float2(ai + ci, cr - ar);
+        } else {
+            E = make_float2(0.5f * (ar + cr), 0.5f * (ai - ci));
+            O = make_float2(0.5f * (ai + ci), 0.5f * (cr - ar));
+        }
+    };
 #pragma unroll
     for (int j = 0; j < C::JC; ++j) {
 #pragma unroll
-        for (int k2 = 0; k2 < C::L2; ++k2) {
+        for (int k2 = 0; k2 < C::L2 / 2; ++k2) {
             // partner Z_{L-k}: thread T - t, slot (JC - 1 - j, L2 - 1 - k2); for
             // t = 0 the partner is this thread's own (JC - j) % JC or, for j = 0,
             // slot (0, (L2 - k2) % L2)
@@ -260,33 +287,21 @@ __device__ __forceinline__ void line_forward(float *line, float *scr, const floa
             if (k == 0) {
                 line[0] = (ar + ai) * s.s0;
                 line[C::L] = (ar - ai) * 0.70710678118654752f * s.s1;
+                // k = L/2: thread 0, slot (0, L2/2), partnered with itself
+                const float hr = zr[j0][C::L2 / 2], hi = zi[j0][C::L2 / 2];
+                float2 E, O;
+                eo(hr, hi, hr, hi, E, O);
+                put(C::L / 2, E, O, ts[C::L / 2]);
             } else {
-                const float4 w = ts[k];  // (exp(-2 pi i k / N), exp(-i pi k / (2N)))
-                if constexpr (FOLD) {
-                    // 2E, 2O; the table's second factor carries s_1 / 2
-                    const float2 E = make_float2(ar + cr, ai - ci);
-                    const float2 O = make_float2(ai + ci, cr - ar);
-                    const float2 P = cmul(make_float2(w.x, w.y), O);
-                    const float2 WV = cmul(make_float2(w.z, w.w), make_float2(E.x + P.x, E.y + P.y));
-                    line[k] = WV.x;
-                    line[N - k] = -WV.y;
-                } else {
-                    const float2 E = make_float2(0.5f * (ar + cr), 0.5f * (ai - ci));
-                    const float2 O = make_float2(0.5f * (ai + ci), 0.5f * (cr - ar));
-                    const float2 P = cmul(make_float2(w.x, w.y), O);
-                    const float2 V = make_float2(E.x + P.x, E.y + P.y);
-                    const float2 WV = cmul(make_float2(w.z, w.w), V);
-                    line[k] = WV.x * s.s1;
-                    line[N - k] = -WV.y * s.s1;
-                }
+                float2 E, O;
+                eo(ar, ai, cr, ci, E, O);
+                put(k, E, O, ts[k]);
+                put(C::L - k, make_float2(E.x, -E.y), make_float2(O.x, -O.y), ts[C::L - k]);
             }
         }
     }
     __syncwarp();
 }
-
-// Inverse DCT-III of one line.  On entry `line` holds y in natural order; on
-// exit x (natural order).  Input scales s_k applied on entry.
 template <int N, bool FOLD = false>
 __device__ __forceinline__ void line_inverse(float *line, float *scr, const float2 *ta, const float4 *ts, int t,
                                              AxisScale s)
