@@ -50,6 +50,24 @@ def _dist_env():
     return rank, world, local
 
 
+def job_time_ms(ms_local: float, world: int, device=None) -> float:
+    """The job's time: the maximum over ranks of each rank's timed region
+    (every rank calls it; one process per GPU, any process-group backend)."""
+    if world <= 1:
+        return ms_local
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value_gbs(ms_job: float, steps: int, step_bytes: int, world: int) -> float:
+    """Whole-job throughput: the units of every rank over the job's time (the
+    ranks run independent replicas of the step: weak scaling)."""
+    return world * steps * step_bytes / (ms_job * 1e-3) / 1e9
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons, sampled while the timed region runs."""
 
@@ -339,13 +357,10 @@ def run_ours(args):
     # per-kernel averages: the same K launches of one kernel alone, same pool
     kt = {name: replay_ms(graphs[name], stream) / args.steps for name in ("forward", "inverse")}
     clocks = sampler.stop()
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = job_time_ms(ms_total, world, dev)
     elems = IMG * IMG
     step_bytes = elems * BYTES_PER_ELEM_STEP
-    value = world * args.steps * step_bytes / (ms_total * 1e-3) / 1e9
+    value = job_value_gbs(ms_total, args.steps, step_bytes, world)
     kern = {1: "k_fused", 3: "k_tc_split"}.get(info.variant, "dense")
 
     # ---- dominant kernel roofline (8 B/element/launch)

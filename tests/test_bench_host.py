@@ -44,3 +44,54 @@ def test_source_key_tracks_code_not_comments(tmp_path, monkeypatch):
     header.write_text(header.read_text().replace("\nstatic const int kProbe = 1;\n", "\nstatic const int kProbe = 2;\n"))
     assert bench.source_key("k_tc_split<16,tiled>") == tc
 
+
+
+def _rank_main(rank, world, port, ms_local, out_q):
+    import os
+    import sys
+    os.environ.update({"RANK": str(rank), "WORLD_SIZE": str(world), "LOCAL_RANK": str(rank),
+                       "MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port)})
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import torch.distributed as dist
+    import bench as b
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        r, w, local = b._dist_env()
+        dist.barrier()
+        ms = b.job_time_ms(ms_local, w)
+        out_q.put((r, w, local, ms, b.job_value_gbs(ms, 100, 1 << 26, w)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_ranks_max_time_and_whole_job_value():
+    """world_size 2 over gloo on CPU: every rank takes the slower rank's time,
+    and the value counts both ranks' steps over that time."""
+    import multiprocessing as mp
+    import socket
+    with socket.socket() as sck:
+        sck.bind(("127.0.0.1", 0))
+        port = sck.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    times = {0: 12.5, 1: 20.0}
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, times[r], q)) for r in (0, 1)]
+    for p in procs:
+        p.start()
+    got = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for r, (rank, world, local, ms, value) in enumerate(got):
+        assert (rank, world, local) == (r, 2, r)
+        assert ms == 20.0
+        assert abs(value - 2 * 100 * (1 << 26) / 20e-3 / 1e9) < 1e-6
+
+
+def test_reference_arm_other_ranks_exit_without_work(monkeypatch):
+    """Under torchrun the reference arm runs on rank 0 only; the other ranks
+    return 0 at once (no oracle, no output)."""
+    import argparse
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    assert bench.run_reference(argparse.Namespace(steps=1, warmup=1)) == 0
