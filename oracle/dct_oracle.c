@@ -113,76 +113,153 @@ void oracle_matrix(int n, int dir, int norm, double *M)
     free(G);
 }
 
-/* One array: out = Mh * X * Mw^T, X is h x w (float), out is h x w (double).
- * First T = X Mw^T (every row transformed), then out = Mh T (every column). */
-static void sandwich_one(int h, int w, const double *Mh, const double *Mw,
-                         const float *X, double *out, double *T)
+/* The two passes of Eq. 2 for one array, out = Mh X Mw^T, split into row
+ * ranges so that one array can be shared by several threads.  Every output
+ * element is one plain double sum in index order (j in pass 1, i in pass 2),
+ * whatever the split; the intermediate T is kept transposed (Tt[l][i]) only so
+ * that pass 2 reads it contiguously.
+ *
+ * Pass 1, rows i0 .. i1-1:  T[i][l] = sum_j X[i][j] Mw[l][j]  (stored Tt[l][i]).
+ * The input is float (xf) or double (xd, the round trip's second half).      */
+static void pass_rows(int h, int w, const double *Mw, const float *xf, const double *xd,
+                      double *Tt, int i0, int i1)
 {
     int last_w = (g_fault == 2) ? w - 1 : w;
-    int last_h = (g_fault == 2) ? h - 1 : h;
-    for (int i = 0; i < h; ++i)
-        for (int l = 0; l < w; ++l) {
-            double acc = 0.0;
-            for (int j = 0; j < last_w; ++j)
-                acc += (double)X[(size_t)i * w + j] * Mw[(size_t)l * w + j];
-            T[(size_t)i * w + l] = acc;
+    for (int i = i0; i < i1; ++i) {
+        const float *rf = xf ? xf + (size_t)i * w : NULL;
+        const double *rd = xd ? xd + (size_t)i * w : NULL;
+        int l = 0;
+        /* four outputs at a time: four independent sums, each in j order */
+        for (; l + 4 <= w; l += 4) {
+            const double *m0 = Mw + (size_t)l * w, *m1 = m0 + w, *m2 = m1 + w, *m3 = m2 + w;
+            double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+            for (int j = 0; j < last_w; ++j) {
+                double x = rf ? (double)rf[j] : rd[j];
+                a0 += x * m0[j];
+                a1 += x * m1[j];
+                a2 += x * m2[j];
+                a3 += x * m3[j];
+            }
+            Tt[(size_t)l * h + i] = a0;
+            Tt[(size_t)(l + 1) * h + i] = a1;
+            Tt[(size_t)(l + 2) * h + i] = a2;
+            Tt[(size_t)(l + 3) * h + i] = a3;
         }
-    for (int k = 0; k < h; ++k)
-        for (int l = 0; l < w; ++l) {
-            double acc = 0.0;
-            for (int i = 0; i < last_h; ++i)
-                acc += Mh[(size_t)k * h + i] * T[(size_t)i * w + l];
-            out[(size_t)k * w + l] = acc;
+        for (; l < w; ++l) {
+            const double *m0 = Mw + (size_t)l * w;
+            double a0 = 0.0;
+            for (int j = 0; j < last_w; ++j) a0 += (rf ? (double)rf[j] : rd[j]) * m0[j];
+            Tt[(size_t)l * h + i] = a0;
         }
+    }
 }
 
-/* Same as sandwich_one for a double input (used by the round-trip composition). */
-static void sandwich_one_d(int h, int w, const double *Mh, const double *Mw,
-                           const double *X, double *out, double *T)
+/* Pass 2, output rows k0 .. k1-1:  out[k][l] = sum_i Mh[k][i] T[i][l]. */
+static void pass_cols(int h, int w, const double *Mh, const double *Tt, double *out, int k0, int k1)
 {
-    for (int i = 0; i < h; ++i)
-        for (int l = 0; l < w; ++l) {
-            double acc = 0.0;
-            for (int j = 0; j < w; ++j)
-                acc += X[(size_t)i * w + j] * Mw[(size_t)l * w + j];
-            T[(size_t)i * w + l] = acc;
+    int last_h = (g_fault == 2) ? h - 1 : h;
+    for (int k = k0; k < k1; ++k) {
+        const double *mk = Mh + (size_t)k * h;
+        int l = 0;
+        for (; l + 4 <= w; l += 4) {
+            const double *t0 = Tt + (size_t)l * h, *t1 = t0 + h, *t2 = t1 + h, *t3 = t2 + h;
+            double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+            for (int i = 0; i < last_h; ++i) {
+                double m = mk[i];
+                a0 += m * t0[i];
+                a1 += m * t1[i];
+                a2 += m * t2[i];
+                a3 += m * t3[i];
+            }
+            out[(size_t)k * w + l] = a0;
+            out[(size_t)k * w + l + 1] = a1;
+            out[(size_t)k * w + l + 2] = a2;
+            out[(size_t)k * w + l + 3] = a3;
         }
-    for (int k = 0; k < h; ++k)
-        for (int l = 0; l < w; ++l) {
-            double acc = 0.0;
-            for (int i = 0; i < h; ++i)
-                acc += Mh[(size_t)k * h + i] * T[(size_t)i * w + l];
-            out[(size_t)k * w + l] = acc;
+        for (; l < w; ++l) {
+            const double *t0 = Tt + (size_t)l * h;
+            double a0 = 0.0;
+            for (int i = 0; i < last_h; ++i) a0 += mk[i] * t0[i];
+            out[(size_t)k * w + l] = a0;
         }
+    }
 }
 
+/* Work shared by the threads of one call.  Arrays are dealt out whole to
+ * threads when there are at least as many arrays as threads; otherwise the
+ * threads share each array, splitting both passes by rows (a barrier between
+ * the passes). */
 typedef struct {
-    int h, w, dir, norm;
+    int h, w, nthreads;
     const double *Mh, *Mw, *Mh2, *Mw2;
     const float *in;
     double *out;
-    int64_t first, last;
+    int64_t batch;
     int roundtrip;
+    int shared;              /* 1: threads share each array */
+    double *Tt, *F;          /* shared mode: the intermediates of the current array */
+    pthread_barrier_t bar;
+} call_t;
+
+typedef struct {
+    call_t *c;
+    int t;
 } job_t;
+
+static void range_of(int n, int parts, int t, int *a, int *b)
+{
+    int per = n / parts, rem = n % parts;
+    *a = t * per + (t < rem ? t : rem);
+    *b = *a + per + (t < rem ? 1 : 0);
+}
 
 static void *worker(void *arg)
 {
     job_t *jb = (job_t *)arg;
-    size_t hw = (size_t)jb->h * jb->w;
-    double *T = (double *)malloc(sizeof(double) * hw);
-    double *F = jb->roundtrip ? (double *)malloc(sizeof(double) * hw) : NULL;
-    for (int64_t b = jb->first; b < jb->last; ++b) {
-        const float *x = jb->in + (size_t)b * hw;
-        double *y = jb->out + (size_t)b * hw;
-        if (!jb->roundtrip) {
-            sandwich_one(jb->h, jb->w, jb->Mh, jb->Mw, x, y, T);
-        } else {
-            sandwich_one(jb->h, jb->w, jb->Mh, jb->Mw, x, F, T);
-            sandwich_one_d(jb->h, jb->w, jb->Mh2, jb->Mw2, F, y, T);
+    call_t *c = jb->c;
+    const int h = c->h, w = c->w;
+    const size_t hw = (size_t)h * w;
+    if (!c->shared) {
+        double *Tt = (double *)malloc(sizeof(double) * hw);
+        double *F = c->roundtrip ? (double *)malloc(sizeof(double) * hw) : NULL;
+        int64_t per = c->batch / c->nthreads, rem = c->batch % c->nthreads;
+        int64_t first = jb->t * per + (jb->t < rem ? jb->t : rem);
+        int64_t last = first + per + (jb->t < rem ? 1 : 0);
+        for (int64_t b = first; b < last; ++b) {
+            const float *x = c->in + (size_t)b * hw;
+            double *y = c->out + (size_t)b * hw;
+            if (!c->roundtrip) {
+                pass_rows(h, w, c->Mw, x, NULL, Tt, 0, h);
+                pass_cols(h, w, c->Mh, Tt, y, 0, h);
+            } else {
+                pass_rows(h, w, c->Mw, x, NULL, Tt, 0, h);
+                pass_cols(h, w, c->Mh, Tt, F, 0, h);
+                pass_rows(h, w, c->Mw2, NULL, F, Tt, 0, h);
+                pass_cols(h, w, c->Mh2, Tt, y, 0, h);
+            }
         }
+        free(Tt);
+        free(F);
+        return NULL;
     }
-    free(T);
-    free(F);
+    int r0, r1;
+    range_of(h, c->nthreads, jb->t, &r0, &r1);
+    for (int64_t b = 0; b < c->batch; ++b) {
+        const float *x = c->in + (size_t)b * hw;
+        double *y = c->out + (size_t)b * hw;
+        pass_rows(h, w, c->Mw, x, NULL, c->Tt, r0, r1);
+        pthread_barrier_wait(&c->bar);
+        if (!c->roundtrip) {
+            pass_cols(h, w, c->Mh, c->Tt, y, r0, r1);
+        } else {
+            pass_cols(h, w, c->Mh, c->Tt, c->F, r0, r1);
+            pthread_barrier_wait(&c->bar);
+            pass_rows(h, w, c->Mw2, NULL, c->F, c->Tt, r0, r1);
+            pthread_barrier_wait(&c->bar);
+            pass_cols(h, w, c->Mh2, c->Tt, y, r0, r1);
+        }
+        pthread_barrier_wait(&c->bar); /* Tt is reused by the next array */
+    }
     return NULL;
 }
 
@@ -203,8 +280,18 @@ static int run_jobs(int h, int w, int dir, int norm, const float *in, double *ou
     if (h < 1 || w < 1 || batch < 0) return -1;
     if (batch == 0) return 0;
     if (threads <= 0) threads = oracle_default_threads();
-    if (threads > batch) threads = (int)batch;
     if (threads > 512) threads = 512;
+    int shared = 0;
+    if (threads > batch) {
+        /* fewer arrays than threads: share each array when it is big enough
+         * to be worth it, else use one thread per array */
+        if ((int64_t)h * w >= 65536 && h >= 2) {
+            shared = 1;
+            if (threads > h) threads = h;
+        } else {
+            threads = (int)batch;
+        }
+    }
 
     double *Mh = (double *)malloc(sizeof(double) * (size_t)h * h);
     double *Mw = (double *)malloc(sizeof(double) * (size_t)w * w);
@@ -230,17 +317,27 @@ static int run_jobs(int h, int w, int dir, int norm, const float *in, double *ou
         }
     }
 
+    call_t c;
+    memset(&c, 0, sizeof(c));
+    c.h = h; c.w = w; c.nthreads = threads;
+    c.Mh = Mh; c.Mw = Mw; c.Mh2 = Mh2; c.Mw2 = Mw2;
+    c.in = in; c.out = out; c.batch = batch; c.roundtrip = roundtrip; c.shared = shared;
+    if (shared) {
+        c.Tt = (double *)malloc(sizeof(double) * (size_t)h * w);
+        c.F = roundtrip ? (double *)malloc(sizeof(double) * (size_t)h * w) : NULL;
+        pthread_barrier_init(&c.bar, NULL, (unsigned)threads);
+    }
     pthread_t *tid = (pthread_t *)malloc(sizeof(pthread_t) * threads);
     job_t *jobs = (job_t *)malloc(sizeof(job_t) * threads);
-    int64_t per = batch / threads, rem = batch % threads, start = 0;
-    for (int t = 0; t < threads; ++t) {
-        int64_t cnt = per + (t < rem ? 1 : 0);
-        jobs[t] = (job_t){h, w, dir, norm, Mh, Mw, Mh2, Mw2, in, out, start, start + cnt, roundtrip};
-        start += cnt;
-    }
+    for (int t = 0; t < threads; ++t) { jobs[t].c = &c; jobs[t].t = t; }
     for (int t = 1; t < threads; ++t) pthread_create(&tid[t], NULL, worker, &jobs[t]);
     worker(&jobs[0]);
     for (int t = 1; t < threads; ++t) pthread_join(tid[t], NULL);
+    if (shared) {
+        pthread_barrier_destroy(&c.bar);
+        free(c.Tt);
+        free(c.F);
+    }
     free(tid);
     free(jobs);
     free(Mh);
