@@ -98,8 +98,9 @@ int bdct_plan_destroy(bdct_plan *plan);
 
 /* Transform `batch` contiguous rows x cols float32 arrays from `in` to `out`
  * (device pointers, 16-byte aligned).  batch == 0 is a no-op.  in == out
- * (exact in-place) is allowed on fused on-chip variants; any other overlap is
- * BDCT_ERR_ALIAS.  The input is left unchanged when in != out.             */
+ * (exact in-place) is allowed on every variant (the separable routes go
+ * through the plan's workspace); any other overlap is BDCT_ERR_ALIAS.  The
+ * input is left unchanged when in != out.                                  */
 int bdct_forward(const bdct_plan *plan, const float *in, float *out, size_t batch, void *stream);
 int bdct_inverse(const bdct_plan *plan, const float *in, float *out, size_t batch, void *stream);
 int bdct_roundtrip(const bdct_plan *plan, const float *in, float *out, size_t batch, void *stream);
@@ -108,13 +109,17 @@ int bdct_roundtrip(const bdct_plan *plan, const float *in, float *out, size_t ba
 int bdct_execute(const bdct_plan *plan, unsigned kind, const float *in, float *out,
                  size_t batch, void *stream);
 
-/* Tiled image view: `in` is an img_rows x img_cols row-major image with
+/* Tiled image view (Section 1.1: the motivating phase-unwrapping workload
+ * transforms an image as many independent small blocks; Eq. 2 per block):
+ * `in` is an img_rows x img_cols row-major image with
  * leading dimension ld_in floats; it is cut into (img_rows/rows) x
  * (img_cols/cols) independent rows x cols blocks, block (bi, bj) covering
  * rows bi*rows.. and columns bj*cols..; each block is transformed in place of
  * the same block of `out` (leading dimension ld_out).  img_rows and img_cols
  * must be multiples of the plan's rows and cols; ld_in and ld_out multiples
- * of 4.  Only fused on-chip variants support it (else BDCT_ERR_PATH).      */
+ * of 4.  in == out with ld_in == ld_out is exact in place; any other overlap
+ * is BDCT_ERR_ALIAS.  Only fused on-chip and tensor-core variants support it
+ * (else BDCT_ERR_PATH).                                                     */
 int bdct_execute_tiled(const bdct_plan *plan, unsigned kind, const float *in, float *out,
                        int img_rows, int img_cols, size_t ld_in, size_t ld_out, void *stream);
 

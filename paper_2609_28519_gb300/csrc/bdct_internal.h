@@ -8,9 +8,44 @@
 #include <stdint.h>
 #include <stdlib.h>
 
+#include <atomic>
+#include <mutex>
+
 #include "bdct.h"
 
 namespace bdct {
+
+// Per-device launch set-up of one kernel (its attributes, resident CTAs per
+// SM and the SM count), computed once per device under a lock, so that host
+// threads creating their first plans at the same time do not race on it;
+// later launches read it without locking.
+struct DeviceLaunchCache {
+    std::mutex mu;
+    std::atomic<bool> ready[64];
+    int blocks[64];
+    int sms[64];
+    // init(dev, blocks, sms) runs at most once per device (again only if it
+    // failed); its error is returned.
+    template <class Init>
+    cudaError_t get(int dev, Init &&init, int *blocks_out, int *sms_out)
+    {
+        if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+        if (!ready[dev].load(std::memory_order_acquire)) {
+            std::lock_guard<std::mutex> lock(mu);
+            if (!ready[dev].load(std::memory_order_relaxed)) {
+                int b = 0, n = 0;
+                cudaError_t e = init(dev, b, n);
+                if (e != cudaSuccess) return e;
+                blocks[dev] = b;
+                sms[dev] = n;
+                ready[dev].store(true, std::memory_order_release);
+            }
+        }
+        *blocks_out = blocks[dev];
+        *sms_out = sms[dev];
+        return cudaSuccess;
+    }
+};
 
 // A per-axis diagonal scale that takes one value at index 0 and another at
 // every index > 0 -- every scale of Eq. 1 and of the REDFT pair has this form.

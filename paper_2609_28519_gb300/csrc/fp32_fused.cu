@@ -461,11 +461,13 @@ __global__ void k_gen_cos_table3(float *t)
     t[r] = (r == 768) ? 0.0f : (float)cospi((double)r / 1536.0);
 }
 
+static std::mutex g_table_mutex;
 static bool g_table_ready[64];
 
 cudaError_t fused_init_device(int device)
 {
     if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_table_mutex);
     if (g_table_ready[device]) return cudaSuccess;
     float *tmp = nullptr;
     cudaError_t e = cudaMalloc(&tmp, 4097 * sizeof(float));
@@ -498,24 +500,24 @@ static cudaError_t launch_one(const DirScales &sc, const ExecGeom &g, unsigned i
 {
     using C = FusedCfg<H, W, TILED>;
     auto kern = k_fused<H, W, DIR, TILED>;
-    static int blocks_per_sm[64];
-    static int num_sms[64];
-    int dev = 0;
+    static DeviceLaunchCache cache;
+    int dev = 0, blocks_per_sm = 0, num_sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (blocks_per_sm[dev] == 0) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-        if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[dev], kern, C::THREADS, C::SMEM);
-        if (e != cudaSuccess) return e;
-        e = cudaDeviceGetAttribute(&num_sms[dev], cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
-        if (blocks_per_sm[dev] < 1) return cudaErrorInvalidConfiguration;
-        if (debug_enabled())
-            fprintf(stderr, "[bdct] k_fused<%d,%d,%d,%d>: %d CTAs/SM x %d threads, %d stages, smem %zu B\n", H, W, DIR,
-                    (int)TILED, blocks_per_sm[dev], C::THREADS, C::STAGES, C::SMEM);
-    }
+    e = cache.get(
+        dev,
+        [&](int d, int &bps, int &sms) {
+            cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+            if (r == cudaSuccess) r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, C::THREADS, C::SMEM);
+            if (r == cudaSuccess) r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
+            if (r == cudaSuccess && bps < 1) r = cudaErrorInvalidConfiguration;
+            if (r == cudaSuccess && debug_enabled())
+                fprintf(stderr, "[bdct] k_fused<%d,%d,%d,%d>: %d CTAs/SM x %d threads, %d stages, smem %zu B\n", H, W,
+                        DIR, (int)TILED, bps, C::THREADS, C::STAGES, C::SMEM);
+            return r;
+        },
+        &blocks_per_sm, &num_sms);
+    if (e != cudaSuccess) return e;
     FusedParams p{};
     p.in = g.in;
     p.out = g.out;
@@ -538,7 +540,7 @@ static cudaError_t launch_one(const DirScales &sc, const ExecGeom &g, unsigned i
     if (nch > 0x7ff00000LL) return cudaErrorInvalidValue;  // keeps c + STAGES * grid within int
     p.nchunks = (int)nch;
     // persistent: as many CTAs as fit on the device
-    long long grid = (long long)blocks_per_sm[dev] * num_sms[dev];
+    long long grid = (long long)blocks_per_sm * num_sms;
     if (grid > p.nchunks) grid = p.nchunks;
     // programmatic dependent launch: this grid may be scheduled while the
     // previous kernel in the stream drains; it waits for it before any access

@@ -569,30 +569,31 @@ static cudaError_t lines_launch(const LinesParams &p0, cudaStream_t stream)
 {
     using C = LineCfg<N>;
     auto kern = k_lines<N, DIR>;
-    static int blocks_per_sm[64], num_sms[64];
-    int dev = 0;
+    static DeviceLaunchCache cache;
+    int dev = 0, blocks_per_sm = 0, num_sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (blocks_per_sm[dev] == 0) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-        if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[dev], kern, C::THREADS, C::SMEM);
-        if (e != cudaSuccess) return e;
-        e = cudaDeviceGetAttribute(&num_sms[dev], cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
-        if (blocks_per_sm[dev] < 1) return cudaErrorInvalidConfiguration;
-        if (debug_enabled())
-            fprintf(stderr, "[bdct] k_lines<%d,%d>: %d CTAs/SM x %d threads, panel %d rows, smem %zu B\n", N, DIR,
-                    blocks_per_sm[dev], C::THREADS, C::PR, C::SMEM);
-    }
+    e = cache.get(
+        dev,
+        [&](int d, int &bps, int &sms) {
+            cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+            if (r == cudaSuccess) r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, C::THREADS, C::SMEM);
+            if (r == cudaSuccess) r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
+            if (r == cudaSuccess && bps < 1) r = cudaErrorInvalidConfiguration;
+            if (r == cudaSuccess && debug_enabled())
+                fprintf(stderr, "[bdct] k_lines<%d,%d>: %d CTAs/SM x %d threads, panel %d rows, smem %zu B\n", N, DIR,
+                        bps, C::THREADS, C::PR, C::SMEM);
+            return r;
+        },
+        &blocks_per_sm, &num_sms);
+    if (e != cudaSuccess) return e;
     LinesParams p = p0;
     if (p.rows % C::PR != 0) return cudaErrorInvalidValue;  // panels never straddle two arrays
     const long long np = p.nrows / C::PR;
     if (np <= 0) return cudaSuccess;
     if (np > 0x7ff00000LL) return cudaErrorInvalidValue;
     p.npanels = (int)np;
-    long long grid = (long long)blocks_per_sm[dev] * num_sms[dev];
+    long long grid = (long long)blocks_per_sm * num_sms;
     if (grid > np) grid = np;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);

@@ -696,26 +696,25 @@ static cudaError_t ring_launch_one(const DirScales &sc, const ExecGeom &g, unsig
 {
     using C = RingCfg<H, W, DIR>;
     auto kern = k_ring<H, W, DIR>;
-    static int num_sms[64];
-    static bool ready[64];
-    int dev = 0;
+    static DeviceLaunchCache cache;
+    int dev = 0, bps_dev = 0, num_sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (!ready[dev]) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-        if (e != cudaSuccess) return e;
-        int bps = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, C::THREADS, C::SMEM);
-        if (e != cudaSuccess) return e;
-        if (bps < 1) return cudaErrorInvalidConfiguration;
-        e = cudaDeviceGetAttribute(&num_sms[dev], cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
-        if (debug_enabled())
-            fprintf(stderr, "[bdct] k_ring<%d,%d,%d>: %d slots of %d B, %d groups x %d warps + producer, smem %zu B\n",
-                    H, W, DIR, C::S, C::SLOT_BYTES, C::NG, C::GW, C::SMEM);
-        ready[dev] = true;
-    }
+    e = cache.get(
+        dev,
+        [&](int d, int &bps, int &sms) {
+            cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+            if (r == cudaSuccess) r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, C::THREADS, C::SMEM);
+            if (r == cudaSuccess && bps < 1) r = cudaErrorInvalidConfiguration;
+            if (r == cudaSuccess) r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
+            if (r == cudaSuccess && debug_enabled())
+                fprintf(stderr, "[bdct] k_ring<%d,%d,%d>: %d slots of %d B, %d groups x %d warps + producer, smem %zu B\n",
+                        H, W, DIR, C::S, C::SLOT_BYTES, C::NG, C::GW, C::SMEM);
+            return r;
+        },
+        &bps_dev, &num_sms);
+    if (e != cudaSuccess) return e;
+    (void)bps_dev;
     if (g.count <= 0) return cudaSuccess;
     RingParams p{};
     p.in = g.in;
@@ -744,7 +743,7 @@ static cudaError_t ring_launch_one(const DirScales &sc, const ExecGeom &g, unsig
         if (e == cudaSuccess) e = tma_map_2d(&p.map_out, g.out, rows, W, W, H);
         if (e != cudaSuccess) return e;
     }
-    long long grid = num_sms[dev];
+    long long grid = num_sms;
     if (grid > g.count) grid = g.count;
     if ((g.count + grid - 1) / grid > 0x7fffff00LL) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};

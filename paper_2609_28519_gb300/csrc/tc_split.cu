@@ -257,6 +257,8 @@ __global__ void __launch_bounds__(128) k_tc_split(const TcParams p)
     }
     bool ok = mbar_wait_bounded(&bar[1], 0);
     ok = __syncthreads_and(ok);
+    const bool ops_landed = ok;
+    bool mma_outstanding = false;  // a committed MMA group whose completion was not seen
     uint32_t mma_phase = 0;
 
     const int b_local = tid / N, r_local = tid % N;  // this thread's stack row: array, row
@@ -276,7 +278,9 @@ __global__ void __launch_bounds__(128) k_tc_split(const TcParams p)
             else src = p.in + (brow * N + r_local) * p.ld_in + (long long)(t0 + b_local) * N;
 #pragma unroll
             for (int q = 0; q < N / 4; ++q) {
-                const float4 t = __ldg(reinterpret_cast<const float4 *>(src) + q);
+                // L2-coherent load: with in == out this kernel writes the
+                // same buffer (each tile only after its own rows were read)
+                const float4 t = __ldcg(reinterpret_cast<const float4 *>(src) + q);
                 dstv[4 * q] = t.x; dstv[4 * q + 1] = t.y; dstv[4 * q + 2] = t.z; dstv[4 * q + 3] = t.w;
             }
         } else {
@@ -319,9 +323,12 @@ __global__ void __launch_bounds__(128) k_tc_split(const TcParams p)
                 tc_commit(&bar[0]);
             }
             ok = mbar_wait_bounded(&bar[0], mma_phase);
-            mma_phase ^= 1u;
             ok = __syncthreads_and(ok);
-            if (!ok) break;
+            if (!ok) {
+                mma_outstanding = true;
+                break;
+            }
+            mma_phase ^= 1u;
             tc_fence_after();
             // ---- this thread's TMEM lane of the result
             const uint32_t taddr = d_tmem[pass & 1] + ((uint32_t)(32 * warp) << 16);
@@ -358,7 +365,14 @@ __global__ void __launch_bounds__(128) k_tc_split(const TcParams p)
         __syncthreads();
         tc_fence_after();
     }
-    if (!ok && tid == 0) record_timeout(p.status);
+    if (!ok && tid == 0) {
+        record_timeout(p.status);
+        // error path: let the asynchronous operations this CTA started finish
+        // (each wait bounded) before its shared memory and TMEM are released,
+        // so that nothing lands after the CTA has exited
+        if (!ops_landed) mbar_wait_bounded(&bar[1], 0);
+        if (mma_outstanding) mbar_wait_bounded(&bar[0], mma_phase);
+    }
     tc_fence_before();
     __syncthreads();
     if (warp == 0)
@@ -421,42 +435,46 @@ static cudaError_t tc_launch_one(const TcParams &p0, const __nv_bfloat16 *ops, c
     constexpr int NOPS = NPASS / 2;
     auto kern = k_tc_split<N, NPASS, TERMS, TILED>;
     const size_t smem = (size_t)TERMS * C::A_TERM_BYTES + (size_t)NOPS * 3 * C::B_TERM_BYTES + 64;
-    static int blocks_per_sm[64], num_sms[64];
-    int dev = 0;
+    static DeviceLaunchCache cache;
+    int dev = 0, blocks_per_sm = 0, num_sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (blocks_per_sm[dev] == 0) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        // Resident CTAs per SM from threads, registers and shared memory, capped so
-        // that their TMEM allocations fit in the 512 columns (a CTA beyond that
-        // would wait in tcgen05.alloc until another one exits).  Computed here
-        // because the runtime's occupancy query reports one CTA for kernels that
-        // allocate tensor memory.
-        cudaFuncAttributes fa;
-        e = cudaFuncGetAttributes(&fa, kern);
-        if (e != cudaSuccess) return e;
-        int smem_per_sm = 0, regs_per_sm = 0, reserved = 0;
-        cudaDeviceGetAttribute(&smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-        cudaDeviceGetAttribute(&regs_per_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
-        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
-        const int by_threads = 2048 / 128;
-        const int regs_cta = ((fa.numRegs * 32 + 255) / 256) * 256 * 4;  // per-warp allocation granularity
-        const int by_regs = regs_cta > 0 ? regs_per_sm / regs_cta : by_threads;
-        const int by_smem = (int)((size_t)smem_per_sm / (smem + fa.sharedSizeBytes + (size_t)reserved));
-        const int tmem_cap = 512 / C::TMEM_COLS;
-        int occ = by_threads;
-        if (by_regs < occ) occ = by_regs;
-        if (by_smem < occ) occ = by_smem;
-        blocks_per_sm[dev] = occ < tmem_cap ? occ : tmem_cap;
-        e = cudaDeviceGetAttribute(&num_sms[dev], cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
-        if (blocks_per_sm[dev] < 1) return cudaErrorInvalidConfiguration;
-        if (debug_enabled())
-            fprintf(stderr, "[bdct] k_tc_split<%d,%d,%d,%d>: %d CTAs/SM (regs %d, smem %zu B, TMEM cap %d)\n", N,
-                    NPASS, TERMS, (int)TILED, blocks_per_sm[dev], fa.numRegs, smem, tmem_cap);
-    }
+    e = cache.get(
+        dev,
+        [&](int d, int &bps, int &sms) {
+            cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (r != cudaSuccess) return r;
+            // Resident CTAs per SM from threads, registers and shared memory, capped so
+            // that their TMEM allocations fit in the 512 columns (a CTA beyond that
+            // would wait in tcgen05.alloc until another one exits).  Computed here
+            // because the runtime's occupancy query reports one CTA for kernels that
+            // allocate tensor memory.
+            cudaFuncAttributes fa;
+            r = cudaFuncGetAttributes(&fa, kern);
+            if (r != cudaSuccess) return r;
+            int smem_per_sm = 0, regs_per_sm = 0, reserved = 0;
+            cudaDeviceGetAttribute(&smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, d);
+            cudaDeviceGetAttribute(&regs_per_sm, cudaDevAttrMaxRegistersPerMultiprocessor, d);
+            cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, d);
+            const int by_threads = 2048 / 128;
+            const int regs_cta = ((fa.numRegs * 32 + 255) / 256) * 256 * 4;  // per-warp allocation granularity
+            const int by_regs = regs_cta > 0 ? regs_per_sm / regs_cta : by_threads;
+            const int by_smem = (int)((size_t)smem_per_sm / (smem + fa.sharedSizeBytes + (size_t)reserved));
+            const int tmem_cap = 512 / C::TMEM_COLS;
+            int occ = by_threads;
+            if (by_regs < occ) occ = by_regs;
+            if (by_smem < occ) occ = by_smem;
+            bps = occ < tmem_cap ? occ : tmem_cap;
+            r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
+            if (r != cudaSuccess) return r;
+            if (bps < 1) return cudaErrorInvalidConfiguration;
+            if (debug_enabled())
+                fprintf(stderr, "[bdct] k_tc_split<%d,%d,%d,%d>: %d CTAs/SM (regs %d, smem %zu B, TMEM cap %d)\n", N,
+                        NPASS, TERMS, (int)TILED, bps, fa.numRegs, smem, tmem_cap);
+            return cudaSuccess;
+        },
+        &blocks_per_sm, &num_sms);
+    if (e != cudaSuccess) return e;
     TcParams p = p0;
     p.ops = ops;
     long long nt;
@@ -469,7 +487,7 @@ static cudaError_t tc_launch_one(const TcParams &p0, const __nv_bfloat16 *ops, c
     if (nt <= 0) return cudaSuccess;
     if (nt > 0x7ff00000LL) return cudaErrorInvalidValue;
     p.ntiles = (int)nt;
-    long long grid = (long long)blocks_per_sm[dev] * num_sms[dev];
+    long long grid = (long long)blocks_per_sm * num_sms;
     if (grid > nt) grid = nt;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
