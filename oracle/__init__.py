@@ -14,6 +14,7 @@ from .oracle import (  # noqa: F401
     forward,
     inverse,
     roundtrip,
+    spectral,
     bruteforce,
     matrix,
     cospi_frac,

@@ -12,6 +12,8 @@
  *           C^{-1}(Y) = Q_h^T Y Q_w   (inverse, DCT-III, the adjoint).
  *   Section 7.1 gives the rectangular operator Q_h X Q_w^T for X in R^{h x w}.
  *   The round trip C^{-1}(C(X)) has exact result X (Section 2.1).
+ *   Prop. 1 (Eq. 4): the transform -- diagonal spectral operator -- inverse
+ *   composition U^T Lambda U, i.e. Q_h^T (Lambda o (Q_h X Q_w^T)) Q_w.
  *
  * The unnormalized convention (Section 2.1 names FFTW's REDFT10/REDFT01 pair,
  * pair factor 2n per axis) is read as
@@ -49,7 +51,8 @@ static int g_fault = 0;
  *   2  last term of every 1D sum dropped                (dropped term)
  *   3  cos argument uses (2j-1) instead of (2j+1)        (wrong index)
  *   4  inverse uses M instead of M^T                     (transposed operand)
- *   5  row axis uses the column-axis matrix              (swapped axes)    */
+ *   5  row axis uses the column-axis matrix              (swapped axes)
+ *   6  spectral diagonal read as Lambda[l][k]            (transposed table) */
 void oracle_set_fault(int f) { g_fault = f; }
 int oracle_get_fault(void) { return g_fault; }
 
@@ -185,6 +188,17 @@ static void pass_cols(int h, int w, const double *Mh, const double *Tt, double *
     }
 }
 
+/* The spectral operator of Prop. 1 (Eq. 4): every coefficient Y[k][l] of
+ * rows k0 .. k1-1 multiplied by Lambda[k][l] (row-major h x w). */
+static void apply_lambda(int h, int w, const double *lam, double *F, int k0, int k1)
+{
+    for (int k = k0; k < k1; ++k)
+        for (int l = 0; l < w; ++l) {
+            size_t at = (g_fault == 6) ? (size_t)l * h + k : (size_t)k * w + l;
+            F[(size_t)k * w + l] *= lam[at];
+        }
+}
+
 /* Work shared by the threads of one call.  Arrays are dealt out whole to
  * threads when there are at least as many arrays as threads; otherwise the
  * threads share each array, splitting both passes by rows (a barrier between
@@ -196,6 +210,7 @@ typedef struct {
     double *out;
     int64_t batch;
     int roundtrip;
+    const double *lam;       /* round trip with a spectral diagonal (Eq. 4), or NULL */
     int shared;              /* 1: threads share each array */
     double *Tt, *F;          /* shared mode: the intermediates of the current array */
     pthread_barrier_t bar;
@@ -234,6 +249,7 @@ static void *worker(void *arg)
             } else {
                 pass_rows(h, w, c->Mw, x, NULL, Tt, 0, h);
                 pass_cols(h, w, c->Mh, Tt, F, 0, h);
+                if (c->lam) apply_lambda(h, w, c->lam, F, 0, h);
                 pass_rows(h, w, c->Mw2, NULL, F, Tt, 0, h);
                 pass_cols(h, w, c->Mh2, Tt, y, 0, h);
             }
@@ -253,6 +269,7 @@ static void *worker(void *arg)
             pass_cols(h, w, c->Mh, c->Tt, y, r0, r1);
         } else {
             pass_cols(h, w, c->Mh, c->Tt, c->F, r0, r1);
+            if (c->lam) apply_lambda(h, w, c->lam, c->F, r0, r1);
             pthread_barrier_wait(&c->bar);
             pass_rows(h, w, c->Mw2, NULL, c->F, c->Tt, r0, r1);
             pthread_barrier_wait(&c->bar);
@@ -275,7 +292,7 @@ int oracle_default_threads(void)
 }
 
 static int run_jobs(int h, int w, int dir, int norm, const float *in, double *out,
-                    int64_t batch, int threads, int roundtrip)
+                    int64_t batch, int threads, int roundtrip, const double *lam)
 {
     if (h < 1 || w < 1 || batch < 0) return -1;
     if (batch == 0) return 0;
@@ -322,6 +339,7 @@ static int run_jobs(int h, int w, int dir, int norm, const float *in, double *ou
     c.h = h; c.w = w; c.nthreads = threads;
     c.Mh = Mh; c.Mw = Mw; c.Mh2 = Mh2; c.Mw2 = Mw2;
     c.in = in; c.out = out; c.batch = batch; c.roundtrip = roundtrip; c.shared = shared;
+    c.lam = lam;
     if (shared) {
         c.Tt = (double *)malloc(sizeof(double) * (size_t)h * w);
         c.F = roundtrip ? (double *)malloc(sizeof(double) * (size_t)h * w) : NULL;
@@ -350,19 +368,30 @@ static int run_jobs(int h, int w, int dir, int norm, const float *in, double *ou
 /* Forward 2D DCT-II of `batch` contiguous h x w float arrays into double. */
 int oracle_forward(int h, int w, int norm, const float *in, double *out, int64_t batch, int threads)
 {
-    return run_jobs(h, w, ORACLE_DIR_FORWARD, norm, in, out, batch, threads, 0);
+    return run_jobs(h, w, ORACLE_DIR_FORWARD, norm, in, out, batch, threads, 0, NULL);
 }
 
 /* Inverse 2D DCT-III of `batch` contiguous h x w float arrays into double. */
 int oracle_inverse(int h, int w, int norm, const float *in, double *out, int64_t batch, int threads)
 {
-    return run_jobs(h, w, ORACLE_DIR_INVERSE, norm, in, out, batch, threads, 0);
+    return run_jobs(h, w, ORACLE_DIR_INVERSE, norm, in, out, batch, threads, 0, NULL);
 }
 
 /* FP64 composition C^{-1}(C(X)) (normalized); its exact result is X. */
 int oracle_roundtrip(int h, int w, int norm, const float *in, double *out, int64_t batch, int threads)
 {
-    return run_jobs(h, w, ORACLE_DIR_FORWARD, norm, in, out, batch, threads, 1);
+    return run_jobs(h, w, ORACLE_DIR_FORWARD, norm, in, out, batch, threads, 1, NULL);
+}
+
+/* Transform -- spectral operator -- inverse (Prop. 1, Eq. 4):
+ * out = U^T Lambda U X = Q_h^T (Lambda o (Q_h X Q_w^T)) Q_w for every array,
+ * with the orthonormal Q of Eq. 1 and `lam` the h x w diagonal (row-major,
+ * Lambda[k][l] multiplies coefficient (k, l)).  Lambda = 1 gives the round
+ * trip, whose exact result is X. */
+int oracle_spectral(int h, int w, const double *lam, const float *in, double *out, int64_t batch, int threads)
+{
+    if (!lam) return -1;
+    return run_jobs(h, w, ORACLE_DIR_FORWARD, ORACLE_NORM_ORTHO, in, out, batch, threads, 1, lam);
 }
 
 /* Brute-force O(h^2 w^2) double sum of Eq. 2 for one array, with every cosine

@@ -4,7 +4,8 @@ The arithmetic lives in ``dct_oracle.c``; this module only compiles it with
 gcc, marshals numpy arrays and returns float64 results.  Definitions followed:
 Eq. 1 (orthonormal DCT-II matrix), Eq. 2 (forward ``Q_h X Q_w^T`` and inverse
 ``Q_h^T Y Q_w``), Section 7.1 (rectangles), Section 2.1 (round trip equals X;
-FFTW REDFT10/REDFT01 unnormalized pair, factor 2n per axis).
+FFTW REDFT10/REDFT01 unnormalized pair, factor 2n per axis), Prop. 1 / Eq. 4
+(transform, diagonal spectral operator, inverse).
 """
 from __future__ import annotations
 
@@ -51,6 +52,9 @@ def _load():
                 fn.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, f32p, f64p,
                                ctypes.c_int64, ctypes.c_int]
                 fn.restype = ctypes.c_int
+            lib.oracle_spectral.argtypes = [ctypes.c_int, ctypes.c_int, f64p, f32p, f64p,
+                                            ctypes.c_int64, ctypes.c_int]
+            lib.oracle_spectral.restype = ctypes.c_int
             lib.oracle_bruteforce.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                               ctypes.c_int, f32p, f64p]
             lib.oracle_bruteforce.restype = ctypes.c_int
@@ -100,6 +104,25 @@ def inverse(y: np.ndarray, norm: int = NORM_ORTHO, threads: int = 0) -> np.ndarr
 def roundtrip(x: np.ndarray, norm: int = NORM_ORTHO, threads: int = 0) -> np.ndarray:
     """FP64 composition ``C^{-1}(C(X))`` (normalized); exact result is X."""
     return _run("oracle_roundtrip", x, norm, threads)
+
+
+def spectral(x: np.ndarray, lam: np.ndarray, threads: int = 0) -> np.ndarray:
+    """Prop. 1 / Eq. 4: ``U^T Lambda U X = Q_h^T (Lambda o (Q_h X Q_w^T)) Q_w``
+    of every trailing h x w array, in FP64, with the orthonormal Q of Eq. 1;
+    ``lam`` is the h x w diagonal (``lam[k, l]`` multiplies coefficient k, l)."""
+    lib = _load()
+    x, h, w, batch = _as_batch(x)
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    if lam.shape != (h, w):
+        raise ValueError(f"lambda must be ({h}, {w}), got {lam.shape}")
+    out = np.empty(x.shape, dtype=np.float64)
+    if batch:
+        rc = lib.oracle_spectral(h, w, lam.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                 x.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                 out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), batch, threads)
+        if rc != 0:
+            raise ValueError(f"oracle_spectral rejected h={h} w={w}")
+    return out
 
 
 def bruteforce(x: np.ndarray, direction: str = "forward", norm: int = NORM_ORTHO) -> np.ndarray:

@@ -18,6 +18,10 @@ them; see Section 6 of the paper for the input categories):
   neighbouring floats, weak perturbations of a strong constant, amplitudes
   2^-100 .. 2^90 (Section 6 input categories, regenerated synthetically)
 * ``ragged_shapes``   shapes drawn uniformly from the nine mixed shapes
+* ``random_diagonal`` a seeded h x w spectral diagonal, uniform in [lo, hi]
+* ``poisson_diagonal`` the inverse eigenvalues of the 5-point Laplacian with
+  reflecting (Neumann) borders, the diagonal of a least-squares phase-
+  unwrapping solve (Section 1.1); 0 at (0, 0)
 """
 from __future__ import annotations
 
@@ -130,3 +134,22 @@ def ragged_shapes(seed: int, count: int = 4096, shapes=None):
     rng = np.random.default_rng(seed)
     idx = rng.integers(0, len(shapes), size=count)
     return [shapes[int(i)] for i in idx]
+
+
+def random_diagonal(seed: int, h: int, w: int, lo: float = 0.5, hi: float = 2.0) -> np.ndarray:
+    """A seeded spectral diagonal Lambda (float64, h x w), i.i.d. uniform[lo, hi]."""
+    return np.random.default_rng(seed).uniform(lo, hi, size=(h, w))
+
+
+def poisson_diagonal(h: int, w: int) -> np.ndarray:
+    """1 / (2 cos(pi k / h) + 2 cos(pi l / w) - 4) for (k, l) != (0, 0), and 0 at
+    (0, 0): the inverse eigenvalues of the 5-point Laplacian with reflecting
+    borders on an h x w grid (float64).  An application-side operator (the
+    diagonal of a Poisson solve), not part of the transform."""
+    k = np.arange(h, dtype=np.float64)[:, None]
+    l = np.arange(w, dtype=np.float64)[None, :]
+    ev = 2.0 * np.cos(np.pi * k / h) + 2.0 * np.cos(np.pi * l / w) - 4.0
+    ev[0, 0] = 1.0
+    lam = 1.0 / ev
+    lam[0, 0] = 0.0
+    return lam

@@ -183,6 +183,104 @@ def test_threads_do_not_change_results(oracle_mod):
     assert o.default_threads() >= 1
 
 
+# ---------------------------------------------------------------- spectral operator (Prop. 1, Eq. 4)
+def _neumann_laplacian(phi: np.ndarray) -> np.ndarray:
+    """5-point Laplacian with reflecting borders (ghost cells equal to the
+    border cells), plain stencil arithmetic on each trailing h x w array."""
+    p = np.asarray(phi, dtype=np.float64)
+    up = np.concatenate([p[..., :1, :], p[..., :-1, :]], axis=-2)
+    down = np.concatenate([p[..., 1:, :], p[..., -1:, :]], axis=-2)
+    left = np.concatenate([p[..., :, :1], p[..., :, :-1]], axis=-1)
+    right = np.concatenate([p[..., :, 1:], p[..., :, -1:]], axis=-1)
+    return up + down + left + right - 4.0 * p
+
+
+@pytest.mark.parametrize("h,w,b", [(8, 8, 3), (16, 16, 2), (8, 32, 2), (5, 7, 2), (256, 256, 1)])
+def test_spectral_identity_is_round_trip(oracle_mod, h, w, b):
+    o = oracle_mod
+    x = inputs.uniform(400 + h + w, b, h, w)
+    assert _rel(o.spectral(x, np.ones((h, w))), x.astype(np.float64)) < 1e-13
+
+
+@pytest.mark.parametrize("h,w", [(8, 8), (16, 16), (8, 16), (5, 7), (32, 24)])
+def test_spectral_cosine_modes_are_eigenvectors(oracle_mod, h, w):
+    """A separable cosine mode c_k0(i) c_l0(j) is an eigenvector of
+    U^T Lambda U with eigenvalue Lambda[k0, l0] (an asymmetric Lambda, so a
+    transposed table is caught)."""
+    o = oracle_mod
+    lam = inputs.random_diagonal(7 + h * w, h, w)
+    rng = np.random.default_rng(h + 3 * w)
+    modes = [(0, 0), (0, w - 1), (h - 1, 0), (1, 2 % w)] + [
+        (int(rng.integers(h)), int(rng.integers(w))) for _ in range(4)]
+    i = np.arange(h)[:, None]
+    j = np.arange(w)[None, :]
+    for (k0, l0) in modes:
+        x = (np.cos(np.pi * (2 * i + 1) * k0 / (2 * h)) * np.cos(np.pi * (2 * j + 1) * l0 / (2 * w)))
+        x = x.astype(np.float32)[None]
+        got = o.spectral(x, lam)
+        # x is the float32 rounding of the mode (relative error <= 2^-24 per
+        # element), whose residual is scaled by at most max|Lambda| + Lambda[k0, l0]
+        assert _rel(got, lam[k0, l0] * x.astype(np.float64)) < 4 * 2.0 ** -24 * 2.0 / lam[k0, l0], (k0, l0)
+
+
+@pytest.mark.parametrize("h,w", [(16, 16), (32, 24), (8, 64), (256, 256)])
+def test_spectral_poisson_inverts_neumann_laplacian(oracle_mod, h, w):
+    """Textbook special case: the DCT-II diagonalizes the 5-point Laplacian
+    with reflecting borders, so U^T Lambda_P U applied to L(phi) returns phi
+    minus its mean (the (0, 0) mode is the Laplacian's null space)."""
+    o = oracle_mod
+    phi = inputs.gaussian(600 + h + w, 2, h, w).astype(np.float64)
+    f = _neumann_laplacian(phi)
+    got = o.spectral(f.astype(np.float32), inputs.poisson_diagonal(h, w))
+    # f is rounded to float32 for the call, so compare against the exact
+    # solve of the rounded right-hand side's error budget: Lambda_P is at most
+    # ~ (h^2 + w^2) / (2 pi^2) in size
+    want = phi - phi.mean(axis=(1, 2), keepdims=True)
+    amp = (h * h + w * w) / (2 * np.pi ** 2)
+    assert _rel(got, want) < 1e-7 * amp, _rel(got, want)
+
+
+@pytest.mark.parametrize("h,w", [(1, 1), (2, 3), (3, 2), (4, 4), (3, 5)])
+def test_spectral_bruteforce_tiny(oracle_mod, h, w):
+    """Direct quadruple sum with libm cosines (numpy), no separable form."""
+    o = oracle_mod
+    x = inputs.uniform(33 + h * w, 2, h, w)
+    lam = inputs.random_diagonal(34 + h * w, h, w, -1.0, 1.0)
+    a = lambda k, n: math.sqrt((1.0 if k == 0 else 2.0) / n)
+    out = np.zeros((2, h, w))
+    for b in range(2):
+        for i in range(h):
+            for j in range(w):
+                acc = 0.0
+                for k in range(h):
+                    for l in range(w):
+                        coef = 0.0
+                        for i2 in range(h):
+                            for j2 in range(w):
+                                coef += (float(x[b, i2, j2]) * math.cos(math.pi * (2 * i2 + 1) * k / (2 * h))
+                                         * math.cos(math.pi * (2 * j2 + 1) * l / (2 * w)))
+                        coef *= a(k, h) * a(l, w)
+                        acc += (lam[k, l] * coef * a(k, h) * a(l, w) * math.cos(math.pi * (2 * i + 1) * k / (2 * h))
+                                * math.cos(math.pi * (2 * j + 1) * l / (2 * w)))
+                out[b, i, j] = acc
+    assert _rel(o.spectral(x, lam), out) < 1e-13
+
+
+def test_spectral_symmetric_and_linear_in_lambda(oracle_mod):
+    o = oracle_mod
+    h, w = 16, 24
+    x = inputs.uniform(71, 2, h, w)
+    z = inputs.uniform(72, 2, h, w)
+    l1 = inputs.random_diagonal(73, h, w)
+    l2 = inputs.random_diagonal(74, h, w, -3.0, 1.0)
+    sx = o.spectral(x, l1)
+    # a real diagonal gives a symmetric operator: <S X, Z> = <X, S Z>
+    assert np.allclose(np.sum(sx * z, axis=(1, 2)), np.sum(x.astype(np.float64) * o.spectral(z, l1), axis=(1, 2)),
+                       rtol=1e-12, atol=1e-12)
+    # linear in Lambda
+    assert _rel(o.spectral(x, 2.0 * l1 - l2), 2.0 * sx - o.spectral(x, l2)) < 1e-13
+
+
 # ---------------------------------------------------------------- checker sensitivity
 def _checker_cases(o, h, w):
     x = inputs.uniform(17, 3, h, w)
@@ -229,10 +327,16 @@ def _pins_fail(o) -> list:
     x = inputs.uniform(6, 2, 8, 8)
     if _rel(o.roundtrip(x, 0), x.astype(np.float64)) > 1e-12:
         failed.append("roundtrip")
+    # spectral operator: a cosine mode is an eigenvector with eigenvalue Lambda[k0, l0]
+    lam = inputs.random_diagonal(9, 8, 8)
+    i = np.arange(8)[:, None]
+    xm = (np.cos(np.pi * (2 * i + 1) * 1 / 16) * np.cos(np.pi * (2 * i.T + 1) * 3 / 16)).astype(np.float32)[None]
+    if _rel(o.spectral(xm, lam), lam[1, 3] * xm.astype(np.float64)) > 1e-6:
+        failed.append("spectral-mode")
     return failed
 
 
-@pytest.mark.parametrize("fault", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("fault", [1, 2, 3, 4, 5, 6])
 def test_planted_fault_breaks_a_pin(oracle_mod, fault):
     o = oracle_mod
     assert _pins_fail(o) == []
