@@ -432,6 +432,8 @@ def run_ours(args):
     workloads = None
     if rank == 0 and not args.no_extra:
         workloads = {
+            "spectral_image_poisson_16x16": spectral_image_summary(work, dev, stream, min(args.steps, 200),
+                                                                   check=not args.no_check),
             "square_sweep_512MiB": sweep_summary(dev, [8, 16, 32, 64, 128, 256], 512, ("auto", "split_tc"),
                                                  check=not args.no_check),
             "ragged_4096": ragged_summary(dev),
@@ -552,6 +554,58 @@ def sweep_summary(dev, sizes, mib=512, paths=("auto",), check=True, emit=None):
         del x, y
         torch.cuda.empty_cache()
     return out
+
+
+def spectral_image_summary(work, dev, stream, steps, paths=("fp32", "split_tc"), check=True):
+    """Transform -- Poisson diagonal -- inverse (Prop. 1, Eq. 4) on every
+    16 x 16 block of the rotating image pool, one tiled call per image (the
+    phase-unwrapping block step, Section 1.1); 8 B per element per call."""
+    import ctypes
+    import torch
+    import oracle
+    from paper_2609_28519_gb300 import Plan, inputs, native
+    peak, _ = _peaks()
+    lam = inputs.poisson_diagonal(BLK, BLK)
+    L = native.lib()
+    res = {}
+    for path in paths:
+        plan = Plan(BLK, BLK, kind=native.SPECTRAL, path=path)
+        plan.set_spectral(lam)
+        h = plan.handle
+        p_in = [ctypes.c_void_p(t.data_ptr()) for t in work.imgs]
+        p_out = [ctypes.c_void_p(t.data_ptr()) for t in work.outs]
+
+        def fn(cs, reps=steps):
+            sp = ctypes.c_void_p(cs.cuda_stream)
+            for i in range(reps):
+                k = i % work.pool
+                if L.bdct_execute_tiled(h, native.SPECTRAL, p_in[k], p_out[k], IMG, IMG, IMG, IMG, sp):
+                    raise RuntimeError("bdct_execute_tiled failed")
+        fn(stream, 3)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        cs = torch.cuda.Stream(dev)
+        cs.wait_stream(stream)
+        with torch.cuda.graph(g, stream=cs):
+            fn(cs)
+        torch.cuda.synchronize()
+        g.replay()
+        ms = replay_ms(g, stream) / steps
+        gbs = IMG * IMG * 8 / (ms * 1e-3) / 1e9
+        ent = {"variant": plan.info().variant, "us_per_call": ms * 1e3, "GB/s": gbs, "frac": gbs / peak}
+        if check:
+            src = inputs.image_to_blocks(work.imgs[0].cpu().numpy(), BLK, BLK)
+            fn(stream, 1)
+            torch.cuda.synchronize()
+            got = inputs.image_to_blocks(work.outs[0].cpu().numpy(), BLK, BLK)
+            idx = np.random.default_rng(1).choice(len(src), 256, replace=False)
+            sc = float(np.max(np.abs(lam)))
+            m = oracle.metrics(got[idx] / sc, oracle.spectral(src[idx], lam) / sc, src[idx])
+            ent.update({"e_rel_max": m["e_rel_max"], "accepted": bool(oracle.accept(m)),
+                        "criterion": "Eq. 5 on U^T (Lambda / max|Lambda|) U, 256 sampled blocks"})
+        res[path] = ent
+        plan.close()
+    return res
 
 
 def run_sweep(args):

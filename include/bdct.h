@@ -10,6 +10,10 @@
  *   The round trip C^{-1}(C(X)) has exact result X (Section 2.1); it is
  *   computed with one read and one write of every element, the normalization
  *   folded between the forward core and its adjoint (Prop. 1, Eq. 4).
+ *   The spectral direction is Prop. 1 with a general diagonal: the
+ *   transform -- diagonal spectral operator -- inverse composition
+ *   U^T Lambda U X = Q_h^T (Lambda o (Q_h X Q_w^T)) Q_w (Eq. 4), for instance
+ *   the Poisson solve of a phase-unwrapping method (Section 1.1).
  *
  * Normalization (Section 2.1 names FFTW's REDFT10/REDFT01 pair):
  *   BDCT_NORM_ORTHO  Eq. 1-2 exactly.
@@ -57,6 +61,7 @@ extern "C" {
 #define BDCT_FORWARD   1u  /* 2D DCT-II, Eq. 2 left */
 #define BDCT_INVERSE   2u  /* 2D DCT-III, Eq. 2 right */
 #define BDCT_ROUNDTRIP 4u  /* C^{-1}(C(X)), normalized */
+#define BDCT_SPECTRAL  8u  /* U^T Lambda U X, Prop. 1 / Eq. 4 (needs bdct_plan_set_spectral) */
 
 /* ---------------------------------------------------------- normalization */
 #define BDCT_NORM_ORTHO 0
@@ -80,8 +85,9 @@ extern "C" {
 typedef struct bdct_plan bdct_plan;
 
 /* Create a plan for h = rows, w = cols on the CURRENT CUDA device.
- * kind: non-empty OR of BDCT_FORWARD / BDCT_INVERSE / BDCT_ROUNDTRIP -- the
- *       directions the plan serves (tables are built only for those).
+ * kind: non-empty OR of BDCT_FORWARD / BDCT_INVERSE / BDCT_ROUNDTRIP /
+ *       BDCT_SPECTRAL -- the directions the plan serves (tables are built
+ *       only for those).
  * norm: BDCT_NORM_ORTHO or BDCT_NORM_NONE.   path: one of BDCT_PATH_*.
  * Supported shapes: FP32 path, any 1 <= rows, cols <= 8192 with cols a
  * multiple of 4; power-of-two sides 8..256 run fused on chip, other shapes
@@ -91,6 +97,20 @@ typedef struct bdct_plan bdct_plan;
  * or planning inside a transform).  Plan creation synchronizes the device.
  * On success *plan is set; on failure *plan is NULL and nothing leaks.      */
 int bdct_plan_create(bdct_plan **plan, int rows, int cols, unsigned kind, int norm, int path);
+
+/* Set the diagonal of the plan's spectral direction (Prop. 1, Eq. 4).
+ * lambda: HOST array of rows x cols doubles, row-major, lambda[k*cols + l]
+ * multiplying the orthonormal coefficient (k, l) (k along rows, l along
+ * cols); copied, so the caller keeps ownership.  The plan must have been
+ * created with BDCT_SPECTRAL in its kind (else BDCT_ERR_KIND).  The plan
+ * keeps two FP32 tables computed from it in FP64 on the device: Lambda
+ * itself, and Lambda folded with the squared scales (E Lambda E) for the
+ * kernels that run the unscaled cores.  The spectral composition is the
+ * normalized one under both normalizations (like the round trip).  May be
+ * called again to replace the diagonal; it synchronizes the device, and no
+ * work using the plan may be queued meanwhile.  A spectral execution before
+ * the first call returns BDCT_ERR_INVALID_ARG.                              */
+int bdct_plan_set_spectral(bdct_plan *plan, const double *lambda);
 
 /* Release a plan and its device memory.  The caller must ensure no work
  * using the plan is still queued.  NULL is accepted (no-op).               */
@@ -105,7 +125,11 @@ int bdct_forward(const bdct_plan *plan, const float *in, float *out, size_t batc
 int bdct_inverse(const bdct_plan *plan, const float *in, float *out, size_t batch, void *stream);
 int bdct_roundtrip(const bdct_plan *plan, const float *in, float *out, size_t batch, void *stream);
 
-/* Same as above with the direction as an argument (one of the kind bits). */
+/* Same as above with the direction as an argument (one of the kind bits).
+ * BDCT_SPECTRAL runs in one read and one write of every element on the fused
+ * kernels of sides 8..32 and on the tensor-core route; the other shapes
+ * compose it from the orthonormal forward, the diagonal and the inverse
+ * (three passes over the output).                                          */
 int bdct_execute(const bdct_plan *plan, unsigned kind, const float *in, float *out,
                  size_t batch, void *stream);
 

@@ -69,6 +69,8 @@ static void plan_free(bdct_plan *p)
     if (p->status) cudaFree(p->status);
     if (p->tc_ops) cudaFree(p->tc_ops);
     if (p->line_tw) cudaFree(p->line_tw);
+    if (p->spec_plain) cudaFree(p->spec_plain);
+    if (p->spec_fold) cudaFree(p->spec_fold);
     host_staging_free(p);
     if (p->work) cudaFree(p->work);
     delete p;
@@ -79,7 +81,8 @@ extern "C" int bdct_plan_create(bdct_plan **plan, int rows, int cols, unsigned k
     if (!plan) return BDCT_ERR_INVALID_ARG;
     *plan = nullptr;
     if (rows < 1 || cols < 1) return BDCT_ERR_INVALID_ARG;
-    if (kind == 0 || (kind & ~(BDCT_FORWARD | BDCT_INVERSE | BDCT_ROUNDTRIP))) return BDCT_ERR_INVALID_ARG;
+    if (kind == 0 || (kind & ~(BDCT_FORWARD | BDCT_INVERSE | BDCT_ROUNDTRIP | BDCT_SPECTRAL)))
+        return BDCT_ERR_INVALID_ARG;
     if (norm != BDCT_NORM_ORTHO && norm != BDCT_NORM_NONE) return BDCT_ERR_INVALID_ARG;
     if (path < BDCT_PATH_AUTO || path > BDCT_PATH_BF16) return BDCT_ERR_INVALID_ARG;
     if (rows > 8192 || cols > 8192) return BDCT_ERR_UNSUPPORTED_SHAPE;
@@ -123,8 +126,9 @@ extern "C" int bdct_plan_create(bdct_plan **plan, int rows, int cols, unsigned k
         p->variant = 3;
         p->tc_terms = resolved == BDCT_PATH_SPLIT_TC ? 3 : (resolved == BDCT_PATH_SPLIT_HILO ? 2 : 1);
         const size_t te = tc_table_elems(rows);
-        const size_t ntab = ((kind & BDCT_FORWARD) ? 1 : 0) + ((kind & BDCT_INVERSE) ? 1 : 0) +
-                            ((kind & BDCT_ROUNDTRIP) ? 2 : 0);
+        // the round trip and the spectral direction share the orthonormal pair
+        const bool pair = (kind & (BDCT_ROUNDTRIP | BDCT_SPECTRAL)) != 0;
+        const size_t ntab = ((kind & BDCT_FORWARD) ? 1 : 0) + ((kind & BDCT_INVERSE) ? 1 : 0) + (pair ? 2 : 0);
         e = cudaMalloc(&p->tc_ops, ntab * te * sizeof(__nv_bfloat16));
         if (e != cudaSuccess) { plan_free(p); t_last_cuda_error = (int)e; return BDCT_ERR_NO_MEMORY; }
         p->table_bytes = ntab * te * sizeof(__nv_bfloat16);
@@ -139,7 +143,7 @@ extern "C" int bdct_plan_create(bdct_plan **plan, int rows, int cols, unsigned k
             e = tc_gen_tables(p->tc_ops + off, rows, 2, norm, 0);
             off += te;
         }
-        if (e == cudaSuccess && (kind & BDCT_ROUNDTRIP)) {
+        if (e == cudaSuccess && pair) {
             // the round trip is normalized: orthonormal forward, then its adjoint
             p->tc_off[DIR_RT] = off;
             e = tc_gen_tables(p->tc_ops + off, rows, 1, BDCT_NORM_ORTHO, 0);
@@ -174,7 +178,7 @@ extern "C" int bdct_plan_create(bdct_plan **plan, int rows, int cols, unsigned k
         size_t per_dir = (size_t)rows * rows + (size_t)cols * cols;
         size_t total = 0;
         const bool need[3] = {(kind & BDCT_FORWARD) != 0, (kind & BDCT_INVERSE) != 0,
-                              (kind & BDCT_ROUNDTRIP) != 0};
+                              (kind & (BDCT_ROUNDTRIP | BDCT_SPECTRAL)) != 0};
         size_t nmats = (need[0] ? 1 : 0) + (need[1] ? 1 : 0) + (need[2] ? 2 : 0);
         total = nmats * per_dir;
         e = cudaMalloc(&p->ops, total * sizeof(float));
@@ -204,7 +208,7 @@ extern "C" int bdct_plan_create(bdct_plan **plan, int rows, int cols, unsigned k
         long long chunk = (long long)(kChunkBytes / arr_bytes);
         if (chunk < 1) chunk = 1;
         p->chunk_arrays = chunk;
-        const int nbuf = (kind & BDCT_ROUNDTRIP) ? 2 : 1;
+        const int nbuf = (kind & (BDCT_ROUNDTRIP | BDCT_SPECTRAL)) ? 2 : 1;
         p->work_bytes = (size_t)chunk * arr_bytes * nbuf;
         e = cudaMalloc(&p->work, p->work_bytes);
         if (e != cudaSuccess) { plan_free(p); t_last_cuda_error = (int)e; return BDCT_ERR_NO_MEMORY; }
@@ -233,6 +237,7 @@ static int dir_of(unsigned kind, Dir *d)
         case BDCT_FORWARD: *d = DIR_FWD; return BDCT_OK;
         case BDCT_INVERSE: *d = DIR_INV; return BDCT_OK;
         case BDCT_ROUNDTRIP: *d = DIR_RT; return BDCT_OK;
+        case BDCT_SPECTRAL: *d = DIR_SPEC; return BDCT_OK;
         default: return BDCT_ERR_INVALID_ARG;
     }
 }
@@ -244,8 +249,8 @@ static bool ranges_partially_overlap(const void *a, const void *b, size_t bytes)
     return x < y + bytes && y < x + bytes;
 }
 
-static int run_lines(const bdct_plan *p, Dir dir, const float *in, const long long *in_off, float *out,
-                     const long long *out_off, long long count, cudaStream_t s)
+static int run_lines(const bdct_plan *p, Dir dir, const DirScales &sc, const float *in, const long long *in_off,
+                     float *out, const long long *out_off, long long count, cudaStream_t s)
 {
     const int h = p->rows, w = p->cols;
     const long long hw = (long long)h * w;
@@ -254,10 +259,10 @@ static int run_lines(const bdct_plan *p, Dir dir, const float *in, const long lo
         const float *src = in_off ? in : in + b0 * hw;
         float *dst = out_off ? out : out + b0 * hw;
         // rows of X (h lines of w) -> workspace (w x h), then rows of that (w lines of h) -> out (h x w)
-        cudaError_t e = lines_pass(src, p->work, h, w, nb, dir, p->scales[dir].w, p->line_tw, p->status, s,
+        cudaError_t e = lines_pass(src, p->work, h, w, nb, dir, sc.w, p->line_tw, p->status, s,
                                    in_off ? in_off + b0 : nullptr, nullptr);
         if (e == cudaSuccess)
-            e = lines_pass(p->work, dst, w, h, nb, dir, p->scales[dir].h, p->line_tw + p->line_tw_h, p->status, s,
+            e = lines_pass(p->work, dst, w, h, nb, dir, sc.h, p->line_tw + p->line_tw_h, p->status, s,
                            nullptr, out_off ? out_off + b0 : nullptr, true);
         if (e != cudaSuccess) return cuda_fail(e);
     }
@@ -269,8 +274,9 @@ static int run_separable(const bdct_plan *p, Dir dir, const float *in, const lon
 {
     const int h = p->rows, w = p->cols;
     const long long hw = (long long)h * w;
-    const float *oph = p->ops + p->op_h_off[dir];
-    const float *opw = p->ops + p->op_w_off[dir];
+    const Dir mdir = dir == DIR_SPEC ? DIR_RT : dir;  // the spectral direction uses the orthonormal pair
+    const float *oph = p->ops + p->op_h_off[mdir];
+    const float *opw = p->ops + p->op_w_off[mdir];
     const size_t per_dir = (size_t)h * h + (size_t)w * w;
     float *w1 = p->work;
     float *w2 = p->work + (size_t)p->chunk_arrays * hw;
@@ -284,7 +290,7 @@ static int run_separable(const bdct_plan *p, Dir dir, const float *in, const lon
         // first pass: rows of the input into w1
         if (ioff) e = dense_pass_rows_indexed(in, ioff, w1, opw, h, w, nb, s);
         else e = dense_pass_rows(src, w1, opw, (int)(nb * h), w, s);
-        if (dir != DIR_RT) {
+        if (dir != DIR_RT && dir != DIR_SPEC) {
             if (e == cudaSuccess) {
                 if (ooff) e = dense_pass_cols_indexed(w1, out, ooff, oph, h, w, nb, s);
                 else e = dense_pass_cols(w1, dst, oph, h, w, nb, s);
@@ -293,6 +299,11 @@ static int run_separable(const bdct_plan *p, Dir dir, const float *in, const lon
             // forward core, then the adjoint core (orthonormal pair)
             const float *ioph = oph + per_dir, *iopw = opw + per_dir;
             if (e == cudaSuccess) e = dense_pass_cols(w1, w2, oph, h, w, nb, s);
+            if (e == cudaSuccess && dir == DIR_SPEC) {
+                // the orthonormal spectrum of the chunk, times Lambda (Eq. 4)
+                ExecGeom gw{w2, w2, nb, 0, 0, 0, 0};
+                e = spectral_scale(gw, h, w, p->spec_plain, s);
+            }
             if (e == cudaSuccess) e = dense_pass_cols(w2, w1, ioph, h, w, nb, s);
             if (e == cudaSuccess) {
                 if (ooff) e = dense_pass_rows_out_indexed(w1, out, ooff, iopw, h, w, nb, s);
@@ -304,21 +315,69 @@ static int run_separable(const bdct_plan *p, Dir dir, const float *in, const lon
     return BDCT_OK;
 }
 
+// Orthonormal scales of one direction (the spectral composition of the
+// kernel families without a fused spectral kernel runs the orthonormal forward
+// and inverse around the diagonal, whatever the plan's normalization).
+static DirScales ortho_scales(const bdct_plan *p, Dir dir)
+{
+    return DirScales{axis_scale(p->rows, dir, BDCT_NORM_ORTHO), axis_scale(p->cols, dir, BDCT_NORM_ORTHO)};
+}
+
+// One direction of a fused or tensor-core plan over geometry g (contiguous,
+// indexed or tiled).  The spectral direction runs fused where a kernel has it
+// (sides 8-32, tensor cores) and otherwise as orthonormal forward (in -> out),
+// Lambda (in place), orthonormal inverse (out -> out, exact in place).
+static int run_onchip(const bdct_plan *p, Dir dir, const ExecGeom &g0, cudaStream_t s)
+{
+    ExecGeom g = g0;
+    cudaError_t e;
+    if (p->variant == 3) {
+        const Dir tdir = dir == DIR_SPEC ? DIR_RT : dir;  // tables: the orthonormal pair
+        if (dir == DIR_SPEC) g.lam = p->spec_plain;
+        e = tc_launch(p->rows, dir, p->tc_terms, g, p->tc_ops + p->tc_off[tdir], p->status, s);
+        return e == cudaSuccess ? BDCT_OK : cuda_fail(e);
+    }
+    if (dir != DIR_SPEC) {
+        e = fused_launch(p->rows, p->cols, dir, p->scales[dir], g, p->status, s);
+        return e == cudaSuccess ? BDCT_OK : cuda_fail(e);
+    }
+    if (!ring_supported(p->rows, p->cols)) {
+        g.lam = p->spec_fold;
+        e = fused_launch(p->rows, p->cols, DIR_SPEC, p->scales[DIR_RT], g, p->status, s);
+        return e == cudaSuccess ? BDCT_OK : cuda_fail(e);
+    }
+    e = fused_launch(p->rows, p->cols, DIR_FWD, ortho_scales(p, DIR_FWD), g, p->status, s);
+    if (e == cudaSuccess) e = spectral_scale(g, p->rows, p->cols, p->spec_plain, s);
+    if (e == cudaSuccess) {
+        ExecGeom gi = g;
+        gi.in = g.out;
+        gi.in_off = g.out_off;
+        gi.ld_in = g.ld_out;
+        e = fused_launch(p->rows, p->cols, DIR_INV, ortho_scales(p, DIR_INV), gi, p->status, s);
+    }
+    return e == cudaSuccess ? BDCT_OK : cuda_fail(e);
+}
+
 int bdct::plan_execute(const bdct_plan *p, Dir dir, const float *in, const long long *in_off, float *out,
                        const long long *out_off, long long count, cudaStream_t s)
 {
     if (count <= 0) return BDCT_OK;
-    if (p->variant == 1) {
+    if (dir == DIR_SPEC && !p->spec_plain) return BDCT_ERR_INVALID_ARG;  // no diagonal set
+    if (p->variant == 1 || p->variant == 3) {
         ExecGeom g{in, out, count, 0, 0, 0, 0, in_off, out_off};
-        cudaError_t e = fused_launch(p->rows, p->cols, dir, p->scales[dir], g, p->status, s);
-        return e == cudaSuccess ? BDCT_OK : cuda_fail(e);
+        return run_onchip(p, dir, g, s);
     }
-    if (p->variant == 3) {
-        ExecGeom g{in, out, count, 0, 0, 0, 0, in_off, out_off};
-        cudaError_t e = tc_launch(p->rows, dir, p->tc_terms, g, p->tc_ops + p->tc_off[dir], p->status, s);
-        return e == cudaSuccess ? BDCT_OK : cuda_fail(e);
+    if (p->lines) {
+        if (dir != DIR_SPEC) return run_lines(p, dir, p->scales[dir], in, in_off, out, out_off, count, s);
+        int st = run_lines(p, DIR_FWD, ortho_scales(p, DIR_FWD), in, in_off, out, out_off, count, s);
+        if (st == BDCT_OK) {
+            ExecGeom g{out, out, count, 0, 0, 0, 0, out_off, out_off};
+            cudaError_t e = spectral_scale(g, p->rows, p->cols, p->spec_plain, s);
+            if (e != cudaSuccess) return cuda_fail(e);
+            st = run_lines(p, DIR_INV, ortho_scales(p, DIR_INV), out, out_off, out, out_off, count, s);
+        }
+        return st;
     }
-    if (p->lines) return run_lines(p, dir, in, in_off, out, out_off, count, s);
     return run_separable(p, dir, in, in_off, out, out_off, count, s);
 }
 
@@ -377,16 +436,50 @@ extern "C" int bdct_execute_tiled(const bdct_plan *plan, unsigned kind, const fl
     } else if (ld_in != ld_out) {
         return BDCT_ERR_ALIAS;
     }
+    if (dir == DIR_SPEC && !plan->spec_plain) return BDCT_ERR_INVALID_ARG;  // no diagonal set
     const int tpr = img_cols / plan->cols;
     const long long tiles = (long long)(img_rows / plan->rows) * tpr;
     ExecGeom g{in, out, tiles, 1, tpr, (long long)ld_in, (long long)ld_out};
-    cudaError_t e;
-    if (plan->variant == 3)
-        e = tc_launch(plan->rows, dir, plan->tc_terms, g, plan->tc_ops + plan->tc_off[dir], plan->status,
-                      (cudaStream_t)stream);
-    else
-        e = fused_launch(plan->rows, plan->cols, dir, plan->scales[dir], g, plan->status, (cudaStream_t)stream);
-    return e == cudaSuccess ? BDCT_OK : cuda_fail(e);
+    return run_onchip(plan, dir, g, (cudaStream_t)stream);
+}
+
+extern "C" int bdct_plan_set_spectral(bdct_plan *plan, const double *lambda)
+{
+    if (!plan || !lambda) return BDCT_ERR_INVALID_ARG;
+    if (!(plan->kind & BDCT_SPECTRAL)) return BDCT_ERR_KIND;
+    int cur = -1;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (cur != plan->device) {
+        e = cudaSetDevice(plan->device);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    const size_t n = (size_t)plan->rows * plan->cols;
+    int st = BDCT_OK;
+    double *d_lam = nullptr;
+    if (!plan->spec_plain) {
+        e = cudaMalloc(&plan->spec_plain, n * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&plan->spec_fold, n * sizeof(float));
+        if (e != cudaSuccess) {
+            if (plan->spec_plain) cudaFree(plan->spec_plain);
+            plan->spec_plain = nullptr;
+            t_last_cuda_error = (int)e;
+            st = BDCT_ERR_NO_MEMORY;
+        }
+    }
+    if (st == BDCT_OK) {
+        e = cudaMalloc(&d_lam, n * sizeof(double));
+        if (e != cudaSuccess) { t_last_cuda_error = (int)e; st = BDCT_ERR_NO_MEMORY; }
+    }
+    if (st == BDCT_OK) {
+        e = cudaMemcpy(d_lam, lambda, n * sizeof(double), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = spectral_gen_tables(d_lam, plan->spec_plain, plan->spec_fold, plan->rows, plan->cols, 0);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) st = cuda_fail(e);
+    }
+    if (d_lam) cudaFree(d_lam);
+    if (cur >= 0 && cur != plan->device) cudaSetDevice(cur);
+    return st;
 }
 
 extern "C" int bdct_plan_get_info(const bdct_plan *plan, bdct_plan_info *info)

@@ -72,9 +72,15 @@ struct ExecGeom {
     // indexed batch (ragged classes): array a starts at in + in_off[a] and
     // out + out_off[a] (device arrays of element offsets); null = contiguous
     const long long *in_off = nullptr, *out_off = nullptr;
+    // spectral direction only: the h x w diagonal (row k = frequency index
+    // along h) -- folded with the scales (E Lambda E of Prop. 1) for kernels
+    // that run the unscaled cores, plain Lambda for the tensor-core route
+    const float *lam = nullptr;
 };
 
-enum Dir { DIR_FWD = 0, DIR_INV = 1, DIR_RT = 2 };
+// Directions of one call.  DIR_SPEC is the transform -- diagonal spectral
+// operator -- inverse composition U^T Lambda U of Prop. 1 (Eq. 4).
+enum Dir { DIR_FWD = 0, DIR_INV = 1, DIR_RT = 2, DIR_SPEC = 3 };
 
 // True when the environment variable BDCT_DEBUG is set: kernel launchers then
 // print their launch configuration once to stderr.
@@ -142,6 +148,16 @@ cudaError_t tc_gen_tables(__nv_bfloat16 *dst, int n, int direction, int norm, cu
 // orthonormal forward, then orthonormal inverse); terms = 3, 2 or 1.
 cudaError_t tc_launch(int n, Dir dir, int terms, const ExecGeom &g, const __nv_bfloat16 *ops,
                       unsigned int *status, cudaStream_t stream);
+
+// ---- spectral.cu
+// Build the plan's spectral tables from a device copy of Lambda (FP64, h x w):
+// plain[k][l] = Lambda[k][l] and fold[k][l] = e_h[k] Lambda[k][l] e_w[l] with
+// e_n = the squared scales of Eq. 1 (1/n at index 0, 2/n elsewhere), both
+// rounded once to FP32.
+cudaError_t spectral_gen_tables(const double *lam, float *plain, float *fold, int h, int w, cudaStream_t s);
+// Multiply every h x w array of the call's OUTPUT geometry (contiguous,
+// indexed through out_off, or tiles of an image) by lam elementwise, in place.
+cudaError_t spectral_scale(const ExecGeom &g, int h, int w, const float *lam, cudaStream_t s);
 
 // ---- dense_passes.cu
 // Separable dense passes through a workspace, any shape.  `op_h`, `op_w` are

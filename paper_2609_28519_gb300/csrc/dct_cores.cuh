@@ -276,13 +276,28 @@ __device__ __forceinline__ void scale_line(V (&x)[N], AxisScale s)
     for (int k = 1; k < N; ++k) x[k] = O::mul(x[k], s.s1);
 }
 
+// Unscaled cores, used where every scale is folded into a table (the
+// spectral composition of Prop. 1): CORE_FWD = G (DCT-II), CORE_INV = G^T
+// (DCT-III).
+constexpr int CORE_FWD = 4;
+constexpr int CORE_INV = 5;
+
 // One direction of the 2D transform along one axis of a line held in
-// registers (or of two lines, V = float2).
+// registers (or of two lines, V = float2); DIR may also be CORE_FWD or
+// CORE_INV (no scale).
 template <int N, int DIR, typename V = float>
 __device__ __forceinline__ void line_op(V (&x)[N], AxisScale s)
 {
     V y[N];
-    if constexpr (DIR == DIR_FWD) {
+    if constexpr (DIR == CORE_FWD) {
+        DCT2<N, V>::run(x, y);
+#pragma unroll
+        for (int k = 0; k < N; ++k) x[k] = y[k];
+    } else if constexpr (DIR == CORE_INV) {
+        DCT3<N, V>::run(x, y);
+#pragma unroll
+        for (int k = 0; k < N; ++k) x[k] = y[k];
+    } else if constexpr (DIR == DIR_FWD) {
         DCT2<N, V>::run(x, y);
         scale_line<N, V>(y, s);
 #pragma unroll
@@ -297,6 +312,19 @@ __device__ __forceinline__ void line_op(V (&x)[N], AxisScale s)
         scale_line<N, V>(y, s);
         DCT3<N, V>::run(y, x);
     }
+}
+
+// Transform -- diagonal -- adjoint along one line (the middle factor of
+// Prop. 1, Eq. 4): y = G x, y_k *= d[k], x = G^T y, unscaled cores (the
+// scales of both axes are folded into d).
+template <int N>
+__device__ __forceinline__ void line_spectral(float (&x)[N], const float (&d)[N])
+{
+    float y[N];
+    DCT2<N, float>::run(x, y);
+#pragma unroll
+    for (int k = 0; k < N; ++k) y[k] *= d[k];
+    DCT3<N, float>::run(y, x);
 }
 
 // line_op on two lines a and b held as plain float arrays (for instance two

@@ -160,6 +160,7 @@ struct FusedParams {
     DirScales sc;
     unsigned int *status;
     const long long *in_off, *out_off;  // indexed batch, or null
+    const float *lam;     // spectral only: folded diagonal, h x w
 };
 
 // Start of array a of the batch (contiguous or indexed).
@@ -252,6 +253,126 @@ __device__ __forceinline__ void cta_sync()
     else __syncthreads();
 }
 
+// Column pass over one stage: one column (or two adjacent columns, as one
+// packed line) per thread per step, 1D operation OP along h (a direction of
+// line_op, or an unscaled core).
+template <int H, int W, bool TILED, int OP>
+__device__ __forceinline__ void col_pass(float *stage, int n, int warp, int lane, AxisScale sc)
+{
+    using C = FusedCfg<H, W, TILED>;
+    if constexpr (C::PAIR1) {
+#pragma unroll
+        for (int j = 0; j < C::J1; ++j) {
+            int a, col;
+            if constexpr (C::LAYOUT == LAY_STRIP) {
+                const int s2 = 2 * (lane + 32 * (warp + C::NW * j));  // even strip column
+                a = s2 / W;
+                col = s2 % W;
+            } else {
+                // lanes: 8 arrays x 4 column pairs; with the 4-mod-8 slot pitch each
+                // half-warp's 8-byte accesses cover the 32 banks once
+                const int combo = warp + C::NW * j;
+                a = (lane & 7) + 8 * (combo % (C::G / 8));
+                col = 2 * ((lane >> 3) + 4 * (combo / (C::G / 8)));
+            }
+            if (a < n) {
+                // the two columns run as one packed line (float2 cores)
+                float2 *q = reinterpret_cast<float2 *>(stage + elem<H, W, TILED>(a, 0, col));
+                constexpr int RS2 = row_stride<H, W, TILED>() / 2;
+                float2 x[H];
+#pragma unroll
+                for (int i = 0; i < H; ++i) x[i] = q[i * RS2];
+                line_op<H, OP, float2>(x, sc);
+#pragma unroll
+                for (int i = 0; i < H; ++i) q[i * RS2] = x[i];
+            }
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < C::J1; ++j) {
+            int a, col;
+            map_col<H, W, TILED>(j, warp, lane, a, col);
+            if (a < n) {
+                float *q = stage + elem<H, W, TILED>(a, 0, col);
+                constexpr int RS = row_stride<H, W, TILED>();
+                float x[H];
+#pragma unroll
+                for (int i = 0; i < H; ++i) x[i] = q[i * RS];
+                line_op<H, OP>(x, sc);
+#pragma unroll
+                for (int i = 0; i < H; ++i) q[i * RS] = x[i];
+            }
+        }
+    }
+}
+
+// Row pass over one stage: one row per thread per step, 1D operation along w;
+// with an even number of rows per thread the rows go in packed pairs.  For
+// the spectral direction each row k runs transform -- row k of the folded
+// diagonal -- adjoint (line_spectral).
+template <int H, int W, bool TILED, int DIR>
+__device__ __forceinline__ void row_pass(float *stage, int n, int warp, int lane, AxisScale sc, const float *lam)
+{
+    using C = FusedCfg<H, W, TILED>;
+    if constexpr (C::PAIR2 && DIR != DIR_SPEC) {
+#pragma unroll
+        for (int j = 0; j < C::J2; j += 2) {
+            int a0, r0, a1, r1;
+            map_row<H, W, TILED>(j, warp, lane, a0, r0);
+            map_row<H, W, TILED>(j + 1, warp, lane, a1, r1);
+            const bool v0 = a0 < n, v1 = a1 < n;
+            float4 *q0 = reinterpret_cast<float4 *>(stage + elem<H, W, TILED>(v0 ? a0 : 0, r0, 0));
+            float4 *q1 = reinterpret_cast<float4 *>(stage + elem<H, W, TILED>(v1 ? a1 : 0, r1, 0));
+            float x0[W], x1[W];
+#pragma unroll
+            for (int v = 0; v < W / 4; ++v) {
+                const float4 t0 = q0[v], t1 = q1[v];
+                x0[4 * v] = t0.x; x0[4 * v + 1] = t0.y; x0[4 * v + 2] = t0.z; x0[4 * v + 3] = t0.w;
+                x1[4 * v] = t1.x; x1[4 * v + 1] = t1.y; x1[4 * v + 2] = t1.z; x1[4 * v + 3] = t1.w;
+            }
+            line_op2<W, DIR>(x0, x1, sc);
+            if (v0) {
+#pragma unroll
+                for (int v = 0; v < W / 4; ++v) q0[v] = make_float4(x0[4 * v], x0[4 * v + 1], x0[4 * v + 2], x0[4 * v + 3]);
+            }
+            if (v1) {
+#pragma unroll
+                for (int v = 0; v < W / 4; ++v) q1[v] = make_float4(x1[4 * v], x1[4 * v + 1], x1[4 * v + 2], x1[4 * v + 3]);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < C::J2; ++j) {
+            int a, r;
+            map_row<H, W, TILED>(j, warp, lane, a, r);
+            if (a < n) {
+                float4 *q = reinterpret_cast<float4 *>(stage + elem<H, W, TILED>(a, r, 0));
+                float x[W];
+#pragma unroll
+                for (int v = 0; v < W / 4; ++v) {
+                    const float4 t = q[v];
+                    x[4 * v] = t.x; x[4 * v + 1] = t.y; x[4 * v + 2] = t.z; x[4 * v + 3] = t.w;
+                }
+                if constexpr (DIR == DIR_SPEC) {
+                    // row r of the spectrum after the column pass holds frequency r along h
+                    float d[W];
+                    const float4 *lr = reinterpret_cast<const float4 *>(lam + r * W);
+#pragma unroll
+                    for (int v = 0; v < W / 4; ++v) {
+                        const float4 t = __ldg(lr + v);
+                        d[4 * v] = t.x; d[4 * v + 1] = t.y; d[4 * v + 2] = t.z; d[4 * v + 3] = t.w;
+                    }
+                    line_spectral<W>(x, d);
+                } else {
+                    line_op<W, DIR>(x, sc);
+                }
+#pragma unroll
+                for (int v = 0; v < W / 4; ++v) q[v] = make_float4(x[4 * v], x[4 * v + 1], x[4 * v + 2], x[4 * v + 3]);
+            }
+        }
+    }
+}
+
 template <int H, int W, int DIR, bool TILED>
 __global__ void __launch_bounds__(FusedCfg<H, W, TILED>::THREADS, FusedCfg<H, W, TILED>::MIN_CTAS) k_fused(const FusedParams p)
 {
@@ -280,7 +401,9 @@ __global__ void __launch_bounds__(FusedCfg<H, W, TILED>::THREADS, FusedCfg<H, W,
                 issue_fill<H, W, TILED>(p, chunk_geom<H, W, TILED>(p, c), smem + s * C::STAGE_FLOATS, &full[s], lane);
         }
     }
-    constexpr bool DEFER = C::STAGES >= 3 || DIR != DIR_RT;  // refill policy (see the end of the loop)
+    // refill policy (see the end of the loop): the round trip and the spectral
+    // direction carry twice the arithmetic of one direction
+    constexpr bool DEFER = C::STAGES >= 3 || (DIR != DIR_RT && DIR != DIR_SPEC);
 
     int failed_at = -1;   // iteration whose stage wait expired, if any
     int s = 0;            // stage of the current chunk
@@ -296,51 +419,9 @@ __global__ void __launch_bounds__(FusedCfg<H, W, TILED>::THREADS, FusedCfg<H, W,
         const ChunkGeom g = chunk_geom<H, W, TILED>(p, c);
         const int n = g.n;
 
-        // pass 1: one column (or two adjacent columns) per thread per step,
-        // 1D core along h
-        if constexpr (C::PAIR1) {
-#pragma unroll
-            for (int j = 0; j < C::J1; ++j) {
-                int a, col;
-                if constexpr (C::LAYOUT == LAY_STRIP) {
-                    const int s2 = 2 * (lane + 32 * (warp + C::NW * j));  // even strip column
-                    a = s2 / W;
-                    col = s2 % W;
-                } else {
-                    // lanes: 8 arrays x 4 column pairs; with the 4-mod-8 slot pitch each
-                    // half-warp's 8-byte accesses cover the 32 banks once
-                    const int combo = warp + C::NW * j;
-                    a = (lane & 7) + 8 * (combo % (C::G / 8));
-                    col = 2 * ((lane >> 3) + 4 * (combo / (C::G / 8)));
-                }
-                if (a < n) {
-                    // the two columns run as one packed line (float2 cores)
-                    float2 *q = reinterpret_cast<float2 *>(stage + elem<H, W, TILED>(a, 0, col));
-                    constexpr int RS2 = row_stride<H, W, TILED>() / 2;
-                    float2 x[H];
-#pragma unroll
-                    for (int i = 0; i < H; ++i) x[i] = q[i * RS2];
-                    line_op<H, DIR, float2>(x, p.sc.h);
-#pragma unroll
-                    for (int i = 0; i < H; ++i) q[i * RS2] = x[i];
-                }
-            }
-        } else
-#pragma unroll
-        for (int j = 0; j < C::J1; ++j) {
-            int a, col;
-            map_col<H, W, TILED>(j, warp, lane, a, col);
-            if (a < n) {
-                float *q = stage + elem<H, W, TILED>(a, 0, col);
-                constexpr int RS = row_stride<H, W, TILED>();
-                float x[H];
-#pragma unroll
-                for (int i = 0; i < H; ++i) x[i] = q[i * RS];
-                line_op<H, DIR>(x, p.sc.h);
-#pragma unroll
-                for (int i = 0; i < H; ++i) q[i * RS] = x[i];
-            }
-        }
+        // pass 1: columns, 1D operation along h (the spectral direction runs
+        // the unscaled forward core; its scales live in the folded diagonal)
+        col_pass<H, W, TILED, DIR == DIR_SPEC ? CORE_FWD : DIR>(stage, n, warp, lane, p.sc.h);
         if constexpr (C::NW == 1) ok = __all_sync(0xffffffffu, ok);
         else ok = __syncthreads_and(ok);
         if (!ok) {
@@ -348,51 +429,12 @@ __global__ void __launch_bounds__(FusedCfg<H, W, TILED>::THREADS, FusedCfg<H, W,
             break;
         }
 
-        // pass 2: one row per thread per step, 1D core along w; with an even
-        // number of rows per thread the rows go in packed pairs
-        if constexpr (C::PAIR2) {
-#pragma unroll
-            for (int j = 0; j < C::J2; j += 2) {
-                int a0, r0, a1, r1;
-                map_row<H, W, TILED>(j, warp, lane, a0, r0);
-                map_row<H, W, TILED>(j + 1, warp, lane, a1, r1);
-                const bool v0 = a0 < n, v1 = a1 < n;
-                float4 *q0 = reinterpret_cast<float4 *>(stage + elem<H, W, TILED>(v0 ? a0 : 0, r0, 0));
-                float4 *q1 = reinterpret_cast<float4 *>(stage + elem<H, W, TILED>(v1 ? a1 : 0, r1, 0));
-                float x0[W], x1[W];
-#pragma unroll
-                for (int v = 0; v < W / 4; ++v) {
-                    const float4 t0 = q0[v], t1 = q1[v];
-                    x0[4 * v] = t0.x; x0[4 * v + 1] = t0.y; x0[4 * v + 2] = t0.z; x0[4 * v + 3] = t0.w;
-                    x1[4 * v] = t1.x; x1[4 * v + 1] = t1.y; x1[4 * v + 2] = t1.z; x1[4 * v + 3] = t1.w;
-                }
-                line_op2<W, DIR>(x0, x1, p.sc.w);
-                if (v0) {
-#pragma unroll
-                    for (int v = 0; v < W / 4; ++v) q0[v] = make_float4(x0[4 * v], x0[4 * v + 1], x0[4 * v + 2], x0[4 * v + 3]);
-                }
-                if (v1) {
-#pragma unroll
-                    for (int v = 0; v < W / 4; ++v) q1[v] = make_float4(x1[4 * v], x1[4 * v + 1], x1[4 * v + 2], x1[4 * v + 3]);
-                }
-            }
-        } else
-#pragma unroll
-        for (int j = 0; j < C::J2; ++j) {
-            int a, r;
-            map_row<H, W, TILED>(j, warp, lane, a, r);
-            if (a < n) {
-                float4 *q = reinterpret_cast<float4 *>(stage + elem<H, W, TILED>(a, r, 0));
-                float x[W];
-#pragma unroll
-                for (int v = 0; v < W / 4; ++v) {
-                    const float4 t = q[v];
-                    x[4 * v] = t.x; x[4 * v + 1] = t.y; x[4 * v + 2] = t.z; x[4 * v + 3] = t.w;
-                }
-                line_op<W, DIR>(x, p.sc.w);
-#pragma unroll
-                for (int v = 0; v < W / 4; ++v) q[v] = make_float4(x[4 * v], x[4 * v + 1], x[4 * v + 2], x[4 * v + 3]);
-            }
+        // pass 2: rows, 1D operation along w
+        row_pass<H, W, TILED, DIR>(stage, n, warp, lane, p.sc.w, p.lam);
+        if constexpr (DIR == DIR_SPEC) {
+            // pass 3 (spectral only): columns, unscaled adjoint core along h
+            cta_sync<C::NW>();
+            col_pass<H, W, TILED, CORE_INV>(stage, n, warp, lane, p.sc.h);
         }
         fence_proxy_async_smem();
         cta_sync<C::NW>();
@@ -529,6 +571,8 @@ static cudaError_t launch_one(const DirScales &sc, const ExecGeom &g, unsigned i
     p.status = status;
     p.in_off = g.in_off;
     p.out_off = g.out_off;
+    p.lam = g.lam;
+    if (DIR == DIR_SPEC && !p.lam) return cudaErrorInvalidValue;
     long long nch;
     if (!TILED) {
         nch = (g.count + C::G - 1) / C::G;
@@ -564,7 +608,8 @@ static cudaError_t launch_hw(Dir dir, const DirScales &sc, const ExecGeom &g, un
     switch (dir) {
         case DIR_FWD: return t ? launch_one<H, W, DIR_FWD, true>(sc, g, st, s) : launch_one<H, W, DIR_FWD, false>(sc, g, st, s);
         case DIR_INV: return t ? launch_one<H, W, DIR_INV, true>(sc, g, st, s) : launch_one<H, W, DIR_INV, false>(sc, g, st, s);
-        default: return t ? launch_one<H, W, DIR_RT, true>(sc, g, st, s) : launch_one<H, W, DIR_RT, false>(sc, g, st, s);
+        case DIR_RT: return t ? launch_one<H, W, DIR_RT, true>(sc, g, st, s) : launch_one<H, W, DIR_RT, false>(sc, g, st, s);
+        default: return t ? launch_one<H, W, DIR_SPEC, true>(sc, g, st, s) : launch_one<H, W, DIR_SPEC, false>(sc, g, st, s);
     }
 }
 
@@ -583,7 +628,10 @@ static cudaError_t launch_h(int cols, Dir dir, const DirScales &sc, const ExecGe
 cudaError_t fused_launch(int rows, int cols, Dir dir, const DirScales &sc, const ExecGeom &g,
                          unsigned int *status, cudaStream_t stream)
 {
-    if (ring_supported(rows, cols)) return ring_launch(rows, cols, dir, sc, g, status, stream);
+    if (ring_supported(rows, cols)) {
+        if (dir == DIR_SPEC) return cudaErrorInvalidValue;  // composed by the caller from F, scale, I
+        return ring_launch(rows, cols, dir, sc, g, status, stream);
+    }
     switch (rows) {
         case 8: return launch_h<8>(cols, dir, sc, g, status, stream);
         case 16: return launch_h<16>(cols, dir, sc, g, status, stream);

@@ -32,6 +32,7 @@ int dir_of_kind(unsigned k, Dir *d)
         case BDCT_FORWARD: *d = DIR_FWD; return BDCT_OK;
         case BDCT_INVERSE: *d = DIR_INV; return BDCT_OK;
         case BDCT_ROUNDTRIP: *d = DIR_RT; return BDCT_OK;
+        case BDCT_SPECTRAL: *d = DIR_SPEC; return BDCT_OK;
         default: return BDCT_ERR_INVALID_ARG;
     }
 }

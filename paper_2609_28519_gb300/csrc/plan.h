@@ -32,6 +32,9 @@ struct bdct_plan {
     __nv_bfloat16 *tc_ops = nullptr;
     size_t tc_off[3] = {0, 0, 0};
     int tc_terms = 3;
+    // spectral direction (bdct_plan_set_spectral): Lambda in FP32, and Lambda
+    // folded with the squared scales for the unscaled fused cores (Prop. 1)
+    float *spec_plain = nullptr, *spec_fold = nullptr;
     // host-buffer execution (bdct_plan_set_host_staging): kStageSlots slots of
     // two device buffers, and streams/events of the copy-in / transform /
     // copy-out pipeline

@@ -128,6 +128,7 @@ struct TcParams {
     long long ld_in, ld_out;  // tiled only
     int ntiles;
     const __nv_bfloat16 *ops;  // operator term tables, [op][term][B layout]
+    const float *lam;          // spectral only: the N x N diagonal Lambda[k][l]
     unsigned int *status;
     const long long *in_off, *out_off;  // indexed batch, or null
 };
@@ -217,7 +218,10 @@ __device__ __forceinline__ void tile_geom(const TcParams &p, int tile, long long
 }
 
 // NPASS = 2 (forward or inverse; ops 0, 0) or 4 (round trip; ops 0, 0, 1, 1).
-template <int N, int NPASS, int TERMS, bool TILED>
+// SPEC (with NPASS = 4): the spectral composition of Prop. 1 -- after the
+// second product every coefficient is multiplied by Lambda (the operators are
+// the orthonormal forward and inverse, so the plain diagonal applies).
+template <int N, int NPASS, int TERMS, bool TILED, bool SPEC = false>
 __global__ void __launch_bounds__(128) k_tc_split(const TcParams p)
 {
     using C = TcCfg<N>;
@@ -334,6 +338,14 @@ __global__ void __launch_bounds__(128) k_tc_split(const TcParams p)
             const uint32_t taddr = d_tmem[pass & 1] + ((uint32_t)(32 * warp) << 16);
 #pragma unroll
             for (int c = 0; c < N / 16; ++c) tmem_ld16(taddr + 16 * c, v + 16 * c);
+            if constexpr (SPEC) {
+                // after the second product thread (array, l) holds column l of
+                // the spectrum, v[k] = Y[k][l]
+                if (pass == 1) {
+#pragma unroll
+                    for (int k = 0; k < N; ++k) v[k] *= __ldg(p.lam + k * N + r_local);
+                }
+            }
         }
         if (!ok) break;
         // ---- store.  After two passes thread (array, c) holds column c of the
@@ -428,12 +440,12 @@ cudaError_t tc_gen_tables(__nv_bfloat16 *dst, int n, int direction, int norm, cu
     return cudaGetLastError();
 }
 
-template <int N, int NPASS, int TERMS, bool TILED>
+template <int N, int NPASS, int TERMS, bool TILED, bool SPEC = false>
 static cudaError_t tc_launch_one(const TcParams &p0, const __nv_bfloat16 *ops, cudaStream_t stream)
 {
     using C = TcCfg<N>;
     constexpr int NOPS = NPASS / 2;
-    auto kern = k_tc_split<N, NPASS, TERMS, TILED>;
+    auto kern = k_tc_split<N, NPASS, TERMS, TILED, SPEC>;
     const size_t smem = (size_t)TERMS * C::A_TERM_BYTES + (size_t)NOPS * 3 * C::B_TERM_BYTES + 64;
     static DeviceLaunchCache cache;
     int dev = 0, blocks_per_sm = 0, num_sms = 0;
@@ -477,6 +489,7 @@ static cudaError_t tc_launch_one(const TcParams &p0, const __nv_bfloat16 *ops, c
     if (e != cudaSuccess) return e;
     TcParams p = p0;
     p.ops = ops;
+    if (SPEC && !p.lam) return cudaErrorInvalidValue;
     long long nt;
     if (!TILED) {
         nt = (p.count + C::G - 1) / C::G;
@@ -507,6 +520,9 @@ static cudaError_t tc_launch_nt(Dir dir, const TcParams &p, const __nv_bfloat16 
 {
     if (dir == DIR_RT)
         return tiled ? tc_launch_one<N, 4, TERMS, true>(p, ops, s) : tc_launch_one<N, 4, TERMS, false>(p, ops, s);
+    if (dir == DIR_SPEC)
+        return tiled ? tc_launch_one<N, 4, TERMS, true, true>(p, ops, s)
+                     : tc_launch_one<N, 4, TERMS, false, true>(p, ops, s);
     return tiled ? tc_launch_one<N, 2, TERMS, true>(p, ops, s) : tc_launch_one<N, 2, TERMS, false>(p, ops, s);
 }
 
@@ -534,6 +550,7 @@ cudaError_t tc_launch(int n, Dir dir, int terms, const ExecGeom &g, const __nv_b
     p.status = status;
     p.in_off = g.in_off;
     p.out_off = g.out_off;
+    p.lam = g.lam;
     const bool tiled = g.tiled != 0;
     switch (n) {
         case 16: return tc_launch_n<16>(dir, terms, p, ops, stream, tiled);

@@ -16,20 +16,20 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libbdct.so")
 
 # kinds, norms, paths, statuses (mirrors include/bdct.h)
-FORWARD, INVERSE, ROUNDTRIP = 1, 2, 4
+FORWARD, INVERSE, ROUNDTRIP, SPECTRAL = 1, 2, 4, 8
 NORM_ORTHO, NORM_NONE = 0, 1
 PATH_AUTO, PATH_FP32, PATH_SPLIT_TC, PATH_SPLIT_HILO, PATH_BF16 = 0, 1, 2, 3, 4
 PATHS = {"auto": PATH_AUTO, "fp32": PATH_FP32, "split_tc": PATH_SPLIT_TC,
          "split_hilo": PATH_SPLIT_HILO, "bf16": PATH_BF16}
 NORMS = {"ortho": NORM_ORTHO, "none": NORM_NONE}
-KINDS = {"forward": FORWARD, "inverse": INVERSE, "roundtrip": ROUNDTRIP}
+KINDS = {"forward": FORWARD, "inverse": INVERSE, "roundtrip": ROUNDTRIP, "spectral": SPECTRAL}
 STATUS = {0: "OK", 1: "ERR_INVALID_ARG", 2: "ERR_UNSUPPORTED_SHAPE", 3: "ERR_KIND",
           4: "ERR_ALIGN", 5: "ERR_ALIAS", 6: "ERR_CUDA", 7: "ERR_ARCH",
           8: "ERR_DEVICE_TIMEOUT", 9: "ERR_NO_MEMORY", 10: "ERR_PATH"}
 
 # every symbol the header declares, in declaration order
 EXPORTS = [
-    "bdct_plan_create", "bdct_plan_destroy", "bdct_forward", "bdct_inverse", "bdct_roundtrip",
+    "bdct_plan_create", "bdct_plan_set_spectral", "bdct_plan_destroy", "bdct_forward", "bdct_inverse", "bdct_roundtrip",
     "bdct_execute", "bdct_execute_tiled", "bdct_plan_set_host_staging", "bdct_execute_host",
     "bdct_execute_tiled_host", "bdct_plan_get_info", "bdct_plan_device_status",
     "bdct_ragged_create", "bdct_ragged_execute", "bdct_ragged_destroy", "bdct_ragged_num_classes",
@@ -76,6 +76,7 @@ def lib() -> ctypes.CDLL:
             vp, sz, ci, cu = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_uint
             L.bdct_plan_create.argtypes = [ctypes.POINTER(vp), ci, ci, cu, ci, ci]
             L.bdct_plan_destroy.argtypes = [vp]
+            L.bdct_plan_set_spectral.argtypes = [vp, vp]
             for name in ("bdct_forward", "bdct_inverse", "bdct_roundtrip"):
                 getattr(L, name).argtypes = [vp, vp, vp, sz, vp]
             L.bdct_execute.argtypes = [vp, cu, vp, vp, sz, vp]
@@ -117,7 +118,7 @@ def _stream_of(t, stream):
 class Plan:
     """A plan for rows x cols arrays (``bdct_plan_create``)."""
 
-    def __init__(self, rows: int, cols: int, kind=FORWARD | INVERSE | ROUNDTRIP,
+    def __init__(self, rows: int, cols: int, kind=FORWARD | INVERSE | ROUNDTRIP | SPECTRAL,
                  norm="ortho", path="auto"):
         L = lib()
         self.rows, self.cols = int(rows), int(cols)
@@ -190,6 +191,18 @@ class Plan:
 
     def roundtrip(self, x, out=None, stream=None):
         return self.execute(ROUNDTRIP, x, out, stream)
+
+    def set_spectral(self, lam) -> None:
+        """The rows x cols diagonal of the spectral direction (numpy, any float
+        dtype; passed as row-major float64 to bdct_plan_set_spectral)."""
+        import numpy as np
+        a = np.ascontiguousarray(lam, dtype=np.float64)
+        if a.shape != (self.rows, self.cols):
+            raise ValueError(f"diagonal must be ({self.rows}, {self.cols}), got {a.shape}")
+        _check(lib().bdct_plan_set_spectral(self.handle, ctypes.c_void_p(a.ctypes.data)), "bdct_plan_set_spectral")
+
+    def spectral(self, x, out=None, stream=None):
+        return self.execute(SPECTRAL, x, out, stream)
 
     def set_host_staging(self, chunk_bytes: int = 8 << 20) -> None:
         _check(lib().bdct_plan_set_host_staging(self.handle, int(chunk_bytes)), "bdct_plan_set_host_staging")

@@ -51,7 +51,7 @@ def test_argument_validation_before_cuda(bdct_lib):
     assert L.bdct_plan_create(ctypes.byref(h), 0, 8, 1, 0, 0) == 1
     assert L.bdct_plan_create(ctypes.byref(h), 8, -3, 1, 0, 0) == 1
     assert L.bdct_plan_create(ctypes.byref(h), 8, 8, 0, 0, 0) == 1
-    assert L.bdct_plan_create(ctypes.byref(h), 8, 8, 8, 0, 0) == 1
+    assert L.bdct_plan_create(ctypes.byref(h), 8, 8, 16, 0, 0) == 1  # not a kind bit
     assert L.bdct_plan_create(ctypes.byref(h), 8, 8, 1, 7, 0) == 1
     assert L.bdct_plan_create(ctypes.byref(h), 8, 8, 1, 0, 9) == 1
     assert L.bdct_plan_create(ctypes.byref(h), 8, 10, 1, 0, 0) == 2  # cols not a multiple of 4
@@ -59,6 +59,7 @@ def test_argument_validation_before_cuda(bdct_lib):
     assert h.value is None
     assert L.bdct_plan_destroy(None) == 0
     assert L.bdct_execute(None, 1, None, None, 1, None) == 1
+    assert L.bdct_plan_set_spectral(None, None) == 1
     info = __import__("paper_2609_28519_gb300.native", fromlist=["PlanInfo"]).PlanInfo()
     assert L.bdct_plan_get_info(None, ctypes.byref(info)) == 1
 

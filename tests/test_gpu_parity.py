@@ -548,3 +548,91 @@ def test_large_full_rank_against_oracle(oracle_mod, cuda_dev, n):
     for kind in KINDS:
         y = _run(plan, kind, x, cuda_dev)
         _assert_parity(oracle_mod, y, _ref(oracle_mod, kind, x, 0), x, 0, kind, ("large", n, kind))
+
+
+# ------------------------------------------------------------ spectral operator (Prop. 1, Eq. 4)
+def _assert_spectral(o, y, x, lam, tag):
+    """Eq. 5 read for the composition U^T Lambda U: the error relative to
+    max|Lambda| times the input, i.e. the transform bars applied to
+    U^T (Lambda / max|Lambda|) U (Lambda = 1 gives the round-trip check)."""
+    s = float(np.max(np.abs(lam)))
+    return _assert_parity(o, np.asarray(y, np.float64) / s, o.spectral(x, lam) / s, x, 0, "roundtrip", tag)
+
+
+SPECTRAL_CASES = [(h, w, "fp32") for (h, w) in FUSED_SHAPES[:9]] + [
+    (64, 64, "fp32"), (128, 128, "fp32"), (64, 128, "fp32"), (16, 16, "split_tc"), (32, 32, "split_tc"),
+    (64, 64, "split_tc"), (256, 256, "fp32"), (64, 256, "fp32"), (24, 40, "fp32")]
+
+
+@pytest.mark.parametrize("h,w,path", SPECTRAL_CASES)
+@pytest.mark.parametrize("norm", [0, 1])
+def test_spectral_against_oracle(oracle_mod, cuda_dev, h, w, path, norm):
+    """Transform -- diagonal -- inverse: fused in one pass (sides 8..32, tensor
+    cores), composed from forward, diagonal and inverse elsewhere; a seeded
+    diagonal and the Poisson diagonal, several chunks and a ragged tail.  The
+    composition is the normalized one under both plan normalizations."""
+    from paper_2609_28519_gb300 import Plan
+    plan = Plan(h, w, norm=norm, path=path)
+    batch = 37 if h * w <= 4096 else 5
+    x = inputs.uniform(7000 + h + 3 * w + norm, batch, h, w)
+    for lam in (inputs.random_diagonal(7100 + h + w, h, w, -2.0, 3.0), inputs.poisson_diagonal(h, w)):
+        plan.set_spectral(lam)
+        y = _run(plan, "spectral", x, cuda_dev)
+        _assert_spectral(oracle_mod, y, x, lam, ("spectral", h, w, path, norm))
+    # Lambda = 1 is the round trip
+    plan.set_spectral(np.ones((h, w)))
+    y = _run(plan, "spectral", x, cuda_dev)
+    _assert_parity(oracle_mod, y, x.astype(np.float64), x, 0, "roundtrip", ("spectral-identity", h, w, path))
+
+
+@pytest.mark.parametrize("path", ["fp32", "split_tc"])
+def test_spectral_image_16x16_poisson(oracle_mod, cuda_dev, path):
+    """The 2048x2048 image as 16384 16x16 blocks, each solved with the
+    Poisson diagonal (the phase-unwrapping block step, Section 1.1) through
+    the tiled view in one call; in place as well; every block against the
+    oracle."""
+    import torch
+    from paper_2609_28519_gb300 import Plan
+    img = inputs.ramp_image(2)
+    blocks = inputs.image_to_blocks(img, 16, 16)
+    lam = inputs.poisson_diagonal(16, 16)
+    plan = Plan(16, 16, path=path)
+    plan.set_spectral(lam)
+    d = torch.from_numpy(img).to(cuda_dev)
+    out = plan.execute_tiled("spectral", d)
+    torch.cuda.synchronize()
+    got = inputs.image_to_blocks(out.cpu().numpy(), 16, 16)
+    _assert_spectral(oracle_mod, got, blocks, lam, ("spectral-image", path))
+    d2 = d.clone()
+    plan.execute_tiled("spectral", d2, d2)
+    torch.cuda.synchronize()
+    assert torch.equal(d2, out)
+
+
+def test_spectral_host_buffers_and_errors(oracle_mod, cuda_dev):
+    import torch
+    from paper_2609_28519_gb300 import BdctError, Plan, native
+    # host image through the tiled host pipeline: spectral step on the device
+    img = inputs.ramp_image(3, 512, 1024)
+    plan = Plan(16, 16)
+    lam = inputs.poisson_diagonal(16, 16)
+    plan.set_spectral(lam)
+    plan.set_host_staging(1 << 19)
+    h_in = torch.from_numpy(img).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    plan.execute_tiled_host(["spectral"], h_in, h_out)
+    torch.cuda.synchronize()
+    blocks = inputs.image_to_blocks(img, 16, 16)
+    _assert_spectral(oracle_mod, inputs.image_to_blocks(h_out.numpy(), 16, 16), blocks, lam, "spectral-host")
+    # a plan without the spectral direction, and a diagonal never set
+    x = torch.zeros(2, 16, 16, device=cuda_dev)
+    p_f = Plan(16, 16, kind=native.FORWARD)
+    with pytest.raises(BdctError) as e:
+        p_f.set_spectral(lam)
+    assert e.value.code == "ERR_KIND"
+    with pytest.raises(BdctError) as e:
+        p_f.spectral(x)
+    assert e.value.code == "ERR_KIND"
+    with pytest.raises(BdctError) as e:
+        Plan(16, 16).spectral(x)
+    assert e.value.code == "ERR_INVALID_ARG"
