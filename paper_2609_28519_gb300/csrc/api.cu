@@ -68,12 +68,71 @@ static void plan_free(bdct_plan *p)
     if (p->ops) cudaFree(p->ops);
     if (p->status) cudaFree(p->status);
     if (p->tc_ops) cudaFree(p->tc_ops);
+    if (p->tg_ops) cudaFree(p->tg_ops);
     if (p->line_tw) cudaFree(p->line_tw);
     if (p->spec_plain) cudaFree(p->spec_plain);
     if (p->spec_fold) cudaFree(p->spec_fold);
     host_staging_free(p);
     if (p->work) cudaFree(p->work);
     delete p;
+}
+
+// Shapes of the tensor-core separable passes: both sides 16, 32 or a multiple
+// of 64 (up to 8192), or 8 x 8 through the Kronecker operator.
+static bool tg_supported(int rows, int cols)
+{
+    return (rows == 8 && cols == 8) || (tg_axis_ok(rows) && tg_axis_ok(cols));
+}
+
+// Build the blocked operator tables of a variant-4 plan: one per distinct
+// (side, direction, normalization) among the slots the plan's kinds need.
+static int tg_plan_tables(bdct_plan *p)
+{
+    struct Want { int slot, axis, n, direction, norm; };
+    Want want[8];
+    int nw = 0;
+    const unsigned k = p->kind;
+    const bool pair = (k & (BDCT_ROUNDTRIP | BDCT_SPECTRAL)) != 0;
+    auto add = [&](int slot, int direction, int norm) {
+        if (p->tg_kron) {
+            want[nw++] = Want{slot, 0, 8, direction, norm};
+        } else {
+            want[nw++] = Want{slot, 0, p->rows, direction, norm};
+            want[nw++] = Want{slot, 1, p->cols, direction, norm};
+        }
+    };
+    if (k & BDCT_FORWARD) add(0, 1, p->norm);
+    if (k & BDCT_INVERSE) add(1, 2, p->norm);
+    if (pair) { add(2, 1, BDCT_NORM_ORTHO); add(3, 2, BDCT_NORM_ORTHO); }
+    // distinct tables, each 3 n^2 BF16 elements (64 x 64 for the Kronecker operator)
+    int uniq[8][3];
+    size_t uoff[8];
+    int nu = 0;
+    size_t total = 0;
+    size_t off_of[8];
+    for (int i = 0; i < nw; ++i) {
+        int j = 0;
+        for (; j < nu; ++j)
+            if (uniq[j][0] == want[i].n && uniq[j][1] == want[i].direction && uniq[j][2] == want[i].norm) break;
+        if (j == nu) {
+            uniq[nu][0] = want[i].n; uniq[nu][1] = want[i].direction; uniq[nu][2] = want[i].norm;
+            uoff[nu] = total;
+            total += tg_table_elems(p->tg_kron ? 64 : want[i].n);
+            ++nu;
+        }
+        off_of[i] = uoff[j];
+    }
+    cudaError_t e = cudaMalloc(&p->tg_ops, total * sizeof(__nv_bfloat16));
+    if (e != cudaSuccess) { t_last_cuda_error = (int)e; return BDCT_ERR_NO_MEMORY; }
+    p->table_bytes = total * sizeof(__nv_bfloat16);
+    for (int j = 0; j < nu && e == cudaSuccess; ++j)
+        e = tg_gen_table(p->tg_ops + uoff[j], uniq[j][0], uniq[j][1], uniq[j][2], p->tg_kron, 0);
+    if (e != cudaSuccess) return cuda_fail(e);
+    for (int i = 0; i < nw; ++i) {
+        if (want[i].axis == 0) p->tg_h[want[i].slot] = off_of[i];
+        else p->tg_w[want[i].slot] = off_of[i];
+    }
+    return BDCT_OK;
 }
 
 extern "C" int bdct_plan_create(bdct_plan **plan, int rows, int cols, unsigned kind, int norm, int path)
@@ -99,8 +158,11 @@ extern "C" int bdct_plan_create(bdct_plan **plan, int rows, int cols, unsigned k
         else if (tc_supported(rows, cols)) resolved = BDCT_PATH_SPLIT_TC;
         else resolved = BDCT_PATH_FP32;
     }
-    const bool tc = resolved == BDCT_PATH_SPLIT_TC || resolved == BDCT_PATH_SPLIT_HILO || resolved == BDCT_PATH_BF16;
-    if (tc && !tc_supported(rows, cols)) return BDCT_ERR_UNSUPPORTED_SHAPE;
+    const bool tc_path = resolved == BDCT_PATH_SPLIT_TC || resolved == BDCT_PATH_SPLIT_HILO || resolved == BDCT_PATH_BF16;
+    // tensor cores: on chip for squares 16..64, separable passes for the rest
+    const bool tc = tc_path && tc_supported(rows, cols);
+    const bool tg = tc_path && !tc && tg_supported(rows, cols);
+    if (tc_path && !tc && !tg) return BDCT_ERR_UNSUPPORTED_SHAPE;
 
     bdct_plan *p = new (std::nothrow) bdct_plan;
     if (!p) return BDCT_ERR_NO_MEMORY;
@@ -151,6 +213,20 @@ extern "C" int bdct_plan_create(bdct_plan **plan, int rows, int cols, unsigned k
             off += 2 * te;
         }
         if (e != cudaSuccess) { plan_free(p); return cuda_fail(e); }
+    } else if (tg) {
+        p->variant = 4;
+        p->tc_terms = resolved == BDCT_PATH_SPLIT_TC ? 3 : (resolved == BDCT_PATH_SPLIT_HILO ? 2 : 1);
+        p->tg_kron = rows == 8 && cols == 8;
+        st = tg_plan_tables(p);
+        if (st != BDCT_OK) { plan_free(p); return st; }
+        // workspace: whole arrays, about kChunkBytes per chunk
+        const size_t arr_bytes = (size_t)rows * cols * sizeof(float);
+        long long chunk = (long long)(kChunkBytes / arr_bytes);
+        if (chunk < 1) chunk = 1;
+        p->chunk_arrays = chunk;
+        p->work_bytes = (size_t)chunk * arr_bytes;
+        e = cudaMalloc(&p->work, p->work_bytes);
+        if (e != cudaSuccess) { plan_free(p); t_last_cuda_error = (int)e; return BDCT_ERR_NO_MEMORY; }
     } else if (fused_supported(rows, cols)) {
         p->variant = 1;
     } else if (lines_supported(rows) && lines_supported(cols)) {
@@ -358,6 +434,65 @@ static int run_onchip(const bdct_plan *p, Dir dir, const ExecGeom &g0, cudaStrea
     return e == cudaSuccess ? BDCT_OK : cuda_fail(e);
 }
 
+// Tensor-core separable passes (variant 4).  One direction of one slot over a
+// chunk: rows of the input into the workspace (transposed), then the rows of
+// that into the output (transposed back); lam (spectral) multiplies the
+// spectrum in the second pass's epilogue.  The 8 x 8 Kronecker route is one
+// pass per direction.
+static cudaError_t tg_direction(const bdct_plan *p, int slot, const float *src, const long long *src_off, float *dst,
+                                const long long *dst_off, long long nb, const float *lam, cudaStream_t s)
+{
+    const int h = p->rows, w = p->cols;
+    if (p->tg_kron)
+        return tg_pass(src, dst, src_off, dst_off, nb, 1, 64, p->tg_ops + p->tg_h[slot], p->tc_terms, lam, p->status, s);
+    cudaError_t e = tg_pass(src, p->work, src_off, nullptr, nb, h, w, p->tg_ops + p->tg_w[slot], p->tc_terms, nullptr,
+                            p->status, s);
+    if (e == cudaSuccess)
+        e = tg_pass(p->work, dst, nullptr, dst_off, nb, w, h, p->tg_ops + p->tg_h[slot], p->tc_terms, lam, p->status, s);
+    return e;
+}
+
+static int run_tg(const bdct_plan *p, Dir dir, const float *in, const long long *in_off, float *out,
+                  const long long *out_off, long long count, cudaStream_t s)
+{
+    const long long hw = (long long)p->rows * p->cols;
+    const bool inplace = (const void *)in == (const void *)out;
+    for (long long b0 = 0; b0 < count; b0 += p->chunk_arrays) {
+        const long long nb = (count - b0) < p->chunk_arrays ? (count - b0) : p->chunk_arrays;
+        const float *src = in_off ? in : in + b0 * hw;
+        float *dst = out_off ? out : out + b0 * hw;
+        const long long *so = in_off ? in_off + b0 : nullptr;
+        const long long *dof = out_off ? out_off + b0 : nullptr;
+        cudaError_t e = cudaSuccess;
+        if (dir == DIR_FWD || dir == DIR_INV) {
+            const int slot = dir == DIR_FWD ? 0 : 1;
+            if (p->tg_kron && inplace) {
+                // one pass cannot run in place: through the workspace
+                e = tg_pass(src, p->work, so, nullptr, nb, 1, 64, p->tg_ops + p->tg_h[slot], p->tc_terms, nullptr,
+                            p->status, s);
+                ExecGeom g{p->work, dst, nb, 0, 0, 0, 0, nullptr, dof};
+                if (e == cudaSuccess) e = copy_arrays(p->work, g, p->rows, p->cols, s);
+            } else {
+                e = tg_direction(p, slot, src, so, dst, dof, nb, nullptr, s);
+            }
+        } else {
+            // round trip / spectral: orthonormal forward (times Lambda), then the inverse
+            const float *lam = dir == DIR_SPEC ? p->spec_plain : nullptr;
+            if (p->tg_kron) {
+                e = tg_pass(src, p->work, so, nullptr, nb, 1, 64, p->tg_ops + p->tg_h[2], p->tc_terms, lam, p->status, s);
+                if (e == cudaSuccess)
+                    e = tg_pass(p->work, dst, nullptr, dof, nb, 1, 64, p->tg_ops + p->tg_h[3], p->tc_terms, nullptr,
+                                p->status, s);
+            } else {
+                e = tg_direction(p, 2, src, so, dst, dof, nb, lam, s);
+                if (e == cudaSuccess) e = tg_direction(p, 3, dst, dof, dst, dof, nb, nullptr, s);
+            }
+        }
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return BDCT_OK;
+}
+
 int bdct::plan_execute(const bdct_plan *p, Dir dir, const float *in, const long long *in_off, float *out,
                        const long long *out_off, long long count, cudaStream_t s)
 {
@@ -367,6 +502,7 @@ int bdct::plan_execute(const bdct_plan *p, Dir dir, const float *in, const long 
         ExecGeom g{in, out, count, 0, 0, 0, 0, in_off, out_off};
         return run_onchip(p, dir, g, s);
     }
+    if (p->variant == 4) return run_tg(p, dir, in, in_off, out, out_off, count, s);
     if (p->lines) {
         if (dir != DIR_SPEC) return run_lines(p, dir, p->scales[dir], in, in_off, out, out_off, count, s);
         int st = run_lines(p, DIR_FWD, ortho_scales(p, DIR_FWD), in, in_off, out, out_off, count, s);

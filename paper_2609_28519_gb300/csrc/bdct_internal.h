@@ -159,6 +159,28 @@ cudaError_t spectral_gen_tables(const double *lam, float *plain, float *fold, in
 // indexed through out_off, or tiles of an image) by lam elementwise, in place.
 cudaError_t spectral_scale(const ExecGeom &g, int h, int w, const float *lam, cudaStream_t s);
 
+// Copy `count` contiguous h x w arrays from src into the call's OUTPUT
+// geometry g (contiguous or indexed through out_off).
+cudaError_t copy_arrays(const float *src, const ExecGeom &g, int h, int w, cudaStream_t s);
+
+// ---- tc_gemm.cu
+// Split-BF16 tensor-core separable passes: any side 16, 32 or a multiple of
+// 64 up to 8192 per axis, and 8 x 8 arrays as one 64 x 64 Kronecker product.
+bool tg_axis_ok(int n);
+// BF16 elements of one blocked operator table of side n (64 for Kronecker).
+size_t tg_table_elems(int n);
+// Split the FP64 operator of (direction 1 fwd / 2 inv, norm) of side n (or
+// the 8 x 8 Kronecker operator) into three BF16 terms, blocked for tg_pass.
+cudaError_t tg_gen_table(__nv_bfloat16 *dst, int n, int direction, int norm, bool kron, cudaStream_t s);
+// One pass over `count` arrays of R rows of length K: every row gets the 1D
+// operator (K x K) and the result is written transposed, dst[b][n][r]
+// (arrays of K x R; R = 1 writes dst[b][n]).  src_off / dst_off index the
+// arrays (element offsets) or are null for contiguous arrays; lam, if not
+// null, multiplies output (n, r) by lam[n * R + r].  src != dst.
+cudaError_t tg_pass(const float *src, float *dst, const long long *src_off, const long long *dst_off, long long count,
+                    int R, int K, const __nv_bfloat16 *ops, int terms, const float *lam, unsigned int *status,
+                    cudaStream_t stream);
+
 // ---- dense_passes.cu
 // Separable dense passes through a workspace, any shape.  `op_h`, `op_w` are
 // the h x h and w x w FP32 operator matrices of one direction (scales folded

@@ -14,7 +14,7 @@ struct bdct_plan {
     unsigned kind = 0;
     int norm = 0;
     int path = 0;
-    int variant = 0;  // 1 fused register tile, 2 separable passes, 3 tensor core
+    int variant = 0;  // 1 fused register tile, 2 separable passes, 3 tensor core, 4 tensor-core passes
     bool lines = false;  // separable passes through the FFT line engine (else dense GEMM passes)
     float2 *line_tw = nullptr;        // line engine twiddles: w axis at 0, h axis at line_tw_h
     size_t line_tw_h = 0;
@@ -32,6 +32,12 @@ struct bdct_plan {
     __nv_bfloat16 *tc_ops = nullptr;
     size_t tc_off[3] = {0, 0, 0};
     int tc_terms = 3;
+    // tensor-core separable passes (variant 4): blocked operator tables, per
+    // slot (0 forward, 1 inverse in the plan's norm; 2 forward, 3 inverse
+    // orthonormal, for the round trip and the spectral direction) and axis
+    __nv_bfloat16 *tg_ops = nullptr;
+    size_t tg_h[4] = {0, 0, 0, 0}, tg_w[4] = {0, 0, 0, 0};
+    bool tg_kron = false;  // 8 x 8: one pass with the 64 x 64 Kronecker operator
     // spectral direction (bdct_plan_set_spectral): Lambda in FP32, and Lambda
     // folded with the squared scales for the unscaled fused cores (Prop. 1)
     float *spec_plain = nullptr, *spec_fold = nullptr;

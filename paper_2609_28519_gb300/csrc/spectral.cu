@@ -76,4 +76,33 @@ cudaError_t spectral_scale(const ExecGeom &g, int h, int w, const float *lam, cu
     return cudaGetLastError();
 }
 
+__global__ void k_copy_arrays(const float *src, float *out, const long long *out_off, long long count, int hw)
+{
+    const int q = hw / 4;
+    const long long total = count * q;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long a = i / q;
+        const int c4 = (int)(i - a * q);
+        const float4 v = reinterpret_cast<const float4 *>(src + a * hw)[c4];
+        reinterpret_cast<float4 *>(out_off ? out + out_off[a] : out + a * hw)[c4] = v;
+    }
+}
+
+cudaError_t copy_arrays(const float *src, const ExecGeom &g, int h, int w, cudaStream_t s)
+{
+    if (g.count <= 0) return cudaSuccess;
+    const int hw = h * w;
+    if (hw % 4) return cudaErrorInvalidValue;
+    if (!g.out_off) return cudaMemcpyAsync(g.out, src, (size_t)g.count * hw * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    long long blocks = (g.count * (hw / 4) + 255) / 256;
+    if (blocks > (long long)sms * 8) blocks = (long long)sms * 8;
+    k_copy_arrays<<<(unsigned)blocks, 256, 0, s>>>(src, g.out, g.out_off, g.count, hw);
+    return cudaGetLastError();
+}
+
 }  // namespace bdct

@@ -1,0 +1,449 @@
+// Split-BF16 tensor-core separable passes (tcgen05, FP32 accumulation in TMEM)
+// for the shapes the on-chip tensor-core kernel (tc_split.cu, squares 16..64)
+// does not hold: squares 128 and up, rectangles, whole large arrays, and the
+// 8 x 8 blocks as one Kronecker product.
+//
+// What is computed: Eq. 2 of the BRiDCT paper, Y = M_h X M_w^T, as two
+// passes of one contraction each.  A pass takes every row of every array
+// (R rows of length K per array), applies the 1D operator M (N x K, the
+// direction's matrix of Eq. 1 or of the REDFT pair) to it and writes the
+// result transposed, out[b][n][r] = sum_k M[n][k] X[b][r][k]; two passes
+// (rows, then the rows of the transposed intermediate) give the 2D transform
+// in natural layout.  For 8 x 8 arrays one pass with the 64 x 64 Kronecker
+// operator Q (x) Q over the vectorized array (R = 1) gives it directly.
+// Direct matrix evaluation costs K multiply-adds per point (Section 1.2); the
+// tensor cores take them.
+//
+// Exactness (Section 1.1 excludes approximated matrices): each FP32 input is
+// split in the kernel into three BF16 terms x = x0 + x1 + x2 (each the
+// round-to-nearest BF16 of the remaining residual), the FP64 operator into
+// three terms once at plan time, and the six products with term orders
+// summing to at most 2 are accumulated in FP32.  The five small products go
+// to one TMEM accumulator and the main product x0 * m0 to a second one, added
+// in registers at the end: measured in emulation this keeps the FP32
+// accumulation error of a 4096-point contraction at the level of summing the
+// small products first (3e-7 per pass), where interleaving the products chunk
+// by chunk would double it.
+//
+// Organization: a tile is 128 rows (the MMA's M) by NT outputs (its N); K
+// runs in chunks of KC <= 64 through two shared-memory stages.  All 128
+// threads stage A -- thread t loads row t of the chunk (prefetched into
+// registers one chunk ahead), splits it and writes the terms in the
+// canonical K-major layout -- while thread 0 brings the operator's terms for
+// the chunk with one bulk copy and, once both are in, issues the products
+// and commits them to the stage's mbarrier.  The next chunk is staged while
+// those products run.  Epilogue: thread t reads its TMEM lane (row t of the
+// tile), adds the two accumulators and stores its outputs transposed (lanes
+// of a warp hold consecutive rows, so each output index is one coalesced
+// segment).  Persistent CTAs walk the (row tile, output tile) items.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdio>
+
+#include "bdct_internal.h"
+#include "ptx.cuh"
+#include "tc_ptx.cuh"
+
+namespace bdct {
+
+constexpr int kTgM = 128;     // rows per tile
+constexpr int kTgKC = 64;     // largest K chunk
+constexpr int kTgStages = 2;
+
+template <int NT>
+struct TgCfg {
+    static constexpr int A_TERM = kTgM * kTgKC * 2;  // bytes of one BF16 term of the A chunk
+    static constexpr int B_TERM = NT * kTgKC * 2;    // bytes of one BF16 term of the operator chunk
+    static constexpr int STAGE = 3 * A_TERM + 3 * B_TERM;
+    static constexpr size_t SMEM = (size_t)kTgStages * STAGE + 4 * 8 + 16;
+    static constexpr int TMEM_COLS = 2 * NT < 32 ? 32 : 2 * NT;  // small-product and main-product accumulators
+};
+
+struct TgParams {
+    const float *src;
+    float *dst;
+    const long long *src_off, *dst_off;  // indexed arrays (element offsets), or null
+    long long rows_total;                // arrays * R
+    int R;                               // rows per array (1: the output is not transposed)
+    int K, N;                            // contraction length (row length), output length
+    int KC, nk;                          // K per chunk, chunks
+    int n_tiles;                         // N / NT
+    long long items;                     // row tiles * n_tiles
+    const __nv_bfloat16 *ops;            // operator terms, [n tile][k chunk][term][NT x KC K-major]
+    const float *lam;                    // optional: output (n, r) of an array times lam[n * R + r]
+    unsigned int *status;
+};
+
+template <int NT, int TERMS>
+__global__ void __launch_bounds__(128) k_tcg(const TgParams p)
+{
+    using C = TgCfg<NT>;
+    extern __shared__ __align__(1024) uint8_t tgs[];
+    uint64_t *bfull = reinterpret_cast<uint64_t *>(tgs + kTgStages * C::STAGE);  // operator chunk landed
+    uint64_t *mdone = bfull + kTgStages;                                          // products of a stage done
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mdone + kTgStages);
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (tid == 0) {
+        for (int s = 0; s < kTgStages; ++s) {
+            mbar_init(&bfull[s], 1);
+            mbar_init(&mdone[s], 1);
+        }
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(C::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    pdl_launch_dependents();
+    pdl_wait_prerequisites();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t acc_small = tmem, acc_big = tmem + NT;
+    const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+    const int KC = p.KC;
+    const uint32_t sbo = (uint32_t)(KC / 8) * 128u;  // M/N-adjacent core matrices
+    constexpr uint32_t idesc = tc_idesc(NT, false);
+    const uint32_t b_term = (uint32_t)NT * KC * 2;  // bytes of one operator term of a chunk
+    const uint32_t b_bytes = (uint32_t)TERMS * b_term;
+    const long long b_chunk_elems = 3LL * NT * KC;
+
+    // source row of this thread for a row tile (null beyond the last row)
+    auto row_ptr = [&](long long item) -> const float * {
+        const long long m = (item / p.n_tiles) * kTgM + tid;
+        if (m >= p.rows_total) return nullptr;
+        const long long b = m / p.R;
+        const long long r = m - b * p.R;
+        return p.src + (p.src_off ? p.src_off[b] : b * (long long)p.R * p.K) + r * p.K;
+    };
+    float v[kTgKC];
+    auto load_chunk = [&](const float *row, int kc) {
+        if (row) {
+            const float4 *q = reinterpret_cast<const float4 *>(row + (long long)kc * KC);
+#pragma unroll
+            for (int i = 0; i < kTgKC / 4; ++i)
+                if (4 * i < KC) {
+                    const float4 t = __ldg(q + i);
+                    v[4 * i] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
+                }
+        } else {
+#pragma unroll
+            for (int i = 0; i < kTgKC; ++i) v[i] = 0.0f;
+        }
+    };
+
+    bool ok = true;
+    uint32_t g = 0;                  // chunks this CTA has started
+    long long last_b = -1, last_c = -1;  // thread 0: last operator copy and last commit issued
+    long long item = blockIdx.x;
+    if (item < p.items) load_chunk(row_ptr(item), 0);
+    for (; ok && item < p.items; item += gridDim.x) {
+        const int nt = (int)(item % p.n_tiles);
+        const float *row = row_ptr(item);
+        for (int kc = 0; kc < p.nk; ++kc, ++g) {
+            const int s = (int)(g & 1u);
+            const uint32_t use = g >> 1;
+            uint8_t *st = tgs + s * C::STAGE;
+            // the stage is free once the products of chunk g - 2 are done
+            if (g >= 2 && !mbar_wait_bounded(&mdone[s], (use - 1) & 1u)) ok = false;
+            if (tid == 0 && ok) {
+                mbar_arrive_expect_tx(&bfull[s], b_bytes);
+                bulk_load(st + 3 * C::A_TERM, p.ops + ((long long)nt * p.nk + kc) * b_chunk_elems, b_bytes, &bfull[s]);
+                last_b = g;
+            }
+            if (ok) {
+                // split this thread's row of the chunk into BF16 terms (K-major row tid)
+#pragma unroll
+                for (int q = 0; q < kTgKC / 8; ++q) {
+                    if (8 * q < KC) {
+                        __nv_bfloat16 t[TERMS][8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            __nv_bfloat16 sp[3];
+                            split3<TERMS>(v[8 * q + e], sp);
+#pragma unroll
+                            for (int tt = 0; tt < TERMS; ++tt) t[tt][e] = sp[tt];
+                        }
+                        const int off = kmaj_off_bytes(tid, 8 * q, KC);
+#pragma unroll
+                        for (int tt = 0; tt < TERMS; ++tt)
+                            *reinterpret_cast<uint4 *>(st + tt * C::A_TERM + off) = *reinterpret_cast<const uint4 *>(t[tt]);
+                    }
+                }
+            }
+            fence_proxy_async_smem();
+            tc_fence_before();
+            ok = __syncthreads_and(ok);
+            tc_fence_after();
+            if (!ok) break;
+            // prefetch the next chunk's row segment (the next item's first one
+            // after the last chunk) while the products run
+            {
+                const bool more = kc + 1 < p.nk;
+                const long long ni = item + gridDim.x;
+                if (more) load_chunk(row, kc + 1);
+                else if (ni < p.items) load_chunk(row_ptr(ni), 0);
+            }
+            if (tid == 0) {
+                if (!mbar_wait_bounded(&bfull[s], use & 1u)) {
+                    record_timeout(p.status);  // the others learn of it at their next wait
+                } else {
+                    const uint32_t a0 = smem_u32(st), b0 = smem_u32(st + 3 * C::A_TERM);
+                    // small products (term orders summing to 1 or 2), smallest first
+                    constexpr int pa[5] = {2, 1, 0, 1, 0};
+                    constexpr int pb[5] = {0, 1, 2, 0, 1};
+                    constexpr int first = TERMS == 3 ? 0 : (TERMS == 2 ? 3 : 5);
+#pragma unroll
+                    for (int pr = first; pr < 5; ++pr)
+                        for (int ks = 0; ks < KC / 16; ++ks)
+                            tc_mma(acc_small, smem_desc(a0 + pa[pr] * C::A_TERM + ks * 256, 128, sbo),
+                                   smem_desc(b0 + pb[pr] * b_term + ks * 256, 128, sbo), idesc,
+                                   (kc > 0 || pr > first || ks > 0) ? 1u : 0u);
+                    for (int ks = 0; ks < KC / 16; ++ks)
+                        tc_mma(acc_big, smem_desc(a0 + ks * 256, 128, sbo), smem_desc(b0 + ks * 256, 128, sbo), idesc,
+                               (kc > 0 || ks > 0) ? 1u : 0u);
+                    tc_commit(&mdone[s]);
+                    last_c = g;
+                }
+            }
+        }
+        if (!ok) break;
+        // ---- epilogue: this thread's TMEM lane = row tid of the tile
+        const uint32_t gl = g - 1;
+        if (!mbar_wait_bounded(&mdone[gl & 1u], (gl >> 1) & 1u)) ok = false;
+        ok = __syncthreads_and(ok);
+        if (!ok) break;
+        tc_fence_after();
+        const long long m = (item / p.n_tiles) * kTgM + tid;
+        const bool row_ok = m < p.rows_total;
+        long long b = 0, r = 0;
+        float *dbase = nullptr;
+        if (row_ok) {
+            b = m / p.R;
+            r = m - b * p.R;
+            dbase = p.dst + (p.dst_off ? p.dst_off[b] : b * (long long)p.N * p.R);
+        }
+#pragma unroll 1
+        for (int c = 0; c < NT / 16; ++c) {
+            float y[16];
+            tmem_ld16(acc_big + lane_off + 16 * c, y);
+            if constexpr (TERMS > 1) {
+                float ys[16];
+                tmem_ld16(acc_small + lane_off + 16 * c, ys);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) y[j] = ys[j] + y[j];
+            }
+            if (row_ok) {
+                const int n0 = nt * NT + 16 * c;
+                if (p.lam) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) y[j] *= __ldg(p.lam + (long long)(n0 + j) * p.R + r);
+                }
+                if (p.R == 1) {
+                    float4 *d4 = reinterpret_cast<float4 *>(dbase + n0);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) d4[j] = make_float4(y[4 * j], y[4 * j + 1], y[4 * j + 2], y[4 * j + 3]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) dbase[(long long)(n0 + j) * p.R + r] = y[j];
+                }
+            }
+        }
+        // every lane has read its accumulators before the next item's products overwrite them
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+    }
+    if (!ok && tid == 0) {
+        record_timeout(p.status);
+        // error path: the last operator copy and the last committed products of
+        // this CTA finish (each wait bounded) before its shared memory and TMEM
+        // are released
+        if (last_b >= 0) mbar_wait_bounded(&bfull[last_b & 1], (uint32_t)((last_b >> 1) & 1));
+        if (last_c >= 0) mbar_wait_bounded(&mdone[last_c & 1], (uint32_t)((last_c >> 1) & 1));
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS) : "memory");
+}
+
+// ------------------------------------------------------------ operator tables
+// Operator M (N = K = n, or the 64 x 64 Kronecker operator of 8 x 8 arrays)
+// for direction 1 (forward: M[f][j] = s_f cos(pi (2j+1) f / 2n)) or 2
+// (inverse: M[j][f] = s_f cos(...)), s the scale of Eq. 1 (orthonormal) or of
+// the REDFT pair; split in FP64 into three BF16 terms and written blocked for
+// the kernel: block (n tile, k chunk) holds the three terms of its NT x KC
+// piece, each in the canonical K-major layout.
+__device__ double tg_op_value(int row, int col, int n, int direction, int norm)
+{
+    const int f = direction == 1 ? row : col;  // frequency index
+    const int j = direction == 1 ? col : row;  // sample index
+    double s;
+    if (norm == 0) s = (f == 0) ? sqrt(1.0 / n) : sqrt(2.0 / n);
+    else if (direction == 1) s = 2.0;
+    else s = (f == 0) ? 1.0 : 2.0;
+    // cos(pi m / (2n)) with the argument reduced exactly
+    const long long m = (2LL * j + 1) * f;
+    const long long d = 2LL * n;
+    long long red = m % (2 * d);
+    if (red > d) red = 2 * d - red;
+    double sign = 1.0;
+    if (2 * red > d) { red = d - red; sign = -1.0; }
+    double c;
+    if (red == 0) c = sign;
+    else if (2 * red == d) c = 0.0;
+    else c = sign * cospi((double)red / (double)d);
+    return s * c;
+}
+
+__global__ void k_gen_tg_op(__nv_bfloat16 *dst, int N, int K, int direction, int norm, int NT, int KC, int kron)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)N * K) return;
+    const int nn = (int)(idx / K), kk = (int)(idx % K);
+    double val;
+    if (kron) {
+        // (Q (x) Q)[(f1, f2)][(i, j)] = M8[f1][i] * M8[f2][j] for the row-major 8 x 8 array
+        val = tg_op_value(nn >> 3, kk >> 3, 8, direction, norm) * tg_op_value(nn & 7, kk & 7, 8, direction, norm);
+    } else {
+        val = tg_op_value(nn, kk, N, direction, norm);
+    }
+    const __nv_bfloat16 t0 = __double2bfloat16(val);
+    const double r1 = val - (double)__bfloat162float(t0);
+    const __nv_bfloat16 t1 = __double2bfloat16(r1);
+    const double r2 = r1 - (double)__bfloat162float(t1);
+    const __nv_bfloat16 t2 = __double2bfloat16(r2);
+    const long long blk = (long long)(nn / NT) * (K / KC) + kk / KC;
+    const long long base = blk * 3LL * NT * KC + kmaj_off_bytes(nn % NT, kk % KC, KC) / 2;
+    dst[base] = t0;
+    dst[base + (long long)NT * KC] = t1;
+    dst[base + 2LL * NT * KC] = t2;
+}
+
+// Tile width for an output length: the largest of 128, 64, 32, 16 dividing it.
+static int tg_nt(int n)
+{
+    for (int nt : {128, 64, 32, 16})
+        if (n % nt == 0) return nt;
+    return 0;
+}
+
+// K chunk for a contraction length: 64 for multiples of 64, else the length
+// itself (16 or 32).
+static int tg_kc(int k) { return k % 64 == 0 ? 64 : ((k == 16 || k == 32) ? k : 0); }
+
+bool tg_axis_ok(int n) { return n == 16 || n == 32 || (n % 64 == 0 && n >= 64 && n <= 8192); }
+
+size_t tg_table_elems(int n) { return (size_t)3 * n * n; }
+
+cudaError_t tg_gen_table(__nv_bfloat16 *dst, int n, int direction, int norm, bool kron, cudaStream_t s)
+{
+    const int N = kron ? 64 : n;
+    const int NT = tg_nt(N), KC = tg_kc(N);
+    if (!NT || !KC) return cudaErrorInvalidValue;
+    const long long total = (long long)N * N;
+    k_gen_tg_op<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(dst, N, N, direction, norm, NT, KC, kron ? 1 : 0);
+    return cudaGetLastError();
+}
+
+template <int NT, int TERMS>
+static cudaError_t tg_launch_one(const TgParams &p0, cudaStream_t stream)
+{
+    using C = TgCfg<NT>;
+    auto kern = k_tcg<NT, TERMS>;
+    static DeviceLaunchCache cache;
+    int dev = 0, blocks_per_sm = 0, num_sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cache.get(
+        dev,
+        [&](int d, int &bps, int &sms) {
+            cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+            if (r != cudaSuccess) return r;
+            // resident CTAs from shared memory, capped by TMEM (512 columns per
+            // SM) and threads; the runtime's occupancy query does not see TMEM
+            int smem_per_sm = 0, reserved = 0;
+            cudaDeviceGetAttribute(&smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, d);
+            cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, d);
+            int occ = (int)((size_t)smem_per_sm / (C::SMEM + (size_t)reserved));
+            const int tmem_cap = 512 / C::TMEM_COLS;
+            if (occ > tmem_cap) occ = tmem_cap;
+            if (occ > 16) occ = 16;
+            bps = occ;
+            r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
+            if (r != cudaSuccess) return r;
+            if (bps < 1) return cudaErrorInvalidConfiguration;
+            if (debug_enabled())
+                fprintf(stderr, "[bdct] k_tcg<%d,%d>: %d CTAs/SM, smem %zu B, TMEM %d cols\n", NT, TERMS, bps,
+                        C::SMEM, C::TMEM_COLS);
+            return cudaSuccess;
+        },
+        &blocks_per_sm, &num_sms);
+    if (e != cudaSuccess) return e;
+    TgParams p = p0;
+    long long grid = (long long)blocks_per_sm * num_sms;
+    if (grid > p.items) grid = p.items;
+    if (grid <= 0) return cudaSuccess;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(128);
+    cfg.dynamicSmemBytes = C::SMEM;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, p);
+}
+
+template <int NT>
+static cudaError_t tg_launch_nt(int terms, const TgParams &p, cudaStream_t s)
+{
+    switch (terms) {
+        case 3: return tg_launch_one<NT, 3>(p, s);
+        case 2: return tg_launch_one<NT, 2>(p, s);
+        default: return tg_launch_one<NT, 1>(p, s);
+    }
+}
+
+cudaError_t tg_pass(const float *src, float *dst, const long long *src_off, const long long *dst_off, long long count,
+                    int R, int K, const __nv_bfloat16 *ops, int terms, const float *lam, unsigned int *status,
+                    cudaStream_t stream)
+{
+    if (count <= 0) return cudaSuccess;
+    const int N = K;  // square 1D operators (the Kronecker one included)
+    const int NT = tg_nt(N), KC = tg_kc(K);
+    if (!NT || !KC || R < 1) return cudaErrorInvalidValue;
+    if (src == dst) return cudaErrorInvalidValue;  // a pass never runs in place
+    TgParams p{};
+    p.src = src;
+    p.dst = dst;
+    p.src_off = src_off;
+    p.dst_off = dst_off;
+    p.rows_total = count * R;
+    p.R = R;
+    p.K = K;
+    p.N = N;
+    p.KC = KC;
+    p.nk = K / KC;
+    p.n_tiles = N / NT;
+    p.items = ((p.rows_total + kTgM - 1) / kTgM) * p.n_tiles;
+    p.ops = ops;
+    p.lam = lam;
+    p.status = status;
+    switch (NT) {
+        case 128: return tg_launch_nt<128>(terms, p, stream);
+        case 64: return tg_launch_nt<64>(terms, p, stream);
+        case 32: return tg_launch_nt<32>(terms, p, stream);
+        default: return tg_launch_nt<16>(terms, p, stream);
+    }
+}
+
+}  // namespace bdct

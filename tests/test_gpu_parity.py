@@ -636,3 +636,78 @@ def test_spectral_host_buffers_and_errors(oracle_mod, cuda_dev):
     with pytest.raises(BdctError) as e:
         Plan(16, 16).spectral(x)
     assert e.value.code == "ERR_INVALID_ARG"
+
+
+# ------------------------------------------------------------ tensor-core separable passes
+TG_SHAPES = [(8, 8), (128, 128), (256, 256), (16, 64), (64, 16), (32, 128), (128, 32), (64, 256), (192, 320),
+             (128, 512)]
+
+
+@pytest.mark.parametrize("h,w", TG_SHAPES)
+@pytest.mark.parametrize("norm", [0, 1])
+def test_split_tc_passes_against_oracle(oracle_mod, cuda_dev, h, w, norm):
+    """Split-BF16 tcgen05 passes (three terms, six products, two TMEM
+    accumulators): squares beyond 64, rectangles, multiples of 64 that are
+    not powers of two, and 8 x 8 as one Kronecker product.  Forward, inverse,
+    round trip and the spectral direction against the oracle; several row
+    tiles and a ragged tail."""
+    from paper_2609_28519_gb300 import Plan
+    plan = Plan(h, w, norm=norm, path="split_tc")
+    assert plan.info().variant == 4
+    batch = 300 if h * w <= 64 else (5 if h * w <= 65536 else 2)
+    x = inputs.uniform(8000 + h + 7 * w + norm, batch, h, w)
+    for kind in KINDS:
+        y = _run(plan, kind, x, cuda_dev)
+        _assert_parity(oracle_mod, y, _ref(oracle_mod, kind, x, norm), x, norm, kind, ("tg", h, w, norm, kind))
+    lam = inputs.poisson_diagonal(h, w)
+    plan.set_spectral(lam)
+    _assert_spectral(oracle_mod, _run(plan, "spectral", x, cuda_dev), x, lam, ("tg-spectral", h, w))
+    assert plan.device_status() == 0
+
+
+@pytest.mark.parametrize("h,w,b", [(1024, 1024, 2), (4096, 4096, 1), (1024, 768, 1), (768, 1024, 1)])
+def test_split_tc_large_arrays_against_oracle(oracle_mod, cuda_dev, h, w, b):
+    """The large-array shapes (1024^2, 4096^2, 1024 x 768) on the split-BF16
+    tensor-core passes, full-rank Gaussian inputs: forward, inverse and
+    round trip against the oracle at the accepted bars."""
+    from paper_2609_28519_gb300 import Plan
+    plan = Plan(h, w, kind=1 | 2 | 4, path="split_tc")
+    assert plan.info().variant == 4
+    x = inputs.gaussian(8500 + h + w, b, h, w)
+    for kind in KINDS:
+        y = _run(plan, kind, x, cuda_dev)
+        _assert_parity(oracle_mod, y, _ref(oracle_mod, kind, x, 0), x, 0, kind, ("tg-large", h, w, kind))
+
+
+def test_split_tc_passes_inplace_report_only_and_ragged(oracle_mod, cuda_dev):
+    import torch
+    from paper_2609_28519_gb300 import Plan, Ragged
+    # exact in place, Kronecker and two-pass routes
+    for (h, w) in [(8, 8), (128, 64)]:
+        plan = Plan(h, w, path="split_tc")
+        x_np = inputs.uniform(8600 + h + w, 40, h, w)
+        x = torch.from_numpy(x_np).to(cuda_dev)
+        for kind in KINDS:
+            ref_gpu = plan.execute(kind, x)
+            y = x.clone()
+            plan.execute(kind, y, y)
+            torch.cuda.synchronize()
+            assert torch.equal(y, ref_gpu), (h, w, kind)
+    # report-only term counts sit where they should
+    x = inputs.uniform(8700, 8, 128, 128)
+    ref = oracle_mod.forward(x, 0)
+    e_hilo = oracle_mod.metrics(_run(Plan(128, 128, path="split_hilo"), "forward", x, cuda_dev), ref, x)["e_rel_max"]
+    e_bf16 = oracle_mod.metrics(_run(Plan(128, 128, path="bf16"), "forward", x, cuda_dev), ref, x)["e_rel_max"]
+    assert 1e-7 < e_hilo < 1e-4 and 1e-4 < e_bf16 < 3e-2, (e_hilo, e_bf16)
+    # a ragged batch on the tensor-core path: indexed arrays through both routes
+    shapes = [(8, 8), (16, 16), (128, 128), (64, 256), (8, 8), (128, 128), (32, 32)] * 3
+    arrs = _ragged_inputs(shapes, 8800)
+    rg = Ragged(shapes, path="split_tc")
+    xr = _pack(rg, arrs, cuda_dev)
+    for kind in ("forward", "inverse", "roundtrip"):
+        y = torch.full_like(xr, float("nan"))
+        rg.execute(kind, xr, y)
+        torch.cuda.synchronize()
+        for a, o, (r, c) in zip(arrs, _unpack(rg, y, shapes), shapes):
+            _assert_parity(oracle_mod, o[None], _ref(oracle_mod, kind, a[None], 0), a[None], 0, kind,
+                           ("tg-ragged", r, c, kind))
