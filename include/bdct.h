@@ -176,12 +176,23 @@ typedef struct bdct_plan_info {
     unsigned kind;
     int norm;
     int path;              /* resolved path (never AUTO) */
-    int variant;           /* kernel family: 1 fused register tile, 2 separable passes, 3 tensor core */
+    int variant;           /* kernel family: 1 fused register tile, 2 separable passes, 3 tensor core
+                              on chip, 4 tensor-core separable passes */
     size_t workspace_bytes;
     size_t table_bytes;
 } bdct_plan_info;
 
 int bdct_plan_get_info(const bdct_plan *plan, bdct_plan_info *info);
+
+/* The separable routes (variants 2 and 4: two passes over every array, the
+ * first one writing the transposed intermediate to the plan's workspace; the
+ * paper's two-pass structure of Eq. 2) process the batch in chunks of whole
+ * arrays.  Set the chunk to about `bytes` (at least one array): the workspace
+ * is reallocated to match.  A chunk that fits in L2 lets the second pass read
+ * the intermediate from L2 instead of HBM.  The default is 64 MiB; the ragged
+ * autotuner picks it per shape class.  No work using the plan may be queued.
+ * Other variants keep no workspace and ignore the call (BDCT_OK).          */
+int bdct_plan_set_chunk_bytes(bdct_plan *plan, size_t bytes);
 
 /* Synchronize the device and return the plan's device-side status: BDCT_OK,
  * or BDCT_ERR_DEVICE_TIMEOUT if a bounded wait inside one of the plan's
@@ -197,14 +208,18 @@ int bdct_plan_device_status(const bdct_plan *plan, int clear);
  * floats after the base pointers given at execution (offsets multiples of 4;
  * arrays must not overlap, except an array whose in and out spans coincide).
  * Arrays are grouped by shape; each group gets a plan whose path, when `path`
- * is BDCT_PATH_AUTO, is the faster of the accepted candidates (FP32, and the
- * split-BF16 tensor-core path where it exists) timed on scratch arrays at
- * creation -- or read from the file named by the environment variable
- * BDCT_TUNE_CACHE, to which new choices are appended.  Creation allocates,
- * synchronizes and runs those timing launches.
- * Execution launches one persistent kernel per shape class, reading the
- * arrays through device offset tables, from a CUDA graph captured on the first
- * call for each (kind, in_base, out_base) and replayed afterwards on `stream`.
+ * is BDCT_PATH_AUTO, is the fastest of the accepted candidates (FP32, and the
+ * on-chip split-BF16 tensor-core path where it exists; for shapes on the
+ * separable route, its workspace chunk of 16, 32 or 64 MiB) timed on scratch
+ * arrays at creation -- or read from the file named by the environment
+ * variable BDCT_TUNE_CACHE, to which new choices are appended.  Creation
+ * allocates, synchronizes and runs those timing launches.
+ * Execution launches one persistent kernel (or, on the separable routes, one
+ * pair of pass kernels per chunk) per shape class, reading the arrays through
+ * device offset tables, from a CUDA graph captured on the first call for each
+ * (kind, in_base, out_base) and replayed afterwards on `stream`; the largest
+ * class is one branch of the graph and the other classes run on parallel
+ * branches beside it.
  * The first call for new pointers should not itself run inside a stream
  * capture.  Calls on the same ragged plan must not overlap on the GPU.      */
 typedef struct bdct_ragged bdct_ragged;
@@ -215,6 +230,7 @@ typedef struct bdct_ragged_class {
     int path;                  /* chosen path */
     int variant;               /* kernel family, as in bdct_plan_info */
     double tuned_us_per_array; /* measured at creation (0 if not timed) */
+    size_t chunk_bytes;        /* separable routes: workspace chunk chosen (0: none) */
 } bdct_ragged_class;
 
 int bdct_ragged_create(bdct_ragged **ragged, size_t n, const int *rows, const int *cols,

@@ -632,6 +632,41 @@ extern "C" int bdct_plan_get_info(const bdct_plan *plan, bdct_plan_info *info)
     return BDCT_OK;
 }
 
+extern "C" int bdct_plan_set_chunk_bytes(bdct_plan *plan, size_t bytes)
+{
+    if (!plan) return BDCT_ERR_INVALID_ARG;
+    if (plan->variant != 2 && plan->variant != 4) return BDCT_OK;
+    const size_t arr_bytes = (size_t)plan->rows * plan->cols * sizeof(float);
+    long long chunk = (long long)(bytes / arr_bytes);
+    if (chunk < 1) chunk = 1;
+    // the dense route keeps two buffers when it serves the round trip or the spectral direction
+    const int nbuf = (plan->variant == 2 && !plan->lines && (plan->kind & (BDCT_ROUNDTRIP | BDCT_SPECTRAL))) ? 2 : 1;
+    const size_t need = (size_t)chunk * arr_bytes * nbuf;
+    if (need == plan->work_bytes) {
+        plan->chunk_arrays = chunk;
+        return BDCT_OK;
+    }
+    int cur = -1;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (cur != plan->device && (e = cudaSetDevice(plan->device)) != cudaSuccess) return cuda_fail(e);
+    float *w = nullptr;
+    e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMalloc(&w, need);
+    int st = BDCT_OK;
+    if (e != cudaSuccess) {
+        t_last_cuda_error = (int)e;
+        st = BDCT_ERR_NO_MEMORY;
+    } else {
+        if (plan->work) cudaFree(plan->work);
+        plan->work = w;
+        plan->work_bytes = need;
+        plan->chunk_arrays = chunk;
+    }
+    if (cur >= 0 && cur != plan->device) cudaSetDevice(cur);
+    return st;
+}
+
 extern "C" int bdct_plan_device_status(const bdct_plan *plan, int clear)
 {
     if (!plan) return BDCT_ERR_INVALID_ARG;

@@ -38,6 +38,7 @@ struct RaggedClass {
     long long elems = 0;  // total elements of the class
     bdct_plan *plan = nullptr;
     int path = 0;
+    size_t chunk_bytes = 0;  // separable routes: workspace chunk chosen (0 = none)
     double tuned_us = 0.0;  // measured time per array of the chosen path (0 = not measured)
 };
 
@@ -52,7 +53,7 @@ std::mutex g_cache_mutex;
 
 const char *tune_cache_path() { return getenv("BDCT_TUNE_CACHE"); }
 
-bool cache_lookup(int rows, int cols, unsigned kind, int norm, int *path)
+bool cache_lookup(int rows, int cols, unsigned kind, int norm, int *path, size_t *chunk_mb)
 {
     const char *fn = tune_cache_path();
     if (!fn) return false;
@@ -61,12 +62,14 @@ bool cache_lookup(int rows, int cols, unsigned kind, int norm, int *path)
     if (!f) return false;
     int r, c, n, pth;
     unsigned k;
+    size_t mb;
     double us;
     bool found = false;
-    while (fscanf(f, "%d %d %u %d %d %lf", &r, &c, &k, &n, &pth, &us) == 6) {
+    while (fscanf(f, "%d %d %u %d %d %zu %lf", &r, &c, &k, &n, &pth, &mb, &us) == 7) {
         if (r == rows && c == cols && k == kind && n == norm &&
             (pth == BDCT_PATH_FP32 || pth == BDCT_PATH_SPLIT_TC)) {
             *path = pth;  // the last entry wins
+            *chunk_mb = mb;
             found = true;
         }
     }
@@ -74,14 +77,14 @@ bool cache_lookup(int rows, int cols, unsigned kind, int norm, int *path)
     return found;
 }
 
-void cache_store(int rows, int cols, unsigned kind, int norm, int path, double us)
+void cache_store(int rows, int cols, unsigned kind, int norm, int path, size_t chunk_mb, double us)
 {
     const char *fn = tune_cache_path();
     if (!fn) return;
     std::lock_guard<std::mutex> lock(g_cache_mutex);
     FILE *f = fopen(fn, "a");
     if (!f) return;
-    fprintf(f, "%d %d %u %d %d %.4f\n", rows, cols, kind, norm, path, us);
+    fprintf(f, "%d %d %u %d %d %zu %.4f\n", rows, cols, kind, norm, path, chunk_mb, us);
     fclose(f);
 }
 
@@ -93,6 +96,11 @@ struct bdct_ragged {
     int norm = 0;
     std::vector<RaggedClass> classes;  // largest first
     cudaStream_t capture = nullptr;
+    // side streams and events of the captured graph: the largest class runs
+    // on one branch, the others on parallel branches beside it
+    static constexpr int kBranches = 4;
+    cudaStream_t side[kBranches] = {};
+    cudaEvent_t fork = nullptr, join[kBranches] = {};
     std::mutex mu;
     std::vector<GraphEntry> graphs;
 };
@@ -107,6 +115,11 @@ static void ragged_free(bdct_ragged *r)
         if (c.plan) bdct_plan_destroy(c.plan);
     }
     if (r->capture) cudaStreamDestroy(r->capture);
+    for (int i = 0; i < bdct_ragged::kBranches; ++i) {
+        if (r->side[i]) cudaStreamDestroy(r->side[i]);
+        if (r->join[i]) cudaEventDestroy(r->join[i]);
+    }
+    if (r->fork) cudaEventDestroy(r->fork);
     delete r;
 }
 
@@ -138,7 +151,11 @@ static int time_plan(bdct_plan *plan, unsigned kind_mask, float *d_in, float *d_
     return st;
 }
 
-// Pick and create the plan of one class.
+// Pick and create the plan of one class: the accepted candidate paths (FP32,
+// and the on-chip split-BF16 tensor-core route where it exists), and for a
+// separable route the workspace chunk (16, 32 or 64 MiB: small enough for
+// the intermediate to stay in L2 between the passes, or large enough to keep
+// the launches few), each timed on scratch arrays of the class's shape.
 static int class_plan(RaggedClass &c, unsigned kind, int norm, int path)
 {
     const bool tc_ok = tc_supported(c.rows, c.cols);
@@ -147,7 +164,9 @@ static int class_plan(RaggedClass &c, unsigned kind, int norm, int path)
         return bdct_plan_create(&c.plan, c.rows, c.cols, kind, norm, path);
     }
     const long long arr = (long long)c.rows * c.cols;
-    long long n = (32ll << 20) / (arr * 4);
+    const bool separable = !fused_supported(c.rows, c.cols);
+    // scratch: 32 MiB, or 256 MiB where chunk sizes are compared
+    long long n = ((separable ? 256ll : 32ll) << 20) / (arr * 4);
     if (n < 1) n = 1;
     if (n > (long long)c.in_off.size()) n = (long long)c.in_off.size();
     float *d_in = nullptr, *d_out = nullptr;
@@ -155,36 +174,56 @@ static int class_plan(RaggedClass &c, unsigned kind, int norm, int path)
     if (cudaMalloc(&d_out, (size_t)n * arr * 4) != cudaSuccess) { cudaFree(d_in); return BDCT_ERR_NO_MEMORY; }
     cudaMemset(d_in, 0, (size_t)n * arr * 4);
 
+    struct Cand { int path; size_t chunk_mb; };
+    std::vector<Cand> cands;
     int cached = 0;
-    std::vector<int> cands;
-    if (cache_lookup(c.rows, c.cols, kind, norm, &cached)) cands.push_back(cached);
-    else {
-        cands.push_back(BDCT_PATH_FP32);
-        if (tc_ok) cands.push_back(BDCT_PATH_SPLIT_TC);
+    size_t cached_mb = 0;
+    if (cache_lookup(c.rows, c.cols, kind, norm, &cached, &cached_mb)) {
+        cands.push_back({cached, cached_mb});
+    } else if (separable) {
+        for (size_t mb : {16, 32, 64}) cands.push_back({BDCT_PATH_FP32, mb});
+    } else {
+        cands.push_back({BDCT_PATH_FP32, 0});
+        if (tc_ok) cands.push_back({BDCT_PATH_SPLIT_TC, 0});
     }
     int st = BDCT_OK;
     double best = 1e300;
-    for (int cand : cands) {
-        bdct_plan *pl = nullptr;
-        st = bdct_plan_create(&pl, c.rows, c.cols, kind, norm, cand);
-        if (st != BDCT_OK) break;
+    bdct_plan *pl = nullptr;
+    int pl_path = -1;
+    for (const Cand &cd : cands) {
+        if (cd.path != pl_path) {
+            if (pl && pl != c.plan) bdct_plan_destroy(pl);
+            pl = nullptr;
+            st = bdct_plan_create(&pl, c.rows, c.cols, kind, norm, cd.path);
+            if (st != BDCT_OK) break;
+            pl_path = cd.path;
+        }
+        if (cd.chunk_mb) {
+            st = bdct_plan_set_chunk_bytes(pl, cd.chunk_mb << 20);
+            if (st != BDCT_OK) break;
+        }
         double us = 0.0;
         st = time_plan(pl, kind, d_in, d_out, n, &us);
-        if (st != BDCT_OK) { bdct_plan_destroy(pl); break; }
+        if (st != BDCT_OK) break;
         if (us < best) {
-            if (c.plan) bdct_plan_destroy(c.plan);
-            c.plan = pl;
-            c.path = cand;
             best = us;
-        } else {
-            bdct_plan_destroy(pl);
+            c.path = cd.path;
+            c.chunk_bytes = cd.chunk_mb << 20;
+            if (c.plan && c.plan != pl) bdct_plan_destroy(c.plan);
+            c.plan = pl;
         }
     }
+    if (pl && pl != c.plan) bdct_plan_destroy(pl);
     cudaFree(d_in);
     cudaFree(d_out);
     if (st != BDCT_OK) return st;
+    // the same plan may have been timed at a later chunk size than the best one
+    if (c.chunk_bytes) {
+        st = bdct_plan_set_chunk_bytes(c.plan, c.chunk_bytes);
+        if (st != BDCT_OK) return st;
+    }
     c.tuned_us = best;
-    if (cands.size() > 1) cache_store(c.rows, c.cols, kind, norm, c.path, best);
+    if (cands.size() > 1) cache_store(c.rows, c.cols, kind, norm, c.path, c.chunk_bytes >> 20, best);
     return BDCT_OK;
 }
 
@@ -241,22 +280,53 @@ extern "C" int bdct_ragged_create(bdct_ragged **out, size_t n, const int *rows, 
             return BDCT_ERR_CUDA;
         }
     }
-    if (cudaStreamCreateWithFlags(&r->capture, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaStreamCreateWithFlags(&r->capture, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&r->fork, cudaEventDisableTiming) != cudaSuccess) {
         ragged_free(r);
         return BDCT_ERR_CUDA;
     }
+    for (int i = 0; i < bdct_ragged::kBranches; ++i)
+        if (cudaStreamCreateWithFlags(&r->side[i], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&r->join[i], cudaEventDisableTiming) != cudaSuccess) {
+            ragged_free(r);
+            return BDCT_ERR_CUDA;
+        }
     if (cudaDeviceSynchronize() != cudaSuccess) { ragged_free(r); return BDCT_ERR_CUDA; }
     *out = r;
     return BDCT_OK;
 }
 
-static int ragged_launch_all(const bdct_ragged *r, Dir dir, const float *in, float *out, cudaStream_t s)
+// Record every class's launch into the capture stream's graph: the largest
+// class on the capture stream itself, the others round robin on side
+// streams forked from it and joined back, so that the graph holds parallel
+// branches and the small classes can fill SMs the large class leaves idle.
+static int ragged_launch_all(const bdct_ragged *r, Dir dir, const float *in, float *out)
 {
-    for (const auto &c : r->classes) {
-        int st = plan_execute(c.plan, dir, in, c.d_in_off, out, c.d_out_off, (long long)c.in_off.size(), s);
-        if (st != BDCT_OK) return st;
+    const int nb = bdct_ragged::kBranches;
+    if (cudaEventRecord(r->fork, r->capture) != cudaSuccess) return BDCT_ERR_CUDA;
+    bool used[bdct_ragged::kBranches] = {};
+    int st = BDCT_OK;
+    for (size_t i = 0; i < r->classes.size() && st == BDCT_OK; ++i) {
+        const auto &c = r->classes[i];
+        cudaStream_t s = r->capture;
+        if (i > 0) {
+            const int b = (int)((i - 1) % nb);
+            s = r->side[b];
+            if (!used[b]) {
+                if (cudaStreamWaitEvent(s, r->fork, 0) != cudaSuccess) return BDCT_ERR_CUDA;
+                used[b] = true;
+            }
+        }
+        st = plan_execute(c.plan, dir, in, c.d_in_off, out, c.d_out_off, (long long)c.in_off.size(), s);
     }
-    return BDCT_OK;
+    // join every branch that was used (also on error, so that the capture can end)
+    for (int b = 0; b < nb; ++b)
+        if (used[b]) {
+            if (cudaEventRecord(r->join[b], r->side[b]) != cudaSuccess ||
+                cudaStreamWaitEvent(r->capture, r->join[b], 0) != cudaSuccess)
+                st = BDCT_ERR_CUDA;
+        }
+    return st;
 }
 
 extern "C" int bdct_ragged_execute(bdct_ragged *r, unsigned kind, const float *in_base, float *out_base,
@@ -281,7 +351,7 @@ extern "C" int bdct_ragged_execute(bdct_ragged *r, unsigned kind, const float *i
     if (!exec) {
         // capture every class's launch once for these pointers
         if (cudaStreamBeginCapture(r->capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return BDCT_ERR_CUDA;
-        int st = ragged_launch_all(r, dir, in_base, out_base, r->capture);
+        int st = ragged_launch_all(r, dir, in_base, out_base);
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamEndCapture(r->capture, &graph);
         if (st != BDCT_OK) { if (graph) cudaGraphDestroy(graph); return st; }
@@ -318,5 +388,6 @@ extern "C" int bdct_ragged_class_info(const bdct_ragged *r, int index, bdct_ragg
     info->path = c.path == BDCT_PATH_AUTO ? c.plan->path : c.path;
     info->variant = c.plan->variant;
     info->tuned_us_per_array = c.tuned_us;
+    info->chunk_bytes = c.chunk_bytes;
     return BDCT_OK;
 }

@@ -18,24 +18,28 @@
 // split in the kernel into three BF16 terms x = x0 + x1 + x2 (each the
 // round-to-nearest BF16 of the remaining residual), the FP64 operator into
 // three terms once at plan time, and the six products with term orders
-// summing to at most 2 are accumulated in FP32.  The five small products go
-// to one TMEM accumulator and the main product x0 * m0 to a second one, added
-// in registers at the end: measured in emulation this keeps the FP32
-// accumulation error of a 4096-point contraction at the level of summing the
-// small products first (3e-7 per pass), where interleaving the products chunk
-// by chunk would double it.
-//
-// Organization: a tile is 128 rows (the MMA's M) by NT outputs (its N); K
-// runs in chunks of KC <= 64 through two shared-memory stages.  All 128
+// summing to at most 2 are accumulated in FP32, smallest first.  Measured on
+// the GPU, the tensor cores' FP32 accumulation loses about half an FP32 ulp
+// per accumulated MMA step, always in the same direction, so one accumulator
+// over a whole long contraction drifts linearly with its length (1.6e-6 at
+// 1024 points, 7.7e-6 at 4096).  Each K chunk (at most 64 points, four MMA
+// steps per product) therefore gets a fresh TMEM accumulator, and the
+// threads add the chunk partials in registers with round-to-nearest FP32
+// additions, in chunk order.
+
+// Organization: a tile is 128 rows (the MMA's M) by NT <= 64 outputs (its N);
+// K runs in chunks of KC <= 64 through two shared-memory stages and two TMEM
+// accumulators.  All 128
 // threads stage A -- thread t loads row t of the chunk (prefetched into
 // registers one chunk ahead), splits it and writes the terms in the
 // canonical K-major layout -- while thread 0 brings the operator's terms for
 // the chunk with one bulk copy and, once both are in, issues the products
 // and commits them to the stage's mbarrier.  The next chunk is staged while
-// those products run.  Epilogue: thread t reads its TMEM lane (row t of the
-// tile), adds the two accumulators and stores its outputs transposed (lanes
-// of a warp hold consecutive rows, so each output index is one coalesced
-// segment).  Persistent CTAs walk the (row tile, output tile) items.
+// those products run, and the partial of chunk g - 2 is read from its TMEM
+// lane (row t of the tile) into the running sums.  Epilogue: thread t stores
+// its outputs transposed (lanes of a warp hold consecutive rows, so each
+// output index is one coalesced segment).  Persistent CTAs walk the (row
+// tile, output tile) items.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -57,7 +61,7 @@ struct TgCfg {
     static constexpr int B_TERM = NT * kTgKC * 2;    // bytes of one BF16 term of the operator chunk
     static constexpr int STAGE = 3 * A_TERM + 3 * B_TERM;
     static constexpr size_t SMEM = (size_t)kTgStages * STAGE + 4 * 8 + 16;
-    static constexpr int TMEM_COLS = 2 * NT < 32 ? 32 : 2 * NT;  // small-product and main-product accumulators
+    static constexpr int TMEM_COLS = 2 * NT < 32 ? 32 : 2 * NT;  // two chunk accumulators
 };
 
 struct TgParams {
@@ -104,7 +108,7 @@ __global__ void __launch_bounds__(128) k_tcg(const TgParams p)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const uint32_t acc_small = tmem, acc_big = tmem + NT;
+    // chunk partials, double-buffered: accumulator a at TMEM column a * NT
     const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
     const int KC = p.KC;
     const uint32_t sbo = (uint32_t)(KC / 8) * 128u;  // M/N-adjacent core matrices
@@ -138,8 +142,21 @@ __global__ void __launch_bounds__(128) k_tcg(const TgParams p)
     };
 
     bool ok = true;
-    uint32_t g = 0;                  // chunks this CTA has started
+    uint32_t g = 0;                      // chunks this CTA has started
     long long last_b = -1, last_c = -1;  // thread 0: last operator copy and last commit issued
+    float sum[NT];                       // this thread's row of the tile, summed over the chunks
+#pragma unroll
+    for (int j = 0; j < NT; ++j) sum[j] = 0.0f;
+    // add the finished chunk partial in TMEM accumulator a to sum (in chunk order)
+    auto take_partial = [&](int a) {
+#pragma unroll
+        for (int c = 0; c < NT / 16; ++c) {
+            float y[16];
+            tmem_ld16(tmem + (uint32_t)(a * NT) + lane_off + 16 * c, y);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) sum[16 * c + j] += y[j];
+        }
+    };
     long long item = blockIdx.x;
     if (item < p.items) load_chunk(row_ptr(item), 0);
     for (; ok && item < p.items; item += gridDim.x) {
@@ -149,8 +166,17 @@ __global__ void __launch_bounds__(128) k_tcg(const TgParams p)
             const int s = (int)(g & 1u);
             const uint32_t use = g >> 1;
             uint8_t *st = tgs + s * C::STAGE;
-            // the stage is free once the products of chunk g - 2 are done
-            if (g >= 2 && !mbar_wait_bounded(&mdone[s], (use - 1) & 1u)) ok = false;
+            // stage s and accumulator s are free once the products of chunk
+            // g - 2 are done; that chunk's partial is added here when it belongs
+            // to this item (the previous item's last two were added at its end)
+            if (g >= 2) {
+                if (!mbar_wait_bounded(&mdone[s], (use - 1) & 1u)) ok = false;
+                ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld is warp-collective
+                if (ok && kc >= 2) {
+                    tc_fence_after();
+                    take_partial(s);
+                }
+            }
             if (tid == 0 && ok) {
                 mbar_arrive_expect_tx(&bfull[s], b_bytes);
                 bulk_load(st + 3 * C::A_TERM, p.ops + ((long long)nt * p.nk + kc) * b_chunk_elems, b_bytes, &bfull[s]);
@@ -184,9 +210,8 @@ __global__ void __launch_bounds__(128) k_tcg(const TgParams p)
             // prefetch the next chunk's row segment (the next item's first one
             // after the last chunk) while the products run
             {
-                const bool more = kc + 1 < p.nk;
                 const long long ni = item + gridDim.x;
-                if (more) load_chunk(row, kc + 1);
+                if (kc + 1 < p.nk) load_chunk(row, kc + 1);
                 else if (ni < p.items) load_chunk(row_ptr(ni), 0);
             }
             if (tid == 0) {
@@ -194,66 +219,65 @@ __global__ void __launch_bounds__(128) k_tcg(const TgParams p)
                     record_timeout(p.status);  // the others learn of it at their next wait
                 } else {
                     const uint32_t a0 = smem_u32(st), b0 = smem_u32(st + 3 * C::A_TERM);
-                    // small products (term orders summing to 1 or 2), smallest first
-                    constexpr int pa[5] = {2, 1, 0, 1, 0};
-                    constexpr int pb[5] = {0, 1, 2, 0, 1};
+                    // this chunk's products into a fresh accumulator: the small ones
+                    // (term orders summing to 1 or 2) smallest first, the main one last
+                    constexpr int pa[6] = {2, 1, 0, 1, 0, 0};
+                    constexpr int pb[6] = {0, 1, 2, 0, 1, 0};
                     constexpr int first = TERMS == 3 ? 0 : (TERMS == 2 ? 3 : 5);
 #pragma unroll
-                    for (int pr = first; pr < 5; ++pr)
+                    for (int pr = first; pr < 6; ++pr)
                         for (int ks = 0; ks < KC / 16; ++ks)
-                            tc_mma(acc_small, smem_desc(a0 + pa[pr] * C::A_TERM + ks * 256, 128, sbo),
+                            tc_mma(tmem + (uint32_t)(s * NT), smem_desc(a0 + pa[pr] * C::A_TERM + ks * 256, 128, sbo),
                                    smem_desc(b0 + pb[pr] * b_term + ks * 256, 128, sbo), idesc,
-                                   (kc > 0 || pr > first || ks > 0) ? 1u : 0u);
-                    for (int ks = 0; ks < KC / 16; ++ks)
-                        tc_mma(acc_big, smem_desc(a0 + ks * 256, 128, sbo), smem_desc(b0 + ks * 256, 128, sbo), idesc,
-                               (kc > 0 || ks > 0) ? 1u : 0u);
+                                   (pr > first || ks > 0) ? 1u : 0u);
                     tc_commit(&mdone[s]);
                     last_c = g;
                 }
             }
         }
         if (!ok) break;
-        // ---- epilogue: this thread's TMEM lane = row tid of the tile
+        // ---- epilogue: the item's last two chunk partials, then this
+        // thread's row of the tile (TMEM lane tid) is complete
         const uint32_t gl = g - 1;
-        if (!mbar_wait_bounded(&mdone[gl & 1u], (gl >> 1) & 1u)) ok = false;
+        if (p.nk >= 2) {
+            const uint32_t gp = g - 2;
+            if (!mbar_wait_bounded(&mdone[gp & 1u], (gp >> 1) & 1u)) ok = false;
+            ok = __all_sync(0xffffffffu, ok);
+            if (ok) {
+                tc_fence_after();
+                take_partial((int)(gp & 1u));
+            }
+        }
+        if (ok && !mbar_wait_bounded(&mdone[gl & 1u], (gl >> 1) & 1u)) ok = false;
+        ok = __all_sync(0xffffffffu, ok);
+        if (ok) {
+            tc_fence_after();
+            take_partial((int)(gl & 1u));
+        }
         ok = __syncthreads_and(ok);
         if (!ok) break;
-        tc_fence_after();
         const long long m = (item / p.n_tiles) * kTgM + tid;
-        const bool row_ok = m < p.rows_total;
-        long long b = 0, r = 0;
-        float *dbase = nullptr;
-        if (row_ok) {
-            b = m / p.R;
-            r = m - b * p.R;
-            dbase = p.dst + (p.dst_off ? p.dst_off[b] : b * (long long)p.N * p.R);
-        }
-#pragma unroll 1
-        for (int c = 0; c < NT / 16; ++c) {
-            float y[16];
-            tmem_ld16(acc_big + lane_off + 16 * c, y);
-            if constexpr (TERMS > 1) {
-                float ys[16];
-                tmem_ld16(acc_small + lane_off + 16 * c, ys);
+        if (m < p.rows_total) {
+            const long long b = m / p.R;
+            const long long r = m - b * p.R;
+            float *dbase = p.dst + (p.dst_off ? p.dst_off[b] : b * (long long)p.N * p.R);
+            const int n0 = nt * NT;
+            if (p.lam) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) y[j] = ys[j] + y[j];
+                for (int j = 0; j < NT; ++j) sum[j] *= __ldg(p.lam + (long long)(n0 + j) * p.R + r);
             }
-            if (row_ok) {
-                const int n0 = nt * NT + 16 * c;
-                if (p.lam) {
+            if (p.R == 1) {
+                float4 *d4 = reinterpret_cast<float4 *>(dbase + n0);
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) y[j] *= __ldg(p.lam + (long long)(n0 + j) * p.R + r);
-                }
-                if (p.R == 1) {
-                    float4 *d4 = reinterpret_cast<float4 *>(dbase + n0);
+                for (int j = 0; j < NT / 4; ++j)
+                    d4[j] = make_float4(sum[4 * j], sum[4 * j + 1], sum[4 * j + 2], sum[4 * j + 3]);
+            } else {
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) d4[j] = make_float4(y[4 * j], y[4 * j + 1], y[4 * j + 2], y[4 * j + 3]);
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) dbase[(long long)(n0 + j) * p.R + r] = y[j];
-                }
+                for (int j = 0; j < NT; ++j) dbase[(long long)(n0 + j) * p.R + r] = sum[j];
             }
         }
+#pragma unroll
+        for (int j = 0; j < NT; ++j) sum[j] = 0.0f;
         // every lane has read its accumulators before the next item's products overwrite them
         tc_fence_before();
         __syncthreads();
@@ -326,10 +350,11 @@ __global__ void k_gen_tg_op(__nv_bfloat16 *dst, int N, int K, int direction, int
     dst[base + 2LL * NT * KC] = t2;
 }
 
-// Tile width for an output length: the largest of 128, 64, 32, 16 dividing it.
+// Tile width for an output length: the largest of 64, 32, 16 dividing it (a
+// thread holds its row of the tile in registers across the K loop).
 static int tg_nt(int n)
 {
-    for (int nt : {128, 64, 32, 16})
+    for (int nt : {64, 32, 16})
         if (n % nt == 0) return nt;
     return 0;
 }
@@ -439,7 +464,6 @@ cudaError_t tg_pass(const float *src, float *dst, const long long *src_off, cons
     p.lam = lam;
     p.status = status;
     switch (NT) {
-        case 128: return tg_launch_nt<128>(terms, p, stream);
         case 64: return tg_launch_nt<64>(terms, p, stream);
         case 32: return tg_launch_nt<32>(terms, p, stream);
         default: return tg_launch_nt<16>(terms, p, stream);

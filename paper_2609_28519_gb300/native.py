@@ -31,7 +31,7 @@ STATUS = {0: "OK", 1: "ERR_INVALID_ARG", 2: "ERR_UNSUPPORTED_SHAPE", 3: "ERR_KIN
 EXPORTS = [
     "bdct_plan_create", "bdct_plan_set_spectral", "bdct_plan_destroy", "bdct_forward", "bdct_inverse", "bdct_roundtrip",
     "bdct_execute", "bdct_execute_tiled", "bdct_plan_set_host_staging", "bdct_execute_host",
-    "bdct_execute_tiled_host", "bdct_plan_get_info", "bdct_plan_device_status",
+    "bdct_execute_tiled_host", "bdct_plan_get_info", "bdct_plan_set_chunk_bytes", "bdct_plan_device_status",
     "bdct_ragged_create", "bdct_ragged_execute", "bdct_ragged_destroy", "bdct_ragged_num_classes",
     "bdct_ragged_class_info", "bdct_execute_noalloc", "bdct_selftest_wait_timeout", "bdct_status_string",
     "bdct_last_cuda_error", "bdct_version",
@@ -57,7 +57,8 @@ class PlanInfo(ctypes.Structure):
 
 class RaggedClass(ctypes.Structure):
     _fields_ = [("rows", ctypes.c_int), ("cols", ctypes.c_int), ("count", ctypes.c_size_t),
-                ("path", ctypes.c_int), ("variant", ctypes.c_int), ("tuned_us_per_array", ctypes.c_double)]
+                ("path", ctypes.c_int), ("variant", ctypes.c_int), ("tuned_us_per_array", ctypes.c_double),
+                ("chunk_bytes", ctypes.c_size_t)]
 
 
 _lib = None
@@ -86,6 +87,7 @@ def lib() -> ctypes.CDLL:
             L.bdct_execute_host.argtypes = [vp, vp, ci, vp, vp, sz, vp]
             L.bdct_execute_tiled_host.argtypes = [vp, vp, ci, vp, vp, ci, ci, vp]
             L.bdct_plan_device_status.argtypes = [vp, ci]
+            L.bdct_plan_set_chunk_bytes.argtypes = [vp, sz]
             L.bdct_selftest_wait_timeout.argtypes = [cu]
             L.bdct_execute_noalloc.argtypes = [ci, ci, cu, ci, vp, vp, sz, vp]
             L.bdct_ragged_create.argtypes = [ctypes.POINTER(vp), sz, vp, vp, vp, vp, cu, ci, ci]
@@ -140,6 +142,11 @@ class Plan:
         inf = PlanInfo()
         _check(lib().bdct_plan_get_info(self.handle, ctypes.byref(inf)), "bdct_plan_get_info")
         return inf
+
+    def set_chunk_bytes(self, nbytes: int) -> None:
+        """Chunk of whole arrays per two-pass round of the separable routes
+        (bdct_plan_set_chunk_bytes)."""
+        _check(lib().bdct_plan_set_chunk_bytes(self.handle, int(nbytes)), "bdct_plan_set_chunk_bytes")
 
     def device_status(self, clear: bool = True) -> int:
         """Synchronize and return the plan's device status (0, or 8 after a
@@ -291,7 +298,8 @@ class Ragged:
             c = RaggedClass()
             _check(L.bdct_ragged_class_info(self._h, i, ctypes.byref(c)), "bdct_ragged_class_info")
             out.append({"rows": c.rows, "cols": c.cols, "count": c.count, "path": c.path,
-                        "variant": c.variant, "tuned_us_per_array": c.tuned_us_per_array})
+                        "variant": c.variant, "tuned_us_per_array": c.tuned_us_per_array,
+                        "chunk_bytes": c.chunk_bytes})
         return out
 
     def execute(self, kind, x, out, stream=None):
