@@ -112,6 +112,23 @@ int bdct_plan_create(bdct_plan **plan, int rows, int cols, unsigned kind, int no
  * the first call returns BDCT_ERR_INVALID_ARG.                              */
 int bdct_plan_set_spectral(bdct_plan *plan, const double *lambda);
 
+/* Numerical-range protection (Section 6 reports unnormalized intermediates
+ * that overflow although the orthonormal result is representable, and
+ * subnormal inputs that lose relative accuracy; Section 8 lists range
+ * protection as future work).  With on != 0 every call of the plan scales
+ * each array exactly by 2^-e, e the binary exponent of its largest
+ * magnitude, transforms it, and scales the result back by 2^e (every
+ * direction is linear, and a power-of-two scaling is exact while values stay
+ * normal): the cores then never see magnitudes near FLT_MAX, and subnormal
+ * inputs are transformed as normal numbers.  Costs two extra passes over the
+ * output and one over the input; results equal the unprotected ones
+ * wherever those stay within range.  Arrays whose largest magnitude is 0,
+ * infinite or NaN are left unscaled.  The plan allocates 4 MiB of exponent
+ * words (chunks of up to 2^20 arrays; a tiled call may hold at most 2^20
+ * blocks, else BDCT_ERR_UNSUPPORTED_SHAPE).  on == 0 turns it off and frees
+ * them.  No work using the plan may be queued.                             */
+int bdct_plan_set_range_protection(bdct_plan *plan, int on);
+
 /* Release a plan and its device memory.  The caller must ensure no work
  * using the plan is still queued.  NULL is accepted (no-op).               */
 int bdct_plan_destroy(bdct_plan *plan);

@@ -21,4 +21,4 @@ from .oracle import (  # noqa: F401
     set_fault,
     default_threads,
 )
-from .check import metrics, accept, ERR_REL_TOL, MAX_ABS_TOL  # noqa: F401
+from .check import metrics, accept, boundary_metrics, ERR_REL_TOL, MAX_ABS_TOL  # noqa: F401

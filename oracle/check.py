@@ -74,3 +74,30 @@ def accept(m: dict, rel_tol: float = ERR_REL_TOL, abs_tol: float = MAX_ABS_TOL) 
     """True when every array meets both bars and nothing is non-finite."""
     return (m["nonfinite"] == 0 and m["zero_input_violations"] == 0
             and m["e_rel_max"] <= rel_tol and m["max_abs_ratio_max"] <= abs_tol)
+
+
+def boundary_metrics(y_hat, y_ref, x, rel_tol: float = ERR_REL_TOL) -> dict:
+    """Boundary diagnostics (Section 6: extreme amplitudes and subnormals).
+
+    Per array: ``representable`` -- every exact output below FLT_MAX in
+    magnitude; ``passed`` -- the output is finite where representable and its
+    error stays within rel_tol * ||X||_F plus twice the error of rounding the
+    exact result to float32 (no float32 output can do better than that
+    rounding, which for subnormal results is far above 1e-6 relative).
+    """
+    y_hat = np.asarray(y_hat, dtype=np.float64)
+    h, w = y_hat.shape[-2:]
+    yh = y_hat.reshape(-1, h * w)
+    yr = np.asarray(y_ref, dtype=np.float64).reshape(-1, h * w)
+    xx = np.asarray(x, dtype=np.float64).reshape(-1, h * w)
+    fmax = float(np.finfo(np.float32).max)
+    representable = np.max(np.abs(yr), axis=1) < fmax
+    with np.errstate(over="ignore", invalid="ignore"):
+        floor = np.sqrt(np.sum((yr.astype(np.float32).astype(np.float64) - yr) ** 2, axis=1))
+        err = np.sqrt(np.sum((yh - yr) ** 2, axis=1))
+    finite = np.all(np.isfinite(yh), axis=1)
+    bound = rel_tol * np.sqrt(np.sum(xx * xx, axis=1)) + 2.0 * floor
+    passed = representable & finite & (err <= bound)
+    return {"representable": representable, "passed": passed, "err": err, "bound": bound,
+            "checks": int(len(yh)), "n_representable": int(np.sum(representable)),
+            "n_failed": int(np.sum(representable & ~passed))}

@@ -72,6 +72,7 @@ static void plan_free(bdct_plan *p)
     if (p->line_tw) cudaFree(p->line_tw);
     if (p->spec_plain) cudaFree(p->spec_plain);
     if (p->spec_fold) cudaFree(p->spec_fold);
+    if (p->rp_bits) cudaFree(p->rp_bits);
     host_staging_free(p);
     if (p->work) cudaFree(p->work);
     delete p;
@@ -493,11 +494,38 @@ static int run_tg(const bdct_plan *p, Dir dir, const float *in, const long long 
     return BDCT_OK;
 }
 
+static int execute_dir(const bdct_plan *p, Dir dir, const float *in, const long long *in_off, float *out,
+                       const long long *out_off, long long count, cudaStream_t s);
+
 int bdct::plan_execute(const bdct_plan *p, Dir dir, const float *in, const long long *in_off, float *out,
                        const long long *out_off, long long count, cudaStream_t s)
 {
     if (count <= 0) return BDCT_OK;
     if (dir == DIR_SPEC && !p->spec_plain) return BDCT_ERR_INVALID_ARG;  // no diagonal set
+    if (!p->rp_bits) return execute_dir(p, dir, in, in_off, out, out_off, count, s);
+    // range protection, per chunk of arrays: scale into the output, transform
+    // in place there, scale back
+    const long long hw = (long long)p->rows * p->cols;
+    for (long long b0 = 0; b0 < count; b0 += p->rp_cap) {
+        const long long nb = (count - b0) < p->rp_cap ? (count - b0) : p->rp_cap;
+        const float *src = in_off ? in : in + b0 * hw;
+        float *dst = out_off ? out : out + b0 * hw;
+        const long long *so = in_off ? in_off + b0 : nullptr;
+        const long long *dof = out_off ? out_off + b0 : nullptr;
+        ExecGeom g{src, dst, nb, 0, 0, 0, 0, so, dof};
+        cudaError_t e = range_prescale(g, p->rows, p->cols, p->rp_bits, s);
+        if (e != cudaSuccess) return cuda_fail(e);
+        const int st = execute_dir(p, dir, dst, dof, dst, dof, nb, s);
+        if (st != BDCT_OK) return st;
+        e = range_postscale(g, p->rows, p->cols, p->rp_bits, s);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return BDCT_OK;
+}
+
+static int execute_dir(const bdct_plan *p, Dir dir, const float *in, const long long *in_off, float *out,
+                       const long long *out_off, long long count, cudaStream_t s)
+{
     if (p->variant == 1 || p->variant == 3) {
         ExecGeom g{in, out, count, 0, 0, 0, 0, in_off, out_off};
         return run_onchip(p, dir, g, s);
@@ -576,7 +604,50 @@ extern "C" int bdct_execute_tiled(const bdct_plan *plan, unsigned kind, const fl
     const int tpr = img_cols / plan->cols;
     const long long tiles = (long long)(img_rows / plan->rows) * tpr;
     ExecGeom g{in, out, tiles, 1, tpr, (long long)ld_in, (long long)ld_out};
-    return run_onchip(plan, dir, g, (cudaStream_t)stream);
+    if (!plan->rp_bits) return run_onchip(plan, dir, g, (cudaStream_t)stream);
+    // range protection: scale every block into the output, transform there in
+    // place, scale back
+    if (tiles > plan->rp_cap) return BDCT_ERR_UNSUPPORTED_SHAPE;
+    cudaError_t e = range_prescale(g, plan->rows, plan->cols, plan->rp_bits, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    ExecGeom gi = g;
+    gi.in = out;
+    gi.ld_in = (long long)ld_out;
+    st = run_onchip(plan, dir, gi, (cudaStream_t)stream);
+    if (st != BDCT_OK) return st;
+    e = range_postscale(g, plan->rows, plan->cols, plan->rp_bits, (cudaStream_t)stream);
+    return e == cudaSuccess ? BDCT_OK : cuda_fail(e);
+}
+
+extern "C" int bdct_plan_set_range_protection(bdct_plan *plan, int on)
+{
+    if (!plan) return BDCT_ERR_INVALID_ARG;
+    int cur = -1;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (cur != plan->device && (e = cudaSetDevice(plan->device)) != cudaSuccess) return cuda_fail(e);
+    int st = BDCT_OK;
+    if (!on) {
+        if (plan->rp_bits) {
+            e = cudaDeviceSynchronize();
+            cudaFree(plan->rp_bits);
+            plan->rp_bits = nullptr;
+            plan->rp_cap = 0;
+            if (e != cudaSuccess) st = cuda_fail(e);
+        }
+    } else if (!plan->rp_bits) {
+        const long long cap = 1ll << 20;  // arrays per chunk (4 MiB of exponent words)
+        e = cudaMalloc(&plan->rp_bits, (size_t)cap * sizeof(unsigned int));
+        if (e != cudaSuccess) {
+            plan->rp_bits = nullptr;
+            t_last_cuda_error = (int)e;
+            st = BDCT_ERR_NO_MEMORY;
+        } else {
+            plan->rp_cap = cap;
+        }
+    }
+    if (cur >= 0 && cur != plan->device) cudaSetDevice(cur);
+    return st;
 }
 
 extern "C" int bdct_plan_set_spectral(bdct_plan *plan, const double *lambda)

@@ -163,6 +163,14 @@ cudaError_t spectral_scale(const ExecGeom &g, int h, int w, const float *lam, cu
 // geometry g (contiguous or indexed through out_off).
 cudaError_t copy_arrays(const float *src, const ExecGeom &g, int h, int w, cudaStream_t s);
 
+// ---- range.cu
+// Range protection: per array, the binary exponent e of its largest magnitude
+// (maxbits: one word per array, cleared here), and out = in * 2^-e (the
+// call's geometry, in place allowed); range_postscale multiplies the output
+// by 2^e again.
+cudaError_t range_prescale(const ExecGeom &g, int h, int w, unsigned int *maxbits, cudaStream_t s);
+cudaError_t range_postscale(const ExecGeom &g, int h, int w, const unsigned int *maxbits, cudaStream_t s);
+
 // ---- tc_gemm.cu
 // Split-BF16 tensor-core separable passes: any side 16, 32 or a multiple of
 // 64 up to 8192 per axis, and 8 x 8 arrays as one 64 x 64 Kronecker product.

@@ -41,6 +41,10 @@ struct bdct_plan {
     // spectral direction (bdct_plan_set_spectral): Lambda in FP32, and Lambda
     // folded with the squared scales for the unscaled fused cores (Prop. 1)
     float *spec_plain = nullptr, *spec_fold = nullptr;
+    // range protection (bdct_plan_set_range_protection): one exponent word per
+    // array of a chunk of at most rp_cap arrays; null = off
+    unsigned int *rp_bits = nullptr;
+    long long rp_cap = 0;
     // host-buffer execution (bdct_plan_set_host_staging): kStageSlots slots of
     // two device buffers, and streams/events of the copy-in / transform /
     // copy-out pipeline

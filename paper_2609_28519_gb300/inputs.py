@@ -18,6 +18,9 @@ them; see Section 6 of the paper for the input categories):
   neighbouring floats, weak perturbations of a strong constant, amplitudes
   2^-100 .. 2^90 (Section 6 input categories, regenerated synthetically)
 * ``ragged_shapes``   shapes drawn uniformly from the nine mixed shapes
+* ``boundary_suite``  extreme-amplitude cases (Section 6 boundary diagnostics,
+  regenerated synthetically): deep and shallow subnormals, mixed subnormal /
+  normal, amplitudes near FLT_MAX, constants near FLT_MAX / n
 * ``random_diagonal`` a seeded h x w spectral diagonal, uniform in [lo, hi]
 * ``poisson_diagonal`` the inverse eigenvalues of the 5-point Laplacian with
   reflecting (Neumann) borders, the diagonal of a least-squares phase-
@@ -153,3 +156,27 @@ def poisson_diagonal(h: int, w: int) -> np.ndarray:
     lam = 1.0 / ev
     lam[0, 0] = 0.0
     return lam
+
+
+def boundary_suite(seed: int, n: int):
+    """Boundary-diagnostic inputs for n x n arrays (float32), one array per
+    case; returns (x, labels)."""
+    rng = np.random.default_rng(seed)
+    u = lambda: rng.uniform(-1.0, 1.0, size=(n, n))
+    cases = []
+    for e in (-149, -140, -130, -127):          # subnormal and edge-of-normal amplitudes
+        cases.append((f"uniform*2^{e}", u() * 2.0 ** e))
+    mix = u() * 2.0 ** -120
+    mix[rng.random(size=(n, n)) < 0.5] *= 2.0 ** -20
+    cases.append(("mixed 2^-120 / 2^-140", mix))
+    for e in (120, 125, 126, 127):              # near the top of the range
+        cases.append((f"uniform*2^{e}", u() * 2.0 ** e))
+    big = float(np.finfo(np.float32).max) / (2 * n)  # orthonormal results stay below FLT_MAX / 2
+    checker = np.where((np.add.outer(np.arange(n), np.arange(n)) % 2) == 0, 1.0, -1.0)
+    cases.append(("constant FLT_MAX/2n", np.full((n, n), big)))
+    cases.append(("uniform*FLT_MAX/2n", u() * big))
+    cases.append(("checkerboard*FLT_MAX/2n", checker * big))
+    cases.append(("constant 2^127", np.full((n, n), 2.0 ** 127)))
+    cases.append(("checkerboard*2^127", checker * 2.0 ** 127))
+    x = np.stack([c[1] for c in cases]).astype(np.float32)
+    return x, [c[0] for c in cases]

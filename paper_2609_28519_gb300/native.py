@@ -29,7 +29,7 @@ STATUS = {0: "OK", 1: "ERR_INVALID_ARG", 2: "ERR_UNSUPPORTED_SHAPE", 3: "ERR_KIN
 
 # every symbol the header declares, in declaration order
 EXPORTS = [
-    "bdct_plan_create", "bdct_plan_set_spectral", "bdct_plan_destroy", "bdct_forward", "bdct_inverse", "bdct_roundtrip",
+    "bdct_plan_create", "bdct_plan_set_spectral", "bdct_plan_set_range_protection", "bdct_plan_destroy", "bdct_forward", "bdct_inverse", "bdct_roundtrip",
     "bdct_execute", "bdct_execute_tiled", "bdct_plan_set_host_staging", "bdct_execute_host",
     "bdct_execute_tiled_host", "bdct_plan_get_info", "bdct_plan_set_chunk_bytes", "bdct_plan_device_status",
     "bdct_ragged_create", "bdct_ragged_execute", "bdct_ragged_destroy", "bdct_ragged_num_classes",
@@ -78,6 +78,7 @@ def lib() -> ctypes.CDLL:
             L.bdct_plan_create.argtypes = [ctypes.POINTER(vp), ci, ci, cu, ci, ci]
             L.bdct_plan_destroy.argtypes = [vp]
             L.bdct_plan_set_spectral.argtypes = [vp, vp]
+            L.bdct_plan_set_range_protection.argtypes = [vp, ci]
             for name in ("bdct_forward", "bdct_inverse", "bdct_roundtrip"):
                 getattr(L, name).argtypes = [vp, vp, vp, sz, vp]
             L.bdct_execute.argtypes = [vp, cu, vp, vp, sz, vp]
@@ -207,6 +208,11 @@ class Plan:
         if a.shape != (self.rows, self.cols):
             raise ValueError(f"diagonal must be ({self.rows}, {self.cols}), got {a.shape}")
         _check(lib().bdct_plan_set_spectral(self.handle, ctypes.c_void_p(a.ctypes.data)), "bdct_plan_set_spectral")
+
+    def set_range_protection(self, on: bool = True) -> None:
+        """Per-array power-of-two pre-scaling around every call
+        (bdct_plan_set_range_protection)."""
+        _check(lib().bdct_plan_set_range_protection(self.handle, 1 if on else 0), "bdct_plan_set_range_protection")
 
     def spectral(self, x, out=None, stream=None):
         return self.execute(SPECTRAL, x, out, stream)

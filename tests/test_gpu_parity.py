@@ -711,3 +711,69 @@ def test_split_tc_passes_inplace_report_only_and_ragged(oracle_mod, cuda_dev):
         for a, o, (r, c) in zip(arrs, _unpack(rg, y, shapes), shapes):
             _assert_parity(oracle_mod, o[None], _ref(oracle_mod, kind, a[None], 0), a[None], 0, kind,
                            ("tg-ragged", r, c, kind))
+
+
+# ------------------------------------------------------------ range protection (Section 6 boundary cases)
+def boundary_diagnostics(o, dev, sizes=(8, 16, 32, 64), kinds=KINDS, paths=("fp32",)):
+    """Run the boundary suite with range protection off and on; returns the
+    per-setting counts (checks, representable, failed) and the failures."""
+    from paper_2609_28519_gb300 import Plan
+    res = {}
+    for protect in (False, True):
+        tot = {"checks": 0, "representable": 0, "failed": 0, "failures": []}
+        for path in paths:
+            for n in sizes:
+                plan = Plan(n, n, path=path)
+                if protect:
+                    plan.set_range_protection(True)
+                x, labels = inputs.boundary_suite(9000 + n, n)
+                for kind in kinds:
+                    y = _run(plan, kind, x, dev)
+                    m = o.boundary_metrics(y, _ref(o, kind, x, 0), x)
+                    tot["checks"] += m["checks"]
+                    tot["representable"] += m["n_representable"]
+                    tot["failed"] += m["n_failed"]
+                    tot["failures"] += [(path, n, kind, labels[i]) for i in range(len(labels))
+                                        if m["representable"][i] and not m["passed"][i]]
+        res["protected" if protect else "unprotected"] = tot
+    return res
+
+
+def test_range_protection_boundary_suite(oracle_mod, cuda_dev, record_property):
+    """Section 6 boundary diagnostics regenerated synthetically (subnormal,
+    mixed, near-FLT_MAX amplitudes; 14 cases x 3 directions x 4 sizes):
+    without protection the overflowing intermediates and subnormal arithmetic
+    fail some checks (reported, not accepted); with per-array power-of-two
+    scaling every case whose exact result is representable passes, and
+    ordinary inputs give the same bits with protection on as off."""
+    import torch
+    from paper_2609_28519_gb300 import Plan
+    res = boundary_diagnostics(oracle_mod, cuda_dev)
+    for k in ("unprotected", "protected"):
+        record_property(f"boundary_{k}", {kk: res[k][kk] for kk in ("checks", "representable", "failed")})
+    print("boundary diagnostics:", {k: {kk: v[kk] for kk in ("checks", "representable", "failed")}
+                                    for k, v in res.items()})
+    assert res["protected"]["failed"] == 0, res["protected"]["failures"]
+    assert res["unprotected"]["failed"] > 0  # the suite does reach the boundary
+    # ordinary inputs: protection changes nothing (power-of-two scaling is exact)
+    for (h, w, path) in [(16, 16, "fp32"), (64, 128, "fp32"), (256, 256, "fp32"), (32, 32, "split_tc"),
+                         (128, 128, "split_tc")]:
+        x = torch.from_numpy(inputs.uniform(9100 + h + w, 9, h, w)).to(cuda_dev)
+        a, b = Plan(h, w, path=path), Plan(h, w, path=path)
+        b.set_range_protection(True)
+        for kind in KINDS:
+            ya, yb = a.execute(kind, x), b.execute(kind, x)
+            torch.cuda.synchronize()
+            # every core is linear, and scaling all inputs by a power of two
+            # scales every rounding with them: the same bits
+            assert torch.equal(ya, yb), (h, w, path, kind)
+    # the tiled view with protection, in place
+    img = torch.from_numpy(inputs.ramp_image(5, 256, 512) * np.float32(2.0 ** 120)).to(cuda_dev)
+    p = Plan(16, 16)
+    p.set_range_protection(True)
+    out = p.execute_tiled("forward", img.clone())
+    blocks = inputs.image_to_blocks(img.cpu().numpy(), 16, 16)
+    torch.cuda.synchronize()
+    m = oracle_mod.boundary_metrics(inputs.image_to_blocks(out.cpu().numpy(), 16, 16), oracle_mod.forward(blocks, 0),
+                                    blocks)
+    assert m["n_failed"] == 0

@@ -346,3 +346,25 @@ def test_planted_fault_breaks_a_pin(oracle_mod, fault):
     finally:
         o.set_fault(0)
     assert _pins_fail(o) == []
+
+
+def test_boundary_metrics_flags_overflow_and_accepts_rounding(oracle_mod):
+    """The boundary checker: the exact result rounded to float32 passes, an
+    infinity where the result is representable fails, a non-representable
+    case is not counted, and an error far above the rounding floor fails."""
+    o = oracle_mod
+    x, labels = inputs.boundary_suite(3, 8)
+    ref = o.forward(x, 0)
+    with np.errstate(over="ignore"):
+        y32 = ref.astype(np.float32)
+    m = o.boundary_metrics(y32, ref, x)
+    assert m["n_failed"] == 0 and m["n_representable"] == m["checks"] - int(np.sum(~m["representable"]))
+    bad = y32.astype(np.float64).copy()
+    k = labels.index("constant FLT_MAX/2n")
+    bad[k, 0, 0] = np.inf
+    assert not o.boundary_metrics(bad, ref, x)["passed"][k]
+    sub = labels.index("uniform*2^-130")
+    bad2 = ref.copy()
+    bad2[sub] *= 1.001
+    assert not o.boundary_metrics(bad2, ref, x)["passed"][sub]
+    assert not m["representable"][labels.index("constant 2^127")]
