@@ -437,6 +437,7 @@ def run_ours(args):
             "square_sweep_512MiB": sweep_summary(dev, [8, 16, 32, 64, 128, 256], 512, ("auto", "split_tc"),
                                                  check=not args.no_check),
             "ragged_4096": ragged_summary(dev),
+            "boundary_diagnostics": boundary_summary(dev) if not args.no_check else None,
             "large_arrays": large_summary(dev),
         }
 
@@ -605,6 +606,36 @@ def spectral_image_summary(work, dev, stream, steps, paths=("fp32", "split_tc"),
                         "criterion": "Eq. 5 on U^T (Lambda / max|Lambda|) U, 256 sampled blocks"})
         res[path] = ent
         plan.close()
+    return res
+
+
+def boundary_summary(dev, sizes=(8, 16, 32, 64)):
+    """Section 6 boundary diagnostics regenerated synthetically (subnormal,
+    mixed and near-FLT_MAX amplitudes; forward, inverse, round trip), with
+    range protection off and on: checks whose exact result is representable
+    in float32, and how many of them fail the oracle comparison."""
+    import torch
+    import oracle
+    from paper_2609_28519_gb300 import Plan, inputs
+    res = {}
+    for protect in (False, True):
+        tot = {"checks": 0, "representable": 0, "failed": 0}
+        for n in sizes:
+            plan = Plan(n, n)
+            if protect:
+                plan.set_range_protection(True)
+            x, _ = inputs.boundary_suite(9000 + n, n)
+            xd = torch.from_numpy(x).to(dev)
+            for kind in ("forward", "inverse", "roundtrip"):
+                y = plan.execute(kind, xd).cpu().numpy()
+                ref = {"forward": lambda a: oracle.forward(a, 0), "inverse": lambda a: oracle.inverse(a, 0),
+                       "roundtrip": lambda a: a.astype(np.float64)}[kind](x)
+                m = oracle.boundary_metrics(y, ref, x)
+                tot["checks"] += m["checks"]
+                tot["representable"] += m["n_representable"]
+                tot["failed"] += m["n_failed"]
+            plan.close()
+        res["range_protection_on" if protect else "range_protection_off"] = tot
     return res
 
 
