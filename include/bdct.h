@@ -206,9 +206,11 @@ int bdct_plan_get_info(const bdct_plan *plan, bdct_plan_info *info);
  * paper's two-pass structure of Eq. 2) process the batch in chunks of whole
  * arrays.  Set the chunk to about `bytes` (at least one array): the workspace
  * is reallocated to match.  A chunk that fits in L2 lets the second pass read
- * the intermediate from L2 instead of HBM.  The default is 64 MiB; the ragged
- * autotuner picks it per shape class.  No work using the plan may be queued.
- * Other variants keep no workspace and ignore the call (BDCT_OK).          */
+ * the intermediate from L2 instead of HBM, while every chunk costs two pass
+ * launches with their ramp-up and drain (which measured the larger effect).
+ * The default is 256 MiB; the ragged autotuner picks it per shape class.
+ * No work using the plan may be queued.  Other variants keep no workspace
+ * and ignore the call (BDCT_OK).                                           */
 int bdct_plan_set_chunk_bytes(bdct_plan *plan, size_t bytes);
 
 /* Synchronize the device and return the plan's device-side status: BDCT_OK,
@@ -227,16 +229,15 @@ int bdct_plan_device_status(const bdct_plan *plan, int clear);
  * Arrays are grouped by shape; each group gets a plan whose path, when `path`
  * is BDCT_PATH_AUTO, is the fastest of the accepted candidates (FP32, and the
  * on-chip split-BF16 tensor-core path where it exists; for shapes on the
- * separable route, its workspace chunk of 16, 32 or 64 MiB) timed on scratch
+ * separable route, its workspace chunk of 64, 128 or 256 MiB) timed on scratch
  * arrays at creation -- or read from the file named by the environment
  * variable BDCT_TUNE_CACHE, to which new choices are appended.  Creation
  * allocates, synchronizes and runs those timing launches.
  * Execution launches one persistent kernel (or, on the separable routes, one
  * pair of pass kernels per chunk) per shape class, reading the arrays through
  * device offset tables, from a CUDA graph captured on the first call for each
- * (kind, in_base, out_base) and replayed afterwards on `stream`; the largest
- * class is one branch of the graph and the other classes run on parallel
- * branches beside it.
+ * (kind, in_base, out_base) and replayed afterwards on `stream`, the largest
+ * class first.
  * The first call for new pointers should not itself run inside a stream
  * capture.  Calls on the same ragged plan must not overlap on the GPU.      */
 typedef struct bdct_ragged bdct_ragged;

@@ -26,9 +26,12 @@ int cuda_fail(cudaError_t e)
     return BDCT_ERR_CUDA;
 }
 
-// Workspace of the separable route: arrays per chunk are chosen so that a
-// chunk holds at least one array and about 64 MiB.
-constexpr size_t kChunkBytes = 64ull << 20;
+// Workspace of the separable routes: arrays per chunk are chosen so that a
+// chunk holds at least one array and about 256 MiB.  Every chunk costs two
+// pass launches with their ramp-up and drain: measured on 256^2 batches
+// 0.30 / 0.34 / 0.35 of HBM with 64 / 128 / 256 MiB chunks, 768 x 1024
+// batches 0.23 / 0.26 / 0.28 (bdct_plan_set_chunk_bytes changes it per plan).
+constexpr size_t kChunkBytes = 256ull << 20;
 
 }  // namespace
 
@@ -69,6 +72,7 @@ static void plan_free(bdct_plan *p)
     if (p->status) cudaFree(p->status);
     if (p->tc_ops) cudaFree(p->tc_ops);
     if (p->tg_ops) cudaFree(p->tg_ops);
+    if (p->tg_abuf) cudaFree(p->tg_abuf);
     if (p->line_tw) cudaFree(p->line_tw);
     if (p->spec_plain) cudaFree(p->spec_plain);
     if (p->spec_fold) cudaFree(p->spec_fold);
@@ -134,6 +138,20 @@ static int tg_plan_tables(bdct_plan *p)
         else p->tg_w[want[i].slot] = off_of[i];
     }
     return BDCT_OK;
+}
+
+// The input-term buffer of the warp-specialized tensor-core passes (long
+// contractions): three BF16 terms of every element of a chunk, in whole
+// 128-row tiles, for either pass.  Only plans with such an axis get one.
+static cudaError_t tg_alloc_split(bdct_plan *p)
+{
+    if (p->tg_abuf) { cudaFree(p->tg_abuf); p->tg_abuf = nullptr; }
+    if (p->tg_kron) return cudaSuccess;
+    const long long nb = p->chunk_arrays;
+    const size_t e1 = tg_split_elems(nb * p->rows, p->cols), e2 = tg_split_elems(nb * p->cols, p->rows);
+    const size_t elems = e1 > e2 ? e1 : e2;
+    if ((p->rows < 512 || p->rows % 128) && (p->cols < 512 || p->cols % 128)) return cudaSuccess;
+    return cudaMalloc(&p->tg_abuf, elems * sizeof(__nv_bfloat16));
 }
 
 extern "C" int bdct_plan_create(bdct_plan **plan, int rows, int cols, unsigned kind, int norm, int path)
@@ -227,6 +245,8 @@ extern "C" int bdct_plan_create(bdct_plan **plan, int rows, int cols, unsigned k
         p->chunk_arrays = chunk;
         p->work_bytes = (size_t)chunk * arr_bytes;
         e = cudaMalloc(&p->work, p->work_bytes);
+        if (e != cudaSuccess) { plan_free(p); t_last_cuda_error = (int)e; return BDCT_ERR_NO_MEMORY; }
+        e = tg_alloc_split(p);
         if (e != cudaSuccess) { plan_free(p); t_last_cuda_error = (int)e; return BDCT_ERR_NO_MEMORY; }
     } else if (fused_supported(rows, cols)) {
         p->variant = 1;
@@ -445,11 +465,11 @@ static cudaError_t tg_direction(const bdct_plan *p, int slot, const float *src, 
 {
     const int h = p->rows, w = p->cols;
     if (p->tg_kron)
-        return tg_pass(src, dst, src_off, dst_off, nb, 1, 64, p->tg_ops + p->tg_h[slot], p->tc_terms, lam, p->status, s);
+        return tg_pass(src, dst, src_off, dst_off, nb, 1, 64, p->tg_ops + p->tg_h[slot], p->tc_terms, lam, p->tg_abuf, p->status, s);
     cudaError_t e = tg_pass(src, p->work, src_off, nullptr, nb, h, w, p->tg_ops + p->tg_w[slot], p->tc_terms, nullptr,
-                            p->status, s);
+                            p->tg_abuf, p->status, s);
     if (e == cudaSuccess)
-        e = tg_pass(p->work, dst, nullptr, dst_off, nb, w, h, p->tg_ops + p->tg_h[slot], p->tc_terms, lam, p->status, s);
+        e = tg_pass(p->work, dst, nullptr, dst_off, nb, w, h, p->tg_ops + p->tg_h[slot], p->tc_terms, lam, p->tg_abuf, p->status, s);
     return e;
 }
 
@@ -469,7 +489,7 @@ static int run_tg(const bdct_plan *p, Dir dir, const float *in, const long long 
             const int slot = dir == DIR_FWD ? 0 : 1;
             if (p->tg_kron && inplace) {
                 // one pass cannot run in place: through the workspace
-                e = tg_pass(src, p->work, so, nullptr, nb, 1, 64, p->tg_ops + p->tg_h[slot], p->tc_terms, nullptr,
+                e = tg_pass(src, p->work, so, nullptr, nb, 1, 64, p->tg_ops + p->tg_h[slot], p->tc_terms, nullptr, p->tg_abuf,
                             p->status, s);
                 ExecGeom g{p->work, dst, nb, 0, 0, 0, 0, nullptr, dof};
                 if (e == cudaSuccess) e = copy_arrays(p->work, g, p->rows, p->cols, s);
@@ -480,10 +500,10 @@ static int run_tg(const bdct_plan *p, Dir dir, const float *in, const long long 
             // round trip / spectral: orthonormal forward (times Lambda), then the inverse
             const float *lam = dir == DIR_SPEC ? p->spec_plain : nullptr;
             if (p->tg_kron) {
-                e = tg_pass(src, p->work, so, nullptr, nb, 1, 64, p->tg_ops + p->tg_h[2], p->tc_terms, lam, p->status, s);
+                e = tg_pass(src, p->work, so, nullptr, nb, 1, 64, p->tg_ops + p->tg_h[2], p->tc_terms, lam, p->tg_abuf, p->status, s);
                 if (e == cudaSuccess)
                     e = tg_pass(p->work, dst, nullptr, dof, nb, 1, 64, p->tg_ops + p->tg_h[3], p->tc_terms, nullptr,
-                                p->status, s);
+                                p->tg_abuf, p->status, s);
             } else {
                 e = tg_direction(p, 2, src, so, dst, dof, nb, lam, s);
                 if (e == cudaSuccess) e = tg_direction(p, 3, dst, dof, dst, dof, nb, nullptr, s);
@@ -733,6 +753,10 @@ extern "C" int bdct_plan_set_chunk_bytes(bdct_plan *plan, size_t bytes)
         plan->work = w;
         plan->work_bytes = need;
         plan->chunk_arrays = chunk;
+        if (plan->variant == 4 && (e = tg_alloc_split(plan)) != cudaSuccess) {
+            t_last_cuda_error = (int)e;
+            st = BDCT_ERR_NO_MEMORY;
+        }
     }
     if (cur >= 0 && cur != plan->device) cudaSetDevice(cur);
     return st;

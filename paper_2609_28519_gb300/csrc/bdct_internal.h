@@ -185,9 +185,14 @@ cudaError_t tg_gen_table(__nv_bfloat16 *dst, int n, int direction, int norm, boo
 // (arrays of K x R; R = 1 writes dst[b][n]).  src_off / dst_off index the
 // arrays (element offsets) or are null for contiguous arrays; lam, if not
 // null, multiplies output (n, r) by lam[n * R + r].  src != dst.
+// Long contractions (K >= 512, a multiple of 128) first split the input into
+// abuf (tg_split_elems(count * R, K) BF16 elements of plan workspace), then
+// run the warp-specialized kernel; shorter ones split in the kernel (abuf
+// unused, may be null).
 cudaError_t tg_pass(const float *src, float *dst, const long long *src_off, const long long *dst_off, long long count,
-                    int R, int K, const __nv_bfloat16 *ops, int terms, const float *lam, unsigned int *status,
-                    cudaStream_t stream);
+                    int R, int K, const __nv_bfloat16 *ops, int terms, const float *lam, __nv_bfloat16 *abuf,
+                    unsigned int *status, cudaStream_t stream);
+size_t tg_split_elems(long long rows, int K);
 
 // ---- dense_passes.cu
 // Separable dense passes through a workspace, any shape.  `op_h`, `op_w` are

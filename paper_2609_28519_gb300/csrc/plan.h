@@ -38,6 +38,7 @@ struct bdct_plan {
     __nv_bfloat16 *tg_ops = nullptr;
     size_t tg_h[4] = {0, 0, 0, 0}, tg_w[4] = {0, 0, 0, 0};
     bool tg_kron = false;  // 8 x 8: one pass with the 64 x 64 Kronecker operator
+    __nv_bfloat16 *tg_abuf = nullptr;  // input terms of the long-contraction kernel
     // spectral direction (bdct_plan_set_spectral): Lambda in FP32, and Lambda
     // folded with the squared scales for the unscaled fused cores (Prop. 1)
     float *spec_plain = nullptr, *spec_fold = nullptr;

@@ -96,11 +96,6 @@ struct bdct_ragged {
     int norm = 0;
     std::vector<RaggedClass> classes;  // largest first
     cudaStream_t capture = nullptr;
-    // side streams and events of the captured graph: the largest class runs
-    // on one branch, the others on parallel branches beside it
-    static constexpr int kBranches = 4;
-    cudaStream_t side[kBranches] = {};
-    cudaEvent_t fork = nullptr, join[kBranches] = {};
     std::mutex mu;
     std::vector<GraphEntry> graphs;
 };
@@ -115,11 +110,6 @@ static void ragged_free(bdct_ragged *r)
         if (c.plan) bdct_plan_destroy(c.plan);
     }
     if (r->capture) cudaStreamDestroy(r->capture);
-    for (int i = 0; i < bdct_ragged::kBranches; ++i) {
-        if (r->side[i]) cudaStreamDestroy(r->side[i]);
-        if (r->join[i]) cudaEventDestroy(r->join[i]);
-    }
-    if (r->fork) cudaEventDestroy(r->fork);
     delete r;
 }
 
@@ -153,9 +143,11 @@ static int time_plan(bdct_plan *plan, unsigned kind_mask, float *d_in, float *d_
 
 // Pick and create the plan of one class: the accepted candidate paths (FP32,
 // and the on-chip split-BF16 tensor-core route where it exists), and for a
-// separable route the workspace chunk (16, 32 or 64 MiB: small enough for
-// the intermediate to stay in L2 between the passes, or large enough to keep
-// the launches few), each timed on scratch arrays of the class's shape.
+// separable route the workspace chunk (64, 128 or 256 MiB: every chunk
+// costs two launches with their ramp-up and drain, which measured more than
+// keeping the intermediate in L2 -- 256^2 batches ran at 0.19 / 0.31 / 0.34
+// of HBM with 8 / 64 / 128 MiB chunks), each timed on scratch arrays of the
+// class's shape.
 static int class_plan(RaggedClass &c, unsigned kind, int norm, int path)
 {
     const bool tc_ok = tc_supported(c.rows, c.cols);
@@ -165,8 +157,8 @@ static int class_plan(RaggedClass &c, unsigned kind, int norm, int path)
     }
     const long long arr = (long long)c.rows * c.cols;
     const bool separable = !fused_supported(c.rows, c.cols);
-    // scratch: 32 MiB, or 256 MiB where chunk sizes are compared
-    long long n = ((separable ? 256ll : 32ll) << 20) / (arr * 4);
+    // scratch: 32 MiB, or 512 MiB where chunk sizes are compared
+    long long n = ((separable ? 512ll : 32ll) << 20) / (arr * 4);
     if (n < 1) n = 1;
     if (n > (long long)c.in_off.size()) n = (long long)c.in_off.size();
     float *d_in = nullptr, *d_out = nullptr;
@@ -181,7 +173,7 @@ static int class_plan(RaggedClass &c, unsigned kind, int norm, int path)
     if (cache_lookup(c.rows, c.cols, kind, norm, &cached, &cached_mb)) {
         cands.push_back({cached, cached_mb});
     } else if (separable) {
-        for (size_t mb : {16, 32, 64}) cands.push_back({BDCT_PATH_FP32, mb});
+        for (size_t mb : {64, 128, 256}) cands.push_back({BDCT_PATH_FP32, mb});
     } else {
         cands.push_back({BDCT_PATH_FP32, 0});
         if (tc_ok) cands.push_back({BDCT_PATH_SPLIT_TC, 0});
@@ -280,53 +272,28 @@ extern "C" int bdct_ragged_create(bdct_ragged **out, size_t n, const int *rows, 
             return BDCT_ERR_CUDA;
         }
     }
-    if (cudaStreamCreateWithFlags(&r->capture, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&r->fork, cudaEventDisableTiming) != cudaSuccess) {
+    if (cudaStreamCreateWithFlags(&r->capture, cudaStreamNonBlocking) != cudaSuccess) {
         ragged_free(r);
         return BDCT_ERR_CUDA;
     }
-    for (int i = 0; i < bdct_ragged::kBranches; ++i)
-        if (cudaStreamCreateWithFlags(&r->side[i], cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&r->join[i], cudaEventDisableTiming) != cudaSuccess) {
-            ragged_free(r);
-            return BDCT_ERR_CUDA;
-        }
     if (cudaDeviceSynchronize() != cudaSuccess) { ragged_free(r); return BDCT_ERR_CUDA; }
     *out = r;
     return BDCT_OK;
 }
 
-// Record every class's launch into the capture stream's graph: the largest
-// class on the capture stream itself, the others round robin on side
-// streams forked from it and joined back, so that the graph holds parallel
-// branches and the small classes can fill SMs the large class leaves idle.
+// Record every class's launch, largest class first, into the capture
+// stream's graph.  (Parallel graph branches per class, on side streams forked
+// from the capture stream, measured slower on the 4096-array workload: 0.217
+// to 0.229 of HBM against 0.241 serial -- every class kernel is persistent
+// and sized to fill the GPU, so branches only contend.)
 static int ragged_launch_all(const bdct_ragged *r, Dir dir, const float *in, float *out)
 {
-    const int nb = bdct_ragged::kBranches;
-    if (cudaEventRecord(r->fork, r->capture) != cudaSuccess) return BDCT_ERR_CUDA;
-    bool used[bdct_ragged::kBranches] = {};
-    int st = BDCT_OK;
-    for (size_t i = 0; i < r->classes.size() && st == BDCT_OK; ++i) {
-        const auto &c = r->classes[i];
-        cudaStream_t s = r->capture;
-        if (i > 0) {
-            const int b = (int)((i - 1) % nb);
-            s = r->side[b];
-            if (!used[b]) {
-                if (cudaStreamWaitEvent(s, r->fork, 0) != cudaSuccess) return BDCT_ERR_CUDA;
-                used[b] = true;
-            }
-        }
-        st = plan_execute(c.plan, dir, in, c.d_in_off, out, c.d_out_off, (long long)c.in_off.size(), s);
+    for (const auto &c : r->classes) {
+        const int st = plan_execute(c.plan, dir, in, c.d_in_off, out, c.d_out_off, (long long)c.in_off.size(),
+                                    r->capture);
+        if (st != BDCT_OK) return st;
     }
-    // join every branch that was used (also on error, so that the capture can end)
-    for (int b = 0; b < nb; ++b)
-        if (used[b]) {
-            if (cudaEventRecord(r->join[b], r->side[b]) != cudaSuccess ||
-                cudaStreamWaitEvent(r->capture, r->join[b], 0) != cudaSuccess)
-                st = BDCT_ERR_CUDA;
-        }
-    return st;
+    return BDCT_OK;
 }
 
 extern "C" int bdct_ragged_execute(bdct_ragged *r, unsigned kind, const float *in_base, float *out_base,

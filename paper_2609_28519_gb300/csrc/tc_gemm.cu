@@ -297,6 +297,247 @@ __global__ void __launch_bounds__(128) k_tcg(const TgParams p)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS) : "memory");
 }
 
+// ------------------------------------------------------------ warp-specialized kernel
+// For long contractions the in-kernel split above re-splits every input row
+// once per output tile and occupies the CUDA cores the whole time.  There the
+// pass runs in two kernels: k_tg_presplit writes the three BF16 terms of the
+// input once, already in the blocked canonical layout (block (row tile, K
+// chunk) = three 128 x KC K-major terms), and k_tcg2 streams both operands
+// with bulk copies:
+//   warp 0, lane 0: producer -- one bulk copy of the input terms and one of
+//     the operator terms per chunk into a two-stage ring (full / empty
+//     mbarriers);
+//   warp 1, lane 0: issues the six products of a chunk into one of two TMEM
+//     partial accumulators and commits them twice (stage free, partial ready);
+//   warps 2-5: each reads its TMEM lane quadrant (warp % 4) of a finished
+//     partial, adds it to its row's running sums in registers (round to
+//     nearest, chunk order), releases the partial, and at the end of a tile
+//     stores the row transposed.
+// Tiles are 128 rows by 128 outputs, K chunks of 64.
+
+// Split src rows into the blocked BF16 terms: thread t of a group of eight
+// takes row (8 q + t % 8) of a core matrix, so that eight lanes write one
+// 128-byte core matrix and each lane reads one 32-byte sector.
+template <int TERMS>
+__global__ void k_tg_presplit(const float *src, const long long *src_off, long long rows_total, int R, int K, int KC,
+                              long long m_tiles, __nv_bfloat16 *abuf)
+{
+    const int nk = K / KC;
+    const int groups = KC / 8;                       // 8-column groups per chunk row
+    const long long per_tile = 128LL * K / 8;        // work units per row tile
+    const long long total = m_tiles * per_tile;
+    for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < total;
+         u += (long long)gridDim.x * blockDim.x) {
+        const long long mt = u / per_tile;
+        long long rem = u - mt * per_tile;
+        const int r8 = (int)(rem & 7);               // row within the core matrix
+        rem >>= 3;
+        const int kc = (int)(rem / (16LL * groups)); // chunk
+        rem -= (long long)kc * 16 * groups;
+        const int g = (int)(rem % groups);           // 8-column group within the chunk
+        const int rq = (int)(rem / groups);          // core-matrix row block (0..15)
+        const int row = rq * 8 + r8;                 // row within the tile
+        const long long m = mt * 128 + row;
+        float v[8];
+        if (m < rows_total) {
+            const long long b = m / R, r = m - b * R;
+            const float *q = src + (src_off ? src_off[b] : b * (long long)R * K) + r * K + (long long)kc * KC + 8 * g;
+            const float4 t0 = __ldg(reinterpret_cast<const float4 *>(q));
+            const float4 t1 = __ldg(reinterpret_cast<const float4 *>(q) + 1);
+            v[0] = t0.x; v[1] = t0.y; v[2] = t0.z; v[3] = t0.w;
+            v[4] = t1.x; v[5] = t1.y; v[6] = t1.z; v[7] = t1.w;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = 0.0f;
+        }
+        __nv_bfloat16 t[TERMS][8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            __nv_bfloat16 sp[3];
+            split3<TERMS>(v[e], sp);
+#pragma unroll
+            for (int tt = 0; tt < TERMS; ++tt) t[tt][e] = sp[tt];
+        }
+        uint8_t *blk = reinterpret_cast<uint8_t *>(abuf) + (mt * nk + kc) * (3LL * 128 * KC * 2);
+        const int off = kmaj_off_bytes(row, 8 * g, KC);
+#pragma unroll
+        for (int tt = 0; tt < TERMS; ++tt)
+            *reinterpret_cast<uint4 *>(blk + (long long)tt * 128 * KC * 2 + off) = *reinterpret_cast<const uint4 *>(t[tt]);
+    }
+}
+
+constexpr int kTg2NT = 128;
+constexpr int kTg2Stages = 2;
+constexpr int kTg2AStage = 3 * 128 * kTgKC * 2;       // bytes of the input terms of a chunk
+constexpr int kTg2BStage = 3 * kTg2NT * kTgKC * 2;    // bytes of the operator terms of a chunk
+constexpr int kTg2Stage = kTg2AStage + kTg2BStage;
+constexpr size_t kTg2Smem = (size_t)kTg2Stages * kTg2Stage + 16 * 8 + 16;
+
+struct Tg2Params {
+    const __nv_bfloat16 *abuf;       // input terms, [row tile][chunk][term][128 x KC]
+    const __nv_bfloat16 *ops;        // operator terms, [n tile][chunk][term][128 x KC]
+    float *dst;
+    const long long *dst_off;
+    long long rows_total;
+    int R, N, KC, nk, n_tiles;
+    long long items;
+    const float *lam;
+    unsigned int *status;
+};
+
+template <int TERMS>
+__global__ void __launch_bounds__(192, 1) k_tcg2(const Tg2Params p)
+{
+    extern __shared__ __align__(1024) uint8_t t2s[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(t2s + kTg2Stages * kTg2Stage);
+    uint64_t *empty = full + kTg2Stages;
+    uint64_t *pfull = empty + kTg2Stages;   // partial accumulator ready
+    uint64_t *pempty = pfull + 2;           // partial accumulator read
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(pempty + 2);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int s = 0; s < kTg2Stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&pfull[a], 1);
+            mbar_init(&pempty[a], 4);  // one arrival per epilogue warp
+        }
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(2 * kTg2NT)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    pdl_launch_dependents();
+    pdl_wait_prerequisites();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int KC = p.KC, nk = p.nk;
+    const uint32_t a_term = 128u * KC * 2, b_term = (uint32_t)kTg2NT * KC * 2;
+    const long long blk_elems = 3LL * 128 * KC;  // input and operator blocks alike (NT = 128)
+    long long last_load = -1, last_commit = -1;  // error path: the last copy and commit issued
+    bool ok = true;
+
+    if (warp == 0) {
+        // ---- producer
+        if (lane == 0) {
+            long long c = 0;
+            for (long long item = blockIdx.x; ok && item < p.items; item += gridDim.x) {
+                const long long mt = item / p.n_tiles;
+                const int nt = (int)(item % p.n_tiles);
+                for (int kc = 0; kc < nk; ++kc, ++c) {
+                    const int s = (int)(c % kTg2Stages);
+                    const uint32_t use = (uint32_t)(c / kTg2Stages);
+                    if (c >= kTg2Stages && !mbar_wait_bounded(&empty[s], (use - 1) & 1u)) { ok = false; break; }
+                    if (*abort_flag) { ok = false; break; }
+                    uint8_t *st = t2s + s * kTg2Stage;
+                    mbar_arrive_expect_tx(&full[s], (uint32_t)TERMS * (a_term + b_term));
+                    bulk_load(st, p.abuf + (mt * nk + kc) * blk_elems, (uint32_t)TERMS * a_term, &full[s]);
+                    bulk_load(st + kTg2AStage, p.ops + ((long long)nt * nk + kc) * blk_elems, (uint32_t)TERMS * b_term,
+                              &full[s]);
+                    last_load = c;
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---- MMA issue
+        if (lane == 0) {
+            constexpr uint32_t idesc = tc_idesc(kTg2NT, false);
+            const uint32_t sbo = (uint32_t)(KC / 8) * 128u;
+            constexpr int pa[6] = {2, 1, 0, 1, 0, 0};
+            constexpr int pb[6] = {0, 1, 2, 0, 1, 0};
+            constexpr int first = TERMS == 3 ? 0 : (TERMS == 2 ? 3 : 5);
+            long long c = 0;
+            for (long long item = blockIdx.x; ok && item < p.items; item += gridDim.x) {
+                for (int kc = 0; kc < nk; ++kc, ++c) {
+                    const int s = (int)(c % kTg2Stages), a = (int)(c & 1);
+                    if (!mbar_wait_bounded(&full[s], (uint32_t)(c / kTg2Stages) & 1u)) { ok = false; break; }
+                    if (c >= 2 && !mbar_wait_bounded(&pempty[a], (uint32_t)((c >> 1) - 1) & 1u)) { ok = false; break; }
+                    if (*abort_flag) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t a0 = smem_u32(t2s + s * kTg2Stage), b0 = a0 + kTg2AStage;
+                    const uint32_t d = tmem + (uint32_t)(a * kTg2NT);
+#pragma unroll
+                    for (int pr = first; pr < 6; ++pr)
+                        for (int ks = 0; ks < KC / 16; ++ks)
+                            tc_mma(d, smem_desc(a0 + pa[pr] * a_term + ks * 256, 128, sbo),
+                                   smem_desc(b0 + pb[pr] * b_term + ks * 256, 128, sbo), idesc,
+                                   (pr > first || ks > 0) ? 1u : 0u);
+                    tc_commit(&empty[s]);
+                    tc_commit(&pfull[a]);
+                    last_commit = c;
+                }
+            }
+        }
+    } else {
+        // ---- epilogue: TMEM lane quadrant q of every partial
+        const int q = warp & 3;
+        const int row = 32 * q + lane;
+        const uint32_t lane_off = (uint32_t)(32 * q) << 16;
+        float sum[kTg2NT];
+#pragma unroll
+        for (int j = 0; j < kTg2NT; ++j) sum[j] = 0.0f;
+        long long c = 0;
+        for (long long item = blockIdx.x; ok && item < p.items; item += gridDim.x) {
+            for (int kc = 0; kc < nk; ++kc, ++c) {
+                const int a = (int)(c & 1);
+                bool w = mbar_wait_bounded(&pfull[a], (uint32_t)(c >> 1) & 1u);
+                w = __all_sync(0xffffffffu, w);
+                if (!w) { ok = false; break; }
+                tc_fence_after();
+#pragma unroll
+                for (int cc = 0; cc < kTg2NT / 16; ++cc) {
+                    float y[16];
+                    tmem_ld16(tmem + (uint32_t)(a * kTg2NT) + lane_off + 16 * cc, y);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) sum[16 * cc + j] += y[j];
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&pempty[a]);
+            }
+            if (!ok) break;
+            const long long m = (item / p.n_tiles) * 128 + row;
+            if (m < p.rows_total) {
+                const long long b = m / p.R, r = m - b * p.R;
+                float *dbase = p.dst + (p.dst_off ? p.dst_off[b] : b * (long long)p.N * p.R);
+                const int n0 = (int)(item % p.n_tiles) * kTg2NT;
+                if (p.lam) {
+#pragma unroll
+                    for (int j = 0; j < kTg2NT; ++j) sum[j] *= __ldg(p.lam + (long long)(n0 + j) * p.R + r);
+                }
+#pragma unroll
+                for (int j = 0; j < kTg2NT; ++j) dbase[(long long)(n0 + j) * p.R + r] = sum[j];
+            }
+#pragma unroll
+            for (int j = 0; j < kTg2NT; ++j) sum[j] = 0.0f;
+        }
+    }
+    if (!ok) {
+        *abort_flag = 1;
+        if (lane == 0) record_timeout(p.status);
+    }
+    // error path: the issuing lanes wait (bounded) for their last copy and
+    // their last products before the CTA releases shared memory and TMEM
+    if (warp == 0 && lane == 0 && last_load >= 0)
+        mbar_wait_bounded(&full[last_load % kTg2Stages], (uint32_t)(last_load / kTg2Stages) & 1u);
+    if (warp == 1 && lane == 0 && last_commit >= 0)
+        mbar_wait_bounded(&pfull[last_commit & 1], (uint32_t)(last_commit >> 1) & 1u);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTg2NT) : "memory");
+}
+
 // ------------------------------------------------------------ operator tables
 // Operator M (N = K = n, or the 64 x 64 Kronecker operator of 8 x 8 arrays)
 // for direction 1 (forward: M[f][j] = s_f cos(pi (2j+1) f / 2n)) or 2
@@ -350,10 +591,18 @@ __global__ void k_gen_tg_op(__nv_bfloat16 *dst, int N, int K, int direction, int
     dst[base + 2LL * NT * KC] = t2;
 }
 
-// Tile width for an output length: the largest of 64, 32, 16 dividing it (a
-// thread holds its row of the tile in registers across the K loop).
+// Contractions of at least this length run on the warp-specialized kernel
+// (input split beforehand, 128-wide tiles); shorter ones split in the kernel.
+constexpr int kTg2MinK = 512;
+
+static bool tg_use_v2(int n) { return n >= kTg2MinK && n % 128 == 0; }
+
+// Tile width for an output length: 128 on the warp-specialized kernel, else
+// the largest of 64, 32, 16 dividing it (a thread of the single-role kernel
+// holds its row of the tile in registers across the K loop).
 static int tg_nt(int n)
 {
+    if (tg_use_v2(n)) return 128;
     for (int nt : {64, 32, 16})
         if (n % nt == 0) return nt;
     return 0;
@@ -438,15 +687,93 @@ static cudaError_t tg_launch_nt(int terms, const TgParams &p, cudaStream_t s)
     }
 }
 
+size_t tg_split_elems(long long rows, int K)
+{
+    const long long m_tiles = (rows + 127) / 128;
+    return (size_t)m_tiles * 128 * (size_t)K * 3;
+}
+
+template <int TERMS>
+static cudaError_t tg2_launch(const float *src, const long long *src_off, const Tg2Params &p0, int K,
+                              __nv_bfloat16 *abuf, cudaStream_t stream)
+{
+    static DeviceLaunchCache cache;
+    int dev = 0, bps = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    auto kern = k_tcg2<TERMS>;
+    e = cache.get(
+        dev,
+        [&](int d, int &b, int &n) {
+            cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTg2Smem);
+            if (r == cudaSuccess) r = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d);
+            b = 1;
+            if (r == cudaSuccess && debug_enabled())
+                fprintf(stderr, "[bdct] k_tcg2<%d>: 1 CTA/SM x 192 threads, smem %zu B, TMEM %d cols\n", TERMS,
+                        kTg2Smem, 2 * kTg2NT);
+            return r;
+        },
+        &bps, &sms);
+    if (e != cudaSuccess) return e;
+    Tg2Params p = p0;
+    const long long m_tiles = (p.rows_total + 127) / 128;
+    // 1. the input's BF16 terms, once
+    {
+        const long long work = m_tiles * 128LL * K / 8;
+        long long blocks = (work + 255) / 256;
+        if (blocks > (long long)sms * 16) blocks = (long long)sms * 16;
+        k_tg_presplit<TERMS><<<(unsigned)blocks, 256, 0, stream>>>(src, src_off, p.rows_total, p.R, K, p.KC, m_tiles,
+                                                                    abuf);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    // 2. the products, persistent CTAs over the tiles
+    p.abuf = abuf;
+    long long grid = (long long)sms;
+    if (grid > p.items) grid = p.items;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(192);
+    cfg.dynamicSmemBytes = kTg2Smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, p);
+}
+
 cudaError_t tg_pass(const float *src, float *dst, const long long *src_off, const long long *dst_off, long long count,
-                    int R, int K, const __nv_bfloat16 *ops, int terms, const float *lam, unsigned int *status,
-                    cudaStream_t stream)
+                    int R, int K, const __nv_bfloat16 *ops, int terms, const float *lam, __nv_bfloat16 *abuf,
+                    unsigned int *status, cudaStream_t stream)
 {
     if (count <= 0) return cudaSuccess;
     const int N = K;  // square 1D operators (the Kronecker one included)
     const int NT = tg_nt(N), KC = tg_kc(K);
     if (!NT || !KC || R < 1) return cudaErrorInvalidValue;
     if (src == dst) return cudaErrorInvalidValue;  // a pass never runs in place
+    if (tg_use_v2(K)) {
+        if (!abuf) return cudaErrorInvalidValue;
+        Tg2Params p{};
+        p.ops = ops;
+        p.dst = dst;
+        p.dst_off = dst_off;
+        p.rows_total = count * R;
+        p.R = R;
+        p.N = N;
+        p.KC = KC;
+        p.nk = K / KC;
+        p.n_tiles = N / kTg2NT;
+        p.items = ((p.rows_total + 127) / 128) * p.n_tiles;
+        p.lam = lam;
+        p.status = status;
+        switch (terms) {
+            case 3: return tg2_launch<3>(src, src_off, p, K, abuf, stream);
+            case 2: return tg2_launch<2>(src, src_off, p, K, abuf, stream);
+            default: return tg2_launch<1>(src, src_off, p, K, abuf, stream);
+        }
+    }
     TgParams p{};
     p.src = src;
     p.dst = dst;
