@@ -185,7 +185,7 @@ cudaError_t tg_gen_table(__nv_bfloat16 *dst, int n, int direction, int norm, boo
 // (arrays of K x R; R = 1 writes dst[b][n]).  src_off / dst_off index the
 // arrays (element offsets) or are null for contiguous arrays; lam, if not
 // null, multiplies output (n, r) by lam[n * R + r].  src != dst.
-// Long contractions (K >= 512, a multiple of 128) first split the input into
+// Long contractions (K a multiple of 128) first split the input into
 // abuf (tg_split_elems(count * R, K) BF16 elements of plan workspace), then
 // run the warp-specialized kernel; shorter ones split in the kernel (abuf
 // unused, may be null).

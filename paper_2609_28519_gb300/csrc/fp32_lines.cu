@@ -1,5 +1,6 @@
 // FFT-based FP32 line engine: one separable pass of the 2D DCT for long
-// lines (64 .. 4096 points, powers of two, and 768 = 3 * 2^8).
+// lines (64 .. 4096 points, powers of two, and 192, 384, 768, 1536 =
+// 3 * 2^6 .. 3 * 2^9: the half-length FFT takes one radix-3 stage).
 //
 // What is computed: the 1D factor of Eq. 2 of the BRiDCT paper along every
 // row of a batch of arrays -- y_k = s_k sum_j x_j cos(pi (2j+1) k / (2N))
@@ -40,7 +41,8 @@ cudaError_t lines_init_table3(const float *d_table) { return init_cos_table3(d_t
 
 bool lines_supported(int n)
 {
-    return n == 64 || n == 128 || n == 256 || n == 512 || n == 1024 || n == 2048 || n == 4096 || n == 768;
+    return n == 64 || n == 128 || n == 256 || n == 512 || n == 1024 || n == 2048 || n == 4096 || n == 192 ||
+           n == 384 || n == 768 || n == 1536;
 }
 
 // Four-step split L = N/2 = L1 * L2 (step A: L2 FFTs of length L1, step C:
@@ -50,9 +52,10 @@ template <int N>
 struct LineCfg {
     static constexpr int L = N / 2;
     static constexpr int L1 = N == 64 ? 4 : N == 128 ? 8 : N == 256 ? 8 : N == 512 ? 16 : N == 1024 ? 16
-                            : N == 768 ? 24 : 32;
+                            : (N == 192 || N == 384) ? 12 : N == 768 ? 24 : N == 1536 ? 48 : 32;
     static constexpr int L2 = L / L1;
-    static constexpr int T = N == 64 ? 4 : (N == 128 || N == 256 || N == 768) ? 8 : (N == 512 || N == 1024) ? 16 : 32;
+    static constexpr int T = (N == 64 || N == 192 || N == 384) ? 4 : (N == 128 || N == 256 || N == 768) ? 8
+                           : (N == 512 || N == 1024 || N == 1536) ? 16 : 32;
     static constexpr int JA = L2 / T;  // step-A sub-FFTs per thread
     static constexpr int JC = L1 / T;  // step-C sub-FFTs per thread
     static constexpr int LPW = 32 / T;  // lines per warp
@@ -62,7 +65,7 @@ struct LineCfg {
     // Rows per panel.  For T < 16 a half-warp holds several lines; they sit T
     // rows apart (rows 32 b + w + T sub of a 32-row block, w < T), which with a
     // row pitch of 2 mod 32 floats puts them 2T banks apart.
-    static constexpr int PR = T < 16 ? (T == 4 ? 64 : 32) : (N <= 1024 ? 16 : (N == 2048 ? 8 : 4));
+    static constexpr int PR = T < 16 ? (T == 4 ? 64 : 32) : (N <= 1536 ? 16 : (N == 2048 ? 8 : 4));
     static constexpr int ROUNDS = PR / LPR;
     // With L2 >= 16 both FFT steps run in place in the line buffer: step A's
     // results are held in registers across a warp barrier and written back
@@ -455,9 +458,10 @@ __global__ void __launch_bounds__(LineCfg<N>::THREADS) k_lines(const LinesParams
     // panel is transformed, so the global-load latency overlaps the work.
     constexpr int V4 = N / 4;
     constexpr int ITER = C::PR * V4 / C::THREADS;
-    // (768-point inverse and round trip lines already hold 48 complex values)
-    constexpr bool PREFETCH = N <= 2048 && !(N == 768 && DIR != DIR_FWD);
-    constexpr int NB = PREFETCH ? ITER : (ITER < 8 ? ITER : 8);
+    // (lines with a radix-3 stage hold 48 complex values through the split:
+    // only the 768-point forward keeps the prefetch, measured)
+    constexpr bool PREFETCH = N <= 2048 && (N % 3 != 0 || (N == 768 && DIR == DIR_FWD));
+    constexpr int NB = PREFETCH ? ITER : (ITER <= 8 ? ITER : (ITER % 8 == 0 ? 8 : (ITER % 6 == 0 ? 6 : 4)));
     static_assert(ITER * C::THREADS == C::PR * V4 && ITER % NB == 0, "load batches");
     auto panel_src = [&](int pn, long long &b, int &rr) -> const float4 * {
         if (p.reverse) pn = p.npanels - 1 - pn;
@@ -653,7 +657,10 @@ static int line_l1(int n)
         case 1024: return LineCfg<1024>::L1;
         case 2048: return LineCfg<2048>::L1;
         case 4096: return LineCfg<4096>::L1;
+        case 192: return LineCfg<192>::L1;
+        case 384: return LineCfg<384>::L1;
         case 768: return LineCfg<768>::L1;
+        case 1536: return LineCfg<1536>::L1;
         default: return 0;
     }
 }
@@ -690,7 +697,10 @@ cudaError_t lines_pass(const float *src, float *dst, int rows, int n, long long 
         case 1024: return lines_dir<1024>(dir, p, stream);
         case 2048: return lines_dir<2048>(dir, p, stream);
         case 4096: return lines_dir<4096>(dir, p, stream);
+        case 192: return lines_dir<192>(dir, p, stream);
+        case 384: return lines_dir<384>(dir, p, stream);
         case 768: return lines_dir<768>(dir, p, stream);
+        case 1536: return lines_dir<1536>(dir, p, stream);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -593,7 +593,7 @@ __global__ void k_gen_tg_op(__nv_bfloat16 *dst, int N, int K, int direction, int
 
 // Contractions of at least this length run on the warp-specialized kernel
 // (input split beforehand, 128-wide tiles); shorter ones split in the kernel.
-constexpr int kTg2MinK = 512;
+constexpr int kTg2MinK = 128;
 
 static bool tg_use_v2(int n) { return n >= kTg2MinK && n % 128 == 0; }
 

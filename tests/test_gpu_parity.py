@@ -777,3 +777,18 @@ def test_range_protection_boundary_suite(oracle_mod, cuda_dev, record_property):
     m = oracle_mod.boundary_metrics(inputs.image_to_blocks(out.cpu().numpy(), 16, 16), oracle_mod.forward(blocks, 0),
                                     blocks)
     assert m["n_failed"] == 0
+
+
+@pytest.mark.parametrize("h,w", [(192, 192), (384, 384), (1536, 1536), (384, 1536), (1536, 192), (192, 1024),
+                                 (768, 384)])
+@pytest.mark.parametrize("norm", [0, 1])
+def test_radix3_lines_against_oracle(oracle_mod, cuda_dev, h, w, norm):
+    """Sides 3 * 2^k (192, 384, 768, 1536) on the FFT line engine (one radix-3
+    stage in the half-length FFT), alone and mixed with powers of two."""
+    from paper_2609_28519_gb300 import Plan
+    plan = Plan(h, w, norm=norm, path="fp32")
+    assert plan.info().variant == 2
+    x = inputs.gaussian(9500 + h + 3 * w + norm, 2 if h * w <= 1 << 20 else 1, h, w)
+    for kind in KINDS:
+        y = _run(plan, kind, x, cuda_dev)
+        _assert_parity(oracle_mod, y, _ref(oracle_mod, kind, x, norm), x, norm, kind, ("radix3", h, w, norm, kind))
