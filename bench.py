@@ -761,7 +761,9 @@ def run_profile(args):
     x = torch.from_numpy(inputs.uniform(3, batch, h, w)).to(dev)
     y = torch.empty_like(x)
     plan = Plan(h, w, path=args.path)
-    fn = {"f": plan.forward, "i": plan.inverse, "r": plan.roundtrip}[args.kind]
+    if args.kind == "s":
+        plan.set_spectral(inputs.poisson_diagonal(h, w))
+    fn = {"f": plan.forward, "i": plan.inverse, "r": plan.roundtrip, "s": plan.spectral}[args.kind]
     for _ in range(args.warmup):
         fn(x, out=y)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -796,7 +798,8 @@ def main():
     ap.add_argument("--mib", type=int, default=512, help="input MiB per sweep run")
     ap.add_argument("--workload", default="image", choices=["image", "ragged", "large", "profile"])
     ap.add_argument("--shape", default="64x64", help="profile workload: rows x cols")
-    ap.add_argument("--kind", default="f", choices=["f", "i", "r"], help="profile workload: direction")
+    ap.add_argument("--kind", default="f", choices=["f", "i", "r", "s"],
+                    help="profile workload: direction (s: spectral, Poisson diagonal)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
