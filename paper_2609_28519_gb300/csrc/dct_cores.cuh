@@ -327,6 +327,39 @@ __device__ __forceinline__ void line_spectral(float (&x)[N], const float (&d)[N]
     DCT3<N, float>::run(y, x);
 }
 
+// line_spectral on two lines a and b held as plain float arrays, each with
+// its own row of the diagonal: the first and last stages scalar, everything
+// between packed (as line_op2).
+template <int N>
+__device__ __forceinline__ void line_spectral2(float (&a)[N], float (&b)[N], const float (&da)[N],
+                                               const float (&db)[N])
+{
+    static_assert(N >= 4, "split of the first stage");
+    constexpr int H = N / 2;
+    float2 u[H], v[H], ye[H], yo[H];
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+        u[j] = make_float2(a[j] + a[N - 1 - j], b[j] + b[N - 1 - j]);
+        v[j] = make_float2(a[j] - a[N - 1 - j], b[j] - b[N - 1 - j]);
+    }
+    DCT2<H, float2>::run(u, ye);
+    DCT4<H, float2>::run(v, yo);
+    // coefficient 2m is ye[m], 2m + 1 is yo[m]: the diagonal, then the adjoint
+#pragma unroll
+    for (int m = 0; m < H; ++m) {
+        ye[m] = __fmul2_rn(ye[m], make_float2(da[2 * m], db[2 * m]));
+        yo[m] = __fmul2_rn(yo[m], make_float2(da[2 * m + 1], db[2 * m + 1]));
+    }
+    float2 ea[H], ob[H];
+    DCT3<H, float2>::run(ye, ea);
+    DCT4<H, float2>::run(yo, ob);
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+        a[j] = ea[j].x + ob[j].x; a[N - 1 - j] = ea[j].x - ob[j].x;
+        b[j] = ea[j].y + ob[j].y; b[N - 1 - j] = ea[j].y - ob[j].y;
+    }
+}
+
 // line_op on two lines a and b held as plain float arrays (for instance two
 // rows loaded with 16-byte accesses): the first and the last stage run in
 // scalar instructions that read or write the halves of packed pairs, so

@@ -87,6 +87,11 @@ struct FusedCfg {
     // 10% faster) and is mixed on contiguous batches
     static constexpr bool PAIR2 = LAYOUT == LAY_STRIP && J2 % 2 == 0 && W >= 4;
     static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + STAGES * 8;
+    // spectral direction: the folded diagonal staged once per CTA, rows at a
+    // pitch of W + 4 floats (the eight rows a row-pass instruction touches
+    // fall on distinct banks)
+    static constexpr int LAM_P = W + 4;
+    static constexpr size_t LAM_BYTES = (size_t)H * LAM_P * 4 + 8;  // + the alignment pad
     // register-allocation hint (resident CTAs per SM; 0 = none).  Measured: the
     // image strips and the 64-element batches run faster with the allocation
     // the hint gives (16x16 image step 15.0 -> 14.65 us, 8x8 round trip 0.76
@@ -314,7 +319,17 @@ template <int H, int W, bool TILED, int DIR>
 __device__ __forceinline__ void row_pass(float *stage, int n, int warp, int lane, AxisScale sc, const float *lam)
 {
     using C = FusedCfg<H, W, TILED>;
-    if constexpr (C::PAIR2 && DIR != DIR_SPEC) {
+    // row r of the spectrum after the column pass holds frequency r along h;
+    // lam: the folded diagonal in shared memory, pitch LAM_P
+    auto lam_row = [&](int r, float (&d)[W]) {
+        const float4 *lr = reinterpret_cast<const float4 *>(lam + r * C::LAM_P);
+#pragma unroll
+        for (int v = 0; v < W / 4; ++v) {
+            const float4 t = lr[v];
+            d[4 * v] = t.x; d[4 * v + 1] = t.y; d[4 * v + 2] = t.z; d[4 * v + 3] = t.w;
+        }
+    };
+    if constexpr (C::PAIR2) {
 #pragma unroll
         for (int j = 0; j < C::J2; j += 2) {
             int a0, r0, a1, r1;
@@ -330,7 +345,14 @@ __device__ __forceinline__ void row_pass(float *stage, int n, int warp, int lane
                 x0[4 * v] = t0.x; x0[4 * v + 1] = t0.y; x0[4 * v + 2] = t0.z; x0[4 * v + 3] = t0.w;
                 x1[4 * v] = t1.x; x1[4 * v + 1] = t1.y; x1[4 * v + 2] = t1.z; x1[4 * v + 3] = t1.w;
             }
-            line_op2<W, DIR>(x0, x1, sc);
+            if constexpr (DIR == DIR_SPEC) {
+                float d0[W], d1[W];
+                lam_row(r0, d0);
+                lam_row(r1, d1);
+                line_spectral2<W>(x0, x1, d0, d1);
+            } else {
+                line_op2<W, DIR>(x0, x1, sc);
+            }
             if (v0) {
 #pragma unroll
                 for (int v = 0; v < W / 4; ++v) q0[v] = make_float4(x0[4 * v], x0[4 * v + 1], x0[4 * v + 2], x0[4 * v + 3]);
@@ -354,14 +376,8 @@ __device__ __forceinline__ void row_pass(float *stage, int n, int warp, int lane
                     x[4 * v] = t.x; x[4 * v + 1] = t.y; x[4 * v + 2] = t.z; x[4 * v + 3] = t.w;
                 }
                 if constexpr (DIR == DIR_SPEC) {
-                    // row r of the spectrum after the column pass holds frequency r along h
                     float d[W];
-                    const float4 *lr = reinterpret_cast<const float4 *>(lam + r * W);
-#pragma unroll
-                    for (int v = 0; v < W / 4; ++v) {
-                        const float4 t = __ldg(lr + v);
-                        d[4 * v] = t.x; d[4 * v + 1] = t.y; d[4 * v + 2] = t.z; d[4 * v + 3] = t.w;
-                    }
+                    lam_row(r, d);
                     line_spectral<W>(x, d);
                 } else {
                     line_op<W, DIR>(x, sc);
@@ -379,6 +395,8 @@ __global__ void __launch_bounds__(FusedCfg<H, W, TILED>::THREADS, FusedCfg<H, W,
     using C = FusedCfg<H, W, TILED>;
     extern __shared__ __align__(128) float smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + C::STAGES * C::STAGE_FLOATS);
+    // spectral only: the folded diagonal, 16-byte aligned after the barriers
+    float *lam_s = reinterpret_cast<float *>(full + ((C::STAGES + 1) & ~1));
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int grid = (int)gridDim.x;
 
@@ -390,6 +408,9 @@ __global__ void __launch_bounds__(FusedCfg<H, W, TILED>::THREADS, FusedCfg<H, W,
     // after every prerequisite grid has finished
     pdl_launch_dependents();
     pdl_wait_prerequisites();
+    if constexpr (DIR == DIR_SPEC) {
+        for (int e = tid; e < H * W; e += C::THREADS) lam_s[(e / W) * C::LAM_P + e % W] = __ldg(p.lam + e);
+    }
     __syncthreads();
 
     // prologue: fill every stage (chunk k of this CTA uses stage k mod STAGES,
@@ -430,7 +451,7 @@ __global__ void __launch_bounds__(FusedCfg<H, W, TILED>::THREADS, FusedCfg<H, W,
         }
 
         // pass 2: rows, 1D operation along w
-        row_pass<H, W, TILED, DIR>(stage, n, warp, lane, p.sc.w, p.lam);
+        row_pass<H, W, TILED, DIR>(stage, n, warp, lane, p.sc.w, lam_s);
         if constexpr (DIR == DIR_SPEC) {
             // pass 3 (spectral only): columns, unscaled adjoint core along h
             cta_sync<C::NW>();
@@ -542,6 +563,7 @@ static cudaError_t launch_one(const DirScales &sc, const ExecGeom &g, unsigned i
 {
     using C = FusedCfg<H, W, TILED>;
     auto kern = k_fused<H, W, DIR, TILED>;
+    constexpr size_t smem = C::SMEM + (DIR == DIR_SPEC ? C::LAM_BYTES : 0);
     static DeviceLaunchCache cache;
     int dev = 0, blocks_per_sm = 0, num_sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -549,13 +571,13 @@ static cudaError_t launch_one(const DirScales &sc, const ExecGeom &g, unsigned i
     e = cache.get(
         dev,
         [&](int d, int &bps, int &sms) {
-            cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-            if (r == cudaSuccess) r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, C::THREADS, C::SMEM);
+            cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (r == cudaSuccess) r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, C::THREADS, smem);
             if (r == cudaSuccess) r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
             if (r == cudaSuccess && bps < 1) r = cudaErrorInvalidConfiguration;
             if (r == cudaSuccess && debug_enabled())
                 fprintf(stderr, "[bdct] k_fused<%d,%d,%d,%d>: %d CTAs/SM x %d threads, %d stages, smem %zu B\n", H, W,
-                        DIR, (int)TILED, bps, C::THREADS, C::STAGES, C::SMEM);
+                        DIR, (int)TILED, bps, C::THREADS, C::STAGES, smem);
             return r;
         },
         &blocks_per_sm, &num_sms);
@@ -591,7 +613,7 @@ static cudaError_t launch_one(const DirScales &sc, const ExecGeom &g, unsigned i
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(C::THREADS);
-    cfg.dynamicSmemBytes = C::SMEM;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;

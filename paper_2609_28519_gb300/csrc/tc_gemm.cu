@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(128) k_tcg(const TgParams p)
 //   warp 0, lane 0: producer -- one bulk copy of the input terms and one of
 //     the operator terms per chunk into a two-stage ring (full / empty
 //     mbarriers);
-//   warp 1, lane 0: issues the six products of a chunk into one of two TMEM
+//   warp 1, lane 0: issues the six products of a chunk into one of four TMEM
 //     partial accumulators and commits them twice (stage free, partial ready);
 //   warps 2-5: each reads its TMEM lane quadrant (warp % 4) of a finished
 //     partial, adds it to its row's running sums in registers (round to
@@ -368,10 +368,13 @@ __global__ void k_tg_presplit(const float *src, const long long *src_off, long l
 
 constexpr int kTg2NT = 128;
 constexpr int kTg2Stages = 2;
+// TMEM partial accumulators (kTg2Acc x 128 columns of the 512): the MMA lane
+// may run kTg2Acc - 1 chunks ahead of the epilogue warps' reads
+constexpr int kTg2Acc = 4;
 constexpr int kTg2AStage = 3 * 128 * kTgKC * 2;       // bytes of the input terms of a chunk
 constexpr int kTg2BStage = 3 * kTg2NT * kTgKC * 2;    // bytes of the operator terms of a chunk
 constexpr int kTg2Stage = kTg2AStage + kTg2BStage;
-constexpr size_t kTg2Smem = (size_t)kTg2Stages * kTg2Stage + 16 * 8 + 16;
+constexpr size_t kTg2Smem = (size_t)kTg2Stages * kTg2Stage + (2 * kTg2Stages + 2 * kTg2Acc) * 8 + 16;
 
 struct Tg2Params {
     const __nv_bfloat16 *abuf;       // input terms, [row tile][chunk][term][128 x KC]
@@ -392,8 +395,8 @@ __global__ void __launch_bounds__(192, 1) k_tcg2(const Tg2Params p)
     uint64_t *full = reinterpret_cast<uint64_t *>(t2s + kTg2Stages * kTg2Stage);
     uint64_t *empty = full + kTg2Stages;
     uint64_t *pfull = empty + kTg2Stages;   // partial accumulator ready
-    uint64_t *pempty = pfull + 2;           // partial accumulator read
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(pempty + 2);
+    uint64_t *pempty = pfull + kTg2Acc;     // partial accumulator read
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(pempty + kTg2Acc);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -402,7 +405,7 @@ __global__ void __launch_bounds__(192, 1) k_tcg2(const Tg2Params p)
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        for (int a = 0; a < 2; ++a) {
+        for (int a = 0; a < kTg2Acc; ++a) {
             mbar_init(&pfull[a], 1);
             mbar_init(&pempty[a], 4);  // one arrival per epilogue warp
         }
@@ -411,7 +414,7 @@ __global__ void __launch_bounds__(192, 1) k_tcg2(const Tg2Params p)
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(2 * kTg2NT)
+                     "r"(kTg2Acc * kTg2NT)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -459,9 +462,12 @@ __global__ void __launch_bounds__(192, 1) k_tcg2(const Tg2Params p)
             long long c = 0;
             for (long long item = blockIdx.x; ok && item < p.items; item += gridDim.x) {
                 for (int kc = 0; kc < nk; ++kc, ++c) {
-                    const int s = (int)(c % kTg2Stages), a = (int)(c & 1);
+                    const int s = (int)(c % kTg2Stages), a = (int)(c % kTg2Acc);
                     if (!mbar_wait_bounded(&full[s], (uint32_t)(c / kTg2Stages) & 1u)) { ok = false; break; }
-                    if (c >= 2 && !mbar_wait_bounded(&pempty[a], (uint32_t)((c >> 1) - 1) & 1u)) { ok = false; break; }
+                    if (c >= kTg2Acc && !mbar_wait_bounded(&pempty[a], (uint32_t)(c / kTg2Acc - 1) & 1u)) {
+                        ok = false;
+                        break;
+                    }
                     if (*abort_flag) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t a0 = smem_u32(t2s + s * kTg2Stage), b0 = a0 + kTg2AStage;
@@ -489,8 +495,8 @@ __global__ void __launch_bounds__(192, 1) k_tcg2(const Tg2Params p)
         long long c = 0;
         for (long long item = blockIdx.x; ok && item < p.items; item += gridDim.x) {
             for (int kc = 0; kc < nk; ++kc, ++c) {
-                const int a = (int)(c & 1);
-                bool w = mbar_wait_bounded(&pfull[a], (uint32_t)(c >> 1) & 1u);
+                const int a = (int)(c % kTg2Acc);
+                bool w = mbar_wait_bounded(&pfull[a], (uint32_t)(c / kTg2Acc) & 1u);
                 w = __all_sync(0xffffffffu, w);
                 if (!w) { ok = false; break; }
                 tc_fence_after();
@@ -531,11 +537,12 @@ __global__ void __launch_bounds__(192, 1) k_tcg2(const Tg2Params p)
     if (warp == 0 && lane == 0 && last_load >= 0)
         mbar_wait_bounded(&full[last_load % kTg2Stages], (uint32_t)(last_load / kTg2Stages) & 1u);
     if (warp == 1 && lane == 0 && last_commit >= 0)
-        mbar_wait_bounded(&pfull[last_commit & 1], (uint32_t)(last_commit >> 1) & 1u);
+        mbar_wait_bounded(&pfull[last_commit % kTg2Acc], (uint32_t)(last_commit / kTg2Acc) & 1u);
     tc_fence_before();
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTg2NT) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTg2Acc * kTg2NT)
+                     : "memory");
 }
 
 // ------------------------------------------------------------ operator tables
@@ -710,7 +717,7 @@ static cudaError_t tg2_launch(const float *src, const long long *src_off, const 
             b = 1;
             if (r == cudaSuccess && debug_enabled())
                 fprintf(stderr, "[bdct] k_tcg2<%d>: 1 CTA/SM x 192 threads, smem %zu B, TMEM %d cols\n", TERMS,
-                        kTg2Smem, 2 * kTg2NT);
+                        kTg2Smem, kTg2Acc * kTg2NT);
             return r;
         },
         &bps, &sms);
