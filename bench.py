@@ -189,7 +189,7 @@ def run_reference(args):
 # Sources of each captured kernel's translation unit (the kernel file and the
 # headers it includes).
 KERNEL_SOURCES = {"k_fused": ["fp32_fused.cu", "dct_cores.cuh", "ptx.cuh", "bdct_internal.h"],
-                  "k_tc_split": ["tc_split.cu", "ptx.cuh", "bdct_internal.h"]}
+                  "k_tc_split": ["tc_split.cu", "tc_ptx.cuh", "ptx.cuh", "bdct_internal.h"]}
 
 
 def source_key(kernel_key: str) -> str:

@@ -792,3 +792,34 @@ def test_radix3_lines_against_oracle(oracle_mod, cuda_dev, h, w, norm):
     for kind in KINDS:
         y = _run(plan, kind, x, cuda_dev)
         _assert_parity(oracle_mod, y, _ref(oracle_mod, kind, x, norm), x, norm, kind, ("radix3", h, w, norm, kind))
+
+
+def test_spectral_ring_tiled_and_chunk_sizes(oracle_mod, cuda_dev):
+    """The composed spectral direction on image blocks of the ring shapes, in
+    place; and the workspace chunk of the separable routes changes nothing
+    but the launch count (bit-equal results for 1-array and default chunks)."""
+    import torch
+    from paper_2609_28519_gb300 import Plan
+    img = inputs.ramp_image(11, 256, 384)
+    for (h, w) in [(64, 64), (128, 64)]:
+        lam = inputs.random_diagonal(11 + h + w, h, w, -1.0, 2.0)
+        plan = Plan(h, w)
+        plan.set_spectral(lam)
+        d = torch.from_numpy(img).to(cuda_dev)
+        out = plan.execute_tiled("spectral", d)
+        d2 = d.clone()
+        plan.execute_tiled("spectral", d2, d2)
+        torch.cuda.synchronize()
+        assert torch.equal(out, d2)
+        blocks = inputs.image_to_blocks(img, h, w)
+        _assert_spectral(oracle_mod, inputs.image_to_blocks(out.cpu().numpy(), h, w), blocks, lam,
+                         ("spectral-ring-tiled", h, w))
+    for (h, w, path) in [(256, 256, "fp32"), (384, 192, "fp32"), (24, 40, "fp32"), (256, 128, "split_tc")]:
+        x = torch.from_numpy(inputs.uniform(9700 + h + w, 7, h, w)).to(cuda_dev)
+        plan = Plan(h, w, path=path)
+        ref = {k: plan.execute(k, x) for k in KINDS}
+        plan.set_chunk_bytes(1)  # one array per chunk: seven rounds of passes
+        for k in KINDS:
+            y = plan.execute(k, x)
+            torch.cuda.synchronize()
+            assert torch.equal(y, ref[k]), (h, w, path, k)
