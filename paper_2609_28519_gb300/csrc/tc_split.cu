@@ -319,6 +319,218 @@ __global__ void __launch_bounds__(128) k_tc_split(const TcParams p)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS) : "memory");
 }
 
+// ------------------------------------------------------------ warp-specialized kernel
+// Forward and inverse (two products per tile) with the phases of different
+// tiles overlapped.  k_tc_split runs each tile's load, split, products,
+// TMEM read, re-split, products and store one after another in every
+// thread, so a CTA is idle on each wait.  Here each phase has its own warps
+// and double-buffered shared-memory stages and TMEM accumulators:
+//   warps 0-3  (WG1): load tile t's rows (thread = stack row), split into
+//              BF16 terms, write the K-major A operand of product 1;
+//   warp 4, lane 0 : issue product 1 of tile t + 1 and product 2 of tile t,
+//              commit each to the stage-free and result-ready barriers;
+//   warps 5-8  (WG2): read T of tile t from TMEM (lane quadrant warp % 4),
+//              re-split it into the MN-major A operand of product 2;
+//   warps 9-12 (WG3): read Y of tile t from TMEM and store it (thread =
+//              array and column: coalesced across lanes).
+template <int N>
+struct WsCfg {
+    static constexpr int G = 128 / N;
+    static constexpr int A_TERM = 128 * N * 2;
+    static constexpr int A_STAGE = 3 * A_TERM;
+    static constexpr int B_BYTES = 3 * N * N * 2;
+    static constexpr int THREADS = 13 * 32;
+    static constexpr int NBAR = 17;  // 8 pairs of stage barriers and the operator barrier
+    static constexpr size_t SMEM = (size_t)4 * A_STAGE + B_BYTES + NBAR * 8 + 16;
+    static constexpr int TMEM_COLS = 4 * N < 32 ? 32 : 4 * N;  // two T and two Y accumulators
+};
+
+template <int N, int TERMS, bool TILED>
+__global__ void __launch_bounds__(WsCfg<N>::THREADS, 1) k_tc_ws(const TcParams p)
+{
+    using C = WsCfg<N>;
+    extern __shared__ __align__(1024) uint8_t wsm[];
+    uint8_t *a1 = wsm;                       // 2 stages: product-1 operand
+    uint8_t *a2 = wsm + 2 * C::A_STAGE;      // 2 stages: product-2 operand
+    uint8_t *bop = wsm + 4 * C::A_STAGE;     // the operator's three terms
+    uint64_t *bar = reinterpret_cast<uint64_t *>(bop + C::B_BYTES);
+    uint64_t *a1_full = bar, *a1_empty = bar + 2, *t_full = bar + 4, *t_empty = bar + 6;
+    uint64_t *a2_full = bar + 8, *a2_empty = bar + 10, *y_full = bar + 12, *y_empty = bar + 14, *b_full = bar + 16;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + C::NBAR);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&a1_full[i], 128);
+            mbar_init(&a1_empty[i], 1);
+            mbar_init(&t_full[i], 1);
+            mbar_init(&t_empty[i], 128);
+            mbar_init(&a2_full[i], 128);
+            mbar_init(&a2_empty[i], 1);
+            mbar_init(&y_full[i], 1);
+            mbar_init(&y_empty[i], 128);
+        }
+        mbar_init(b_full, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 4) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(C::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    pdl_launch_dependents();
+    pdl_wait_prerequisites();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    // TMEM: T accumulators at columns 0 and N, Y accumulators at 2N and 3N
+    const int ntile_local = p.ntiles > (int)blockIdx.x
+                                ? (p.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x
+                                : 0;
+    bool ok = true;
+    long long last_commit = -1;  // MMA lane: 2 * t + product of the last commit (error path)
+
+    if (warp < 4) {
+        // ---- WG1: load and split tile rows
+        const int b_local = tid / N, r_local = tid % N;
+        float v[N];
+        for (int t = 0; t < ntile_local; ++t) {
+            const int tile = (int)blockIdx.x + t * (int)gridDim.x;
+            long long first, brow;
+            int n, t0;
+            tile_geom<N, TILED>(p, tile, first, n, brow, t0);
+            if (b_local < n) {
+                const float *src;
+                if constexpr (!TILED)
+                    src = (p.in_off ? p.in + p.in_off[first + b_local] : p.in + (first + b_local) * (long long)(N * N)) +
+                          r_local * N;
+                else src = p.in + (brow * N + r_local) * p.ld_in + (long long)(t0 + b_local) * N;
+#pragma unroll
+                for (int q = 0; q < N / 4; ++q) {
+                    const float4 x = __ldcg(reinterpret_cast<const float4 *>(src) + q);
+                    v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < N; ++j) v[j] = 0.0f;
+            }
+            const int s = t & 1;
+            if (t >= 2 && !mbar_wait_bounded(&a1_empty[s], (uint32_t)((t >> 1) - 1) & 1u)) { ok = false; break; }
+            if (*abort_flag) { ok = false; break; }
+            stage_a<N, TERMS, false>(a1 + s * C::A_STAGE, v, tid, 0);
+            fence_proxy_async_smem();
+            mbar_arrive(&a1_full[s]);
+        }
+    } else if (warp == 4) {
+        // ---- MMA issue: product 1 of tile t, then product 2 of tile t - 1
+        if (lane == 0) {
+            mbar_arrive_expect_tx(b_full, C::B_BYTES);
+            bulk_load(bop, p.ops, C::B_BYTES, b_full);
+            if (!mbar_wait_bounded(b_full, 0)) ok = false;
+            const uint32_t b_base = smem_u32(bop);
+            for (int step = 0; ok && step <= ntile_local; ++step) {
+                if (step < ntile_local) {
+                    const int t = step, s = t & 1;
+                    if (!mbar_wait_bounded(&a1_full[s], (uint32_t)(t >> 1) & 1u) ||
+                        (t >= 2 && !mbar_wait_bounded(&t_empty[s], (uint32_t)((t >> 1) - 1) & 1u)) || *abort_flag) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    issue_pass<N, TERMS, false>(smem_u32(a1 + s * C::A_STAGE), b_base, tmem + (uint32_t)(s * N));
+                    tc_commit(&a1_empty[s]);
+                    tc_commit(&t_full[s]);
+                    last_commit = 2LL * t;
+                }
+                if (step >= 1) {
+                    const int t = step - 1, s = t & 1;
+                    if (!mbar_wait_bounded(&a2_full[s], (uint32_t)(t >> 1) & 1u) ||
+                        (t >= 2 && !mbar_wait_bounded(&y_empty[s], (uint32_t)((t >> 1) - 1) & 1u)) || *abort_flag) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    issue_pass<N, TERMS, true>(smem_u32(a2 + s * C::A_STAGE), b_base,
+                                               tmem + (uint32_t)((2 + s) * N));
+                    tc_commit(&a2_empty[s]);
+                    tc_commit(&y_full[s]);
+                    last_commit = 2LL * t + 1;
+                }
+            }
+        }
+    } else {
+        // ---- WG2 (warps 5-8) and WG3 (warps 9-12): TMEM lane quadrant warp % 4
+        const bool wg2 = warp <= 8;
+        const int m = 32 * (warp & 3) + lane;  // stack row of this thread's TMEM lane
+        const int b_local = m / N, r_local = m % N;
+        const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+        float v[N];
+        for (int t = 0; t < ntile_local; ++t) {
+            const int s = t & 1;
+            uint64_t *full = wg2 ? &t_full[s] : &y_full[s];
+            // warp-uniform decisions only: the TMEM loads below are warp-collective
+            bool w = mbar_wait_bounded(full, (uint32_t)(t >> 1) & 1u) && !*abort_flag;
+            w = __all_sync(0xffffffffu, w);
+            if (!w) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t acc = tmem + (uint32_t)((wg2 ? s : 2 + s) * N) + lane_off;
+            if constexpr (N >= 16) {
+#pragma unroll
+                for (int c = 0; c < N / 16; ++c) tmem_ld16(acc + 16 * c, v + 16 * c);
+            }
+            tc_fence_before();
+            mbar_arrive(wg2 ? &t_empty[s] : &y_empty[s]);
+            if (wg2) {
+                // T row r_local of array b_local -> column r_local of the MN-major operand
+                bool w2 = t < 2 || mbar_wait_bounded(&a2_empty[s], (uint32_t)((t >> 1) - 1) & 1u);
+                w2 = __all_sync(0xffffffffu, w2);
+                if (!w2) { ok = false; break; }
+                stage_a<N, TERMS, true>(a2 + s * C::A_STAGE, v, r_local, b_local * N);
+                fence_proxy_async_smem();
+                mbar_arrive(&a2_full[s]);
+            } else {
+                // column r_local of Y[b_local] (values over the row index): coalesced across lanes
+                const int tile = (int)blockIdx.x + t * (int)gridDim.x;
+                long long first, brow;
+                int n, t0;
+                tile_geom<N, TILED>(p, tile, first, n, brow, t0);
+                if (b_local < n) {
+#pragma unroll
+                    for (int k = 0; k < N; ++k) {
+                        float *dst;
+                        if constexpr (!TILED)
+                            dst = (p.out_off ? p.out + p.out_off[first + b_local]
+                                             : p.out + (first + b_local) * (long long)(N * N)) + k * N + r_local;
+                        else dst = p.out + (brow * N + k) * p.ld_out + (long long)(t0 + b_local) * N + r_local;
+                        *dst = v[k];
+                    }
+                }
+            }
+        }
+    }
+    if (!ok) {
+        *abort_flag = 1;
+        if (lane == 0) record_timeout(p.status);
+    }
+    // error path: the MMA lane waits (bounded) for the operator copy and its
+    // last committed products before shared memory and TMEM are released
+    if (warp == 4 && lane == 0 && !ok) {
+        mbar_wait_bounded(b_full, 0);
+        if (last_commit >= 0) {
+            const int t = (int)(last_commit >> 1), s = t & 1;
+            mbar_wait_bounded((last_commit & 1) ? &y_full[s] : &t_full[s], (uint32_t)(t >> 1) & 1u);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 4)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS) : "memory");
+}
+
 // ------------------------------------------------------------ tables
 // Operator matrix M (direction/norm as in the dense route) split into three
 // BF16 terms in FP64, written in the K-major B layout: B[l][j] = M[l][j]
@@ -443,9 +655,61 @@ static cudaError_t tc_launch_one(const TcParams &p0, const __nv_bfloat16 *ops, c
     return cudaLaunchKernelEx(&cfg, kern, p);
 }
 
+template <int N, int TERMS, bool TILED>
+static cudaError_t tc_ws_launch(const TcParams &p0, const __nv_bfloat16 *ops, cudaStream_t stream)
+{
+    using C = WsCfg<N>;
+    auto kern = k_tc_ws<N, TERMS, TILED>;
+    static DeviceLaunchCache cache;
+    int dev = 0, bps = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cache.get(
+        dev,
+        [&](int d, int &b, int &n) {
+            cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+            if (r == cudaSuccess) r = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d);
+            b = 1;
+            if (r == cudaSuccess && debug_enabled())
+                fprintf(stderr, "[bdct] k_tc_ws<%d,%d,%d>: 1 CTA/SM x %d threads, smem %zu B, TMEM %d cols\n", N,
+                        TERMS, (int)TILED, C::THREADS, C::SMEM, C::TMEM_COLS);
+            return r;
+        },
+        &bps, &sms);
+    if (e != cudaSuccess) return e;
+    TcParams p = p0;
+    p.ops = ops;
+    long long nt;
+    if (!TILED) {
+        nt = (p.count + C::G - 1) / C::G;
+    } else {
+        p.chunks_per_row = (p.tiles_per_row + C::G - 1) / C::G;
+        nt = (p.count / p.tiles_per_row) * p.chunks_per_row;
+    }
+    if (nt <= 0) return cudaSuccess;
+    if (nt > 0x7ff00000LL) return cudaErrorInvalidValue;
+    p.ntiles = (int)nt;
+    long long grid = sms;
+    if (grid > nt) grid = nt;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(C::THREADS);
+    cfg.dynamicSmemBytes = C::SMEM;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, p);
+}
+
 template <int N, int TERMS>
 static cudaError_t tc_launch_nt(Dir dir, const TcParams &p, const __nv_bfloat16 *ops, cudaStream_t s, bool tiled)
 {
+    // forward and inverse: the warp-specialized kernel
+    if (dir == DIR_FWD || dir == DIR_INV)
+        return tiled ? tc_ws_launch<N, TERMS, true>(p, ops, s) : tc_ws_launch<N, TERMS, false>(p, ops, s);
     if (dir == DIR_RT)
         return tiled ? tc_launch_one<N, 4, TERMS, true>(p, ops, s) : tc_launch_one<N, 4, TERMS, false>(p, ops, s);
     if (dir == DIR_SPEC)
