@@ -341,7 +341,12 @@ struct WsCfg {
     static constexpr int B_BYTES = 3 * N * N * 2;
     static constexpr int THREADS = 13 * 32;
     static constexpr int NBAR = 17;  // 8 pairs of stage barriers and the operator barrier
-    static constexpr size_t SMEM = (size_t)4 * A_STAGE + B_BYTES + NBAR * 8 + 16;
+    // input rows in flight per loading thread (cp.async into its own padded
+    // row slots: pitch N + 4 floats keeps a warp's 16-byte reads conflict-free)
+    static constexpr int D = N <= 16 ? 8 : 4;
+    static constexpr int XP = N + 4;
+    static constexpr int X_BYTES = D * 128 * XP * 4;
+    static constexpr size_t SMEM = (size_t)4 * A_STAGE + B_BYTES + X_BYTES + NBAR * 8 + 16;
     static constexpr int TMEM_COLS = 4 * N < 32 ? 32 : 4 * N;  // two T and two Y accumulators
 };
 
@@ -353,7 +358,8 @@ __global__ void __launch_bounds__(WsCfg<N>::THREADS, 1) k_tc_ws(const TcParams p
     uint8_t *a1 = wsm;                       // 2 stages: product-1 operand
     uint8_t *a2 = wsm + 2 * C::A_STAGE;      // 2 stages: product-2 operand
     uint8_t *bop = wsm + 4 * C::A_STAGE;     // the operator's three terms
-    uint64_t *bar = reinterpret_cast<uint64_t *>(bop + C::B_BYTES);
+    float *xring = reinterpret_cast<float *>(bop + C::B_BYTES);  // D row slots per loading thread
+    uint64_t *bar = reinterpret_cast<uint64_t *>(reinterpret_cast<uint8_t *>(xring) + C::X_BYTES);
     uint64_t *a1_full = bar, *a1_empty = bar + 2, *t_full = bar + 4, *t_empty = bar + 6;
     uint64_t *a2_full = bar + 8, *a2_empty = bar + 10, *y_full = bar + 12, *y_empty = bar + 14, *b_full = bar + 16;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + C::NBAR);
@@ -395,29 +401,50 @@ __global__ void __launch_bounds__(WsCfg<N>::THREADS, 1) k_tc_ws(const TcParams p
     long long last_commit = -1;  // MMA lane: 2 * t + product of the last commit (error path)
 
     if (warp < 4) {
-        // ---- WG1: load and split tile rows
+        // ---- WG1: load and split tile rows; each thread copies its own row of
+        // the next D tiles with cp.async and reads back only what it copied, so
+        // its own group wait is all the synchronization the copies need
         const int b_local = tid / N, r_local = tid % N;
+        auto issue = [&](int t) {
+            const int tile = (int)blockIdx.x + t * (int)gridDim.x;
+            if (t < ntile_local) {
+                long long first, brow;
+                int n, t0;
+                tile_geom<N, TILED>(p, tile, first, n, brow, t0);
+                if (b_local < n) {
+                    const float *src;
+                    if constexpr (!TILED)
+                        src = (p.in_off ? p.in + p.in_off[first + b_local]
+                                        : p.in + (first + b_local) * (long long)(N * N)) + r_local * N;
+                    else src = p.in + (brow * N + r_local) * p.ld_in + (long long)(t0 + b_local) * N;
+                    float *dst = xring + ((t % C::D) * 128 + tid) * C::XP;
+#pragma unroll
+                    for (int q = 0; q < N / 4; ++q) cp_async16(dst + 4 * q, src + 4 * q);
+                }
+            }
+            cp_async_commit();  // one group per tile, empty past the end
+        };
+#pragma unroll 1
+        for (int t = 0; t < C::D; ++t) issue(t);
         float v[N];
         for (int t = 0; t < ntile_local; ++t) {
             const int tile = (int)blockIdx.x + t * (int)gridDim.x;
             long long first, brow;
             int n, t0;
             tile_geom<N, TILED>(p, tile, first, n, brow, t0);
+            cp_async_wait_group<C::D - 1>();  // this thread's copies of tile t have landed
             if (b_local < n) {
-                const float *src;
-                if constexpr (!TILED)
-                    src = (p.in_off ? p.in + p.in_off[first + b_local] : p.in + (first + b_local) * (long long)(N * N)) +
-                          r_local * N;
-                else src = p.in + (brow * N + r_local) * p.ld_in + (long long)(t0 + b_local) * N;
+                const float4 *q4 = reinterpret_cast<const float4 *>(xring + ((t % C::D) * 128 + tid) * C::XP);
 #pragma unroll
                 for (int q = 0; q < N / 4; ++q) {
-                    const float4 x = __ldcg(reinterpret_cast<const float4 *>(src) + q);
+                    const float4 x = q4[q];
                     v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
                 }
             } else {
 #pragma unroll
                 for (int j = 0; j < N; ++j) v[j] = 0.0f;
             }
+            issue(t + C::D);  // refill the slot just read
             const int s = t & 1;
             if (t >= 2 && !mbar_wait_bounded(&a1_empty[s], (uint32_t)((t >> 1) - 1) & 1u)) { ok = false; break; }
             if (*abort_flag) { ok = false; break; }
@@ -425,6 +452,7 @@ __global__ void __launch_bounds__(WsCfg<N>::THREADS, 1) k_tc_ws(const TcParams p
             fence_proxy_async_smem();
             mbar_arrive(&a1_full[s]);
         }
+        cp_async_wait_all();  // no copy of this thread still in flight at exit
     } else if (warp == 4) {
         // ---- MMA issue: product 1 of tile t, then product 2 of tile t - 1
         if (lane == 0) {
@@ -707,9 +735,11 @@ static cudaError_t tc_ws_launch(const TcParams &p0, const __nv_bfloat16 *ops, cu
 template <int N, int TERMS>
 static cudaError_t tc_launch_nt(Dir dir, const TcParams &p, const __nv_bfloat16 *ops, cudaStream_t s, bool tiled)
 {
-    // forward and inverse: the warp-specialized kernel
-    if (dir == DIR_FWD || dir == DIR_INV)
-        return tiled ? tc_ws_launch<N, TERMS, true>(p, ops, s) : tc_ws_launch<N, TERMS, false>(p, ops, s);
+    // forward and inverse of sides 16 and 32: the warp-specialized kernel
+    if constexpr (N <= 32) {
+        if (dir == DIR_FWD || dir == DIR_INV)
+            return tiled ? tc_ws_launch<N, TERMS, true>(p, ops, s) : tc_ws_launch<N, TERMS, false>(p, ops, s);
+    }
     if (dir == DIR_RT)
         return tiled ? tc_launch_one<N, 4, TERMS, true>(p, ops, s) : tc_launch_one<N, 4, TERMS, false>(p, ops, s);
     if (dir == DIR_SPEC)
