@@ -327,8 +327,9 @@ __global__ void __launch_bounds__(128) k_tc_split(const TcParams p)
 // and double-buffered shared-memory stages and TMEM accumulators:
 //   warps 0-3  (WG1): load tile t's rows (thread = stack row), split into
 //              BF16 terms, write the K-major A operand of product 1;
-//   warp 4, lane 0 : issue product 1 of tile t + 1 and product 2 of tile t,
-//              commit each to the stage-free and result-ready barriers;
+//   warp 4, lane 0 : issue product 1 of every tile, warp 13, lane 0: product
+//              2 (two issuers, so neither waits for the other's inputs), each
+//              committed to the stage-free and result-ready barriers;
 //   warps 5-8  (WG2): read T of tile t from TMEM (lane quadrant warp % 4),
 //              re-split it into the MN-major A operand of product 2;
 //   warps 9-12 (WG3): read Y of tile t from TMEM and store it (thread =
@@ -339,7 +340,7 @@ struct WsCfg {
     static constexpr int A_TERM = 128 * N * 2;
     static constexpr int A_STAGE = 3 * A_TERM;
     static constexpr int B_BYTES = 3 * N * N * 2;
-    static constexpr int THREADS = 13 * 32;
+    static constexpr int THREADS = 14 * 32;
     static constexpr int NBAR = 17;  // 8 pairs of stage barriers and the operator barrier
     // input rows in flight per loading thread (cp.async into its own padded
     // row slots: pitch N + 4 floats keeps a warp's 16-byte reads conflict-free)
@@ -398,7 +399,7 @@ __global__ void __launch_bounds__(WsCfg<N>::THREADS, 1) k_tc_ws(const TcParams p
                                 ? (p.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x
                                 : 0;
     bool ok = true;
-    long long last_commit = -1;  // MMA lane: 2 * t + product of the last commit (error path)
+    long long last_commit = -1;  // MMA lanes: the tile of the last commit (error path)
 
     if (warp < 4) {
         // ---- WG1: load and split tile rows; each thread copies its own row of
@@ -453,41 +454,38 @@ __global__ void __launch_bounds__(WsCfg<N>::THREADS, 1) k_tc_ws(const TcParams p
             mbar_arrive(&a1_full[s]);
         }
         cp_async_wait_all();  // no copy of this thread still in flight at exit
-    } else if (warp == 4) {
-        // ---- MMA issue: product 1 of tile t, then product 2 of tile t - 1
+    } else if (warp == 4 || warp == 13) {
+        // ---- MMA issue, one lane per product so that neither waits for the
+        // other's inputs: warp 4 product 1 (K-major A), warp 13 product 2
         if (lane == 0) {
-            mbar_arrive_expect_tx(b_full, C::B_BYTES);
-            bulk_load(bop, p.ops, C::B_BYTES, b_full);
+            const bool first = warp == 4;
+            if (first) {
+                mbar_arrive_expect_tx(b_full, C::B_BYTES);
+                bulk_load(bop, p.ops, C::B_BYTES, b_full);
+            }
             if (!mbar_wait_bounded(b_full, 0)) ok = false;
             const uint32_t b_base = smem_u32(bop);
-            for (int step = 0; ok && step <= ntile_local; ++step) {
-                if (step < ntile_local) {
-                    const int t = step, s = t & 1;
-                    if (!mbar_wait_bounded(&a1_full[s], (uint32_t)(t >> 1) & 1u) ||
-                        (t >= 2 && !mbar_wait_bounded(&t_empty[s], (uint32_t)((t >> 1) - 1) & 1u)) || *abort_flag) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                    issue_pass<N, TERMS, false>(smem_u32(a1 + s * C::A_STAGE), b_base, tmem + (uint32_t)(s * N));
-                    tc_commit(&a1_empty[s]);
-                    tc_commit(&t_full[s]);
-                    last_commit = 2LL * t;
+            uint64_t *in_full = first ? a1_full : a2_full, *acc_empty = first ? t_empty : y_empty;
+            uint64_t *in_empty = first ? a1_empty : a2_empty, *acc_full = first ? t_full : y_full;
+            uint8_t *abuf = first ? a1 : a2;
+            const int acc_col = first ? 0 : 2 * N;
+            for (int t = 0; ok && t < ntile_local; ++t) {
+                const int s = t & 1;
+                if (!mbar_wait_bounded(&in_full[s], (uint32_t)(t >> 1) & 1u) ||
+                    (t >= 2 && !mbar_wait_bounded(&acc_empty[s], (uint32_t)((t >> 1) - 1) & 1u)) || *abort_flag) {
+                    ok = false;
+                    break;
                 }
-                if (step >= 1) {
-                    const int t = step - 1, s = t & 1;
-                    if (!mbar_wait_bounded(&a2_full[s], (uint32_t)(t >> 1) & 1u) ||
-                        (t >= 2 && !mbar_wait_bounded(&y_empty[s], (uint32_t)((t >> 1) - 1) & 1u)) || *abort_flag) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                    issue_pass<N, TERMS, true>(smem_u32(a2 + s * C::A_STAGE), b_base,
-                                               tmem + (uint32_t)((2 + s) * N));
-                    tc_commit(&a2_empty[s]);
-                    tc_commit(&y_full[s]);
-                    last_commit = 2LL * t + 1;
-                }
+                tc_fence_after();
+                if (first)
+                    issue_pass<N, TERMS, false>(smem_u32(abuf + s * C::A_STAGE), b_base,
+                                                tmem + (uint32_t)(acc_col + s * N));
+                else
+                    issue_pass<N, TERMS, true>(smem_u32(abuf + s * C::A_STAGE), b_base,
+                                               tmem + (uint32_t)(acc_col + s * N));
+                tc_commit(&in_empty[s]);
+                tc_commit(&acc_full[s]);
+                last_commit = t;
             }
         }
     } else {
@@ -546,11 +544,11 @@ __global__ void __launch_bounds__(WsCfg<N>::THREADS, 1) k_tc_ws(const TcParams p
     }
     // error path: the MMA lane waits (bounded) for the operator copy and its
     // last committed products before shared memory and TMEM are released
-    if (warp == 4 && lane == 0 && !ok) {
+    if ((warp == 4 || warp == 13) && lane == 0 && !ok) {
         mbar_wait_bounded(b_full, 0);
         if (last_commit >= 0) {
-            const int t = (int)(last_commit >> 1), s = t & 1;
-            mbar_wait_bounded((last_commit & 1) ? &y_full[s] : &t_full[s], (uint32_t)(t >> 1) & 1u);
+            const int t = (int)last_commit, s = t & 1;
+            mbar_wait_bounded(warp == 4 ? &t_full[s] : &y_full[s], (uint32_t)(t >> 1) & 1u);
         }
     }
     tc_fence_before();
