@@ -341,14 +341,16 @@ struct WsCfg {
     static constexpr int A_STAGE = 3 * A_TERM;
     static constexpr int B_BYTES = 3 * N * N * 2;
     static constexpr int THREADS = 14 * 32;
-    static constexpr int NBAR = 17;  // 8 pairs of stage barriers and the operator barrier
+    // operand stages and accumulators per phase (a deeper ring where tiles are small)
+    static constexpr int NS = N <= 16 ? 4 : 2;
+    static constexpr int NBAR = 8 * NS + 1;  // eight barriers per stage and the operator barrier
     // input rows in flight per loading thread (cp.async into its own padded
     // row slots: pitch N + 4 floats keeps a warp's 16-byte reads conflict-free)
     static constexpr int D = N <= 16 ? 8 : 4;
     static constexpr int XP = N + 4;
     static constexpr int X_BYTES = D * 128 * XP * 4;
-    static constexpr size_t SMEM = (size_t)4 * A_STAGE + B_BYTES + X_BYTES + NBAR * 8 + 16;
-    static constexpr int TMEM_COLS = 4 * N < 32 ? 32 : 4 * N;  // two T and two Y accumulators
+    static constexpr size_t SMEM = (size_t)2 * NS * A_STAGE + B_BYTES + X_BYTES + NBAR * 8 + 16;
+    static constexpr int TMEM_COLS = 2 * NS * N < 32 ? 32 : 2 * NS * N;  // NS T and NS Y accumulators
 };
 
 template <int N, int TERMS, bool TILED>
@@ -356,19 +358,21 @@ __global__ void __launch_bounds__(WsCfg<N>::THREADS, 1) k_tc_ws(const TcParams p
 {
     using C = WsCfg<N>;
     extern __shared__ __align__(1024) uint8_t wsm[];
-    uint8_t *a1 = wsm;                       // 2 stages: product-1 operand
-    uint8_t *a2 = wsm + 2 * C::A_STAGE;      // 2 stages: product-2 operand
-    uint8_t *bop = wsm + 4 * C::A_STAGE;     // the operator's three terms
+    constexpr int NS = C::NS;
+    uint8_t *a1 = wsm;                        // NS stages: product-1 operand
+    uint8_t *a2 = wsm + NS * C::A_STAGE;      // NS stages: product-2 operand
+    uint8_t *bop = wsm + 2 * NS * C::A_STAGE; // the operator's three terms
     float *xring = reinterpret_cast<float *>(bop + C::B_BYTES);  // D row slots per loading thread
     uint64_t *bar = reinterpret_cast<uint64_t *>(reinterpret_cast<uint8_t *>(xring) + C::X_BYTES);
-    uint64_t *a1_full = bar, *a1_empty = bar + 2, *t_full = bar + 4, *t_empty = bar + 6;
-    uint64_t *a2_full = bar + 8, *a2_empty = bar + 10, *y_full = bar + 12, *y_empty = bar + 14, *b_full = bar + 16;
+    uint64_t *a1_full = bar, *a1_empty = bar + NS, *t_full = bar + 2 * NS, *t_empty = bar + 3 * NS;
+    uint64_t *a2_full = bar + 4 * NS, *a2_empty = bar + 5 * NS, *y_full = bar + 6 * NS, *y_empty = bar + 7 * NS;
+    uint64_t *b_full = bar + 8 * NS;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + C::NBAR);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < NS; ++i) {
             mbar_init(&a1_full[i], 128);
             mbar_init(&a1_empty[i], 1);
             mbar_init(&t_full[i], 1);
@@ -394,7 +398,7 @@ __global__ void __launch_bounds__(WsCfg<N>::THREADS, 1) k_tc_ws(const TcParams p
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    // TMEM: T accumulators at columns 0 and N, Y accumulators at 2N and 3N
+    // TMEM: T accumulators at columns s * N, Y accumulators at (NS + s) * N
     const int ntile_local = p.ntiles > (int)blockIdx.x
                                 ? (p.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x
                                 : 0;
@@ -446,8 +450,8 @@ __global__ void __launch_bounds__(WsCfg<N>::THREADS, 1) k_tc_ws(const TcParams p
                 for (int j = 0; j < N; ++j) v[j] = 0.0f;
             }
             issue(t + C::D);  // refill the slot just read
-            const int s = t & 1;
-            if (t >= 2 && !mbar_wait_bounded(&a1_empty[s], (uint32_t)((t >> 1) - 1) & 1u)) { ok = false; break; }
+            const int s = t % NS;
+            if (t >= NS && !mbar_wait_bounded(&a1_empty[s], (uint32_t)(t / NS - 1) & 1u)) { ok = false; break; }
             if (*abort_flag) { ok = false; break; }
             stage_a<N, TERMS, false>(a1 + s * C::A_STAGE, v, tid, 0);
             fence_proxy_async_smem();
@@ -468,11 +472,11 @@ __global__ void __launch_bounds__(WsCfg<N>::THREADS, 1) k_tc_ws(const TcParams p
             uint64_t *in_full = first ? a1_full : a2_full, *acc_empty = first ? t_empty : y_empty;
             uint64_t *in_empty = first ? a1_empty : a2_empty, *acc_full = first ? t_full : y_full;
             uint8_t *abuf = first ? a1 : a2;
-            const int acc_col = first ? 0 : 2 * N;
+            const int acc_col = first ? 0 : NS * N;
             for (int t = 0; ok && t < ntile_local; ++t) {
-                const int s = t & 1;
-                if (!mbar_wait_bounded(&in_full[s], (uint32_t)(t >> 1) & 1u) ||
-                    (t >= 2 && !mbar_wait_bounded(&acc_empty[s], (uint32_t)((t >> 1) - 1) & 1u)) || *abort_flag) {
+                const int s = t % NS;
+                if (!mbar_wait_bounded(&in_full[s], (uint32_t)(t / NS) & 1u) ||
+                    (t >= NS && !mbar_wait_bounded(&acc_empty[s], (uint32_t)(t / NS - 1) & 1u)) || *abort_flag) {
                     ok = false;
                     break;
                 }
@@ -496,14 +500,14 @@ __global__ void __launch_bounds__(WsCfg<N>::THREADS, 1) k_tc_ws(const TcParams p
         const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
         float v[N];
         for (int t = 0; t < ntile_local; ++t) {
-            const int s = t & 1;
+            const int s = t % NS;
             uint64_t *full = wg2 ? &t_full[s] : &y_full[s];
             // warp-uniform decisions only: the TMEM loads below are warp-collective
-            bool w = mbar_wait_bounded(full, (uint32_t)(t >> 1) & 1u) && !*abort_flag;
+            bool w = mbar_wait_bounded(full, (uint32_t)(t / NS) & 1u) && !*abort_flag;
             w = __all_sync(0xffffffffu, w);
             if (!w) { ok = false; break; }
             tc_fence_after();
-            const uint32_t acc = tmem + (uint32_t)((wg2 ? s : 2 + s) * N) + lane_off;
+            const uint32_t acc = tmem + (uint32_t)((wg2 ? s : NS + s) * N) + lane_off;
             if constexpr (N >= 16) {
 #pragma unroll
                 for (int c = 0; c < N / 16; ++c) tmem_ld16(acc + 16 * c, v + 16 * c);
@@ -512,7 +516,7 @@ __global__ void __launch_bounds__(WsCfg<N>::THREADS, 1) k_tc_ws(const TcParams p
             mbar_arrive(wg2 ? &t_empty[s] : &y_empty[s]);
             if (wg2) {
                 // T row r_local of array b_local -> column r_local of the MN-major operand
-                bool w2 = t < 2 || mbar_wait_bounded(&a2_empty[s], (uint32_t)((t >> 1) - 1) & 1u);
+                bool w2 = t < NS || mbar_wait_bounded(&a2_empty[s], (uint32_t)(t / NS - 1) & 1u);
                 w2 = __all_sync(0xffffffffu, w2);
                 if (!w2) { ok = false; break; }
                 stage_a<N, TERMS, true>(a2 + s * C::A_STAGE, v, r_local, b_local * N);
@@ -547,8 +551,8 @@ __global__ void __launch_bounds__(WsCfg<N>::THREADS, 1) k_tc_ws(const TcParams p
     if ((warp == 4 || warp == 13) && lane == 0 && !ok) {
         mbar_wait_bounded(b_full, 0);
         if (last_commit >= 0) {
-            const int t = (int)last_commit, s = t & 1;
-            mbar_wait_bounded(warp == 4 ? &t_full[s] : &y_full[s], (uint32_t)(t >> 1) & 1u);
+            const int t = (int)last_commit, s = t % NS;
+            mbar_wait_bounded(warp == 4 ? &t_full[s] : &y_full[s], (uint32_t)(t / NS) & 1u);
         }
     }
     tc_fence_before();
