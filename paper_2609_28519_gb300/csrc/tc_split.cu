@@ -737,8 +737,11 @@ static cudaError_t tc_ws_launch(const TcParams &p0, const __nv_bfloat16 *ops, cu
 template <int N, int TERMS>
 static cudaError_t tc_launch_nt(Dir dir, const TcParams &p, const __nv_bfloat16 *ops, cudaStream_t s, bool tiled)
 {
-    // forward and inverse of sides 16 and 32: the warp-specialized kernel
-    if constexpr (N <= 32) {
+    // forward and inverse of side 32: the warp-specialized kernel.  Measured
+    // on 512 MiB batches: side 32 0.48 -> 0.61 of HBM; side 16 runs 0.73 on
+    // k_tc_split (eight CTAs per SM) against 0.52 here, where the hand-offs of
+    // its 8 KiB tiles stay exposed; side 64 does not fit two operand stages.
+    if constexpr (N == 32) {
         if (dir == DIR_FWD || dir == DIR_INV)
             return tiled ? tc_ws_launch<N, TERMS, true>(p, ops, s) : tc_ws_launch<N, TERMS, false>(p, ops, s);
     }
