@@ -341,12 +341,13 @@ struct WsCfg {
     static constexpr int A_STAGE = 3 * A_TERM;
     static constexpr int B_BYTES = 3 * N * N * 2;
     static constexpr int THREADS = 14 * 32;
-    // operand stages and accumulators per phase (a deeper ring where tiles are small)
-    static constexpr int NS = N <= 16 ? 4 : 2;
+    // operand stages and accumulators per phase (a deeper ring where tiles are
+    // small; side 64 fits one)
+    static constexpr int NS = N <= 16 ? 4 : (N == 32 ? 2 : 1);
     static constexpr int NBAR = 8 * NS + 1;  // eight barriers per stage and the operator barrier
     // input rows in flight per loading thread (cp.async into its own padded
     // row slots: pitch N + 4 floats keeps a warp's 16-byte reads conflict-free)
-    static constexpr int D = N <= 16 ? 8 : 4;
+    static constexpr int D = N <= 16 ? 8 : (N == 32 ? 4 : 2);
     static constexpr int XP = N + 4;
     static constexpr int X_BYTES = D * 128 * XP * 4;
     static constexpr size_t SMEM = (size_t)2 * NS * A_STAGE + B_BYTES + X_BYTES + NBAR * 8 + 16;
@@ -737,11 +738,12 @@ static cudaError_t tc_ws_launch(const TcParams &p0, const __nv_bfloat16 *ops, cu
 template <int N, int TERMS>
 static cudaError_t tc_launch_nt(Dir dir, const TcParams &p, const __nv_bfloat16 *ops, cudaStream_t s, bool tiled)
 {
-    // forward and inverse of side 32: the warp-specialized kernel.  Measured
-    // on 512 MiB batches: side 32 0.48 -> 0.61 of HBM; side 16 runs 0.73 on
-    // k_tc_split (eight CTAs per SM) against 0.52 here, where the hand-offs of
-    // its 8 KiB tiles stay exposed; side 64 does not fit two operand stages.
-    if constexpr (N == 32) {
+    // forward and inverse of sides 32 and 64: the warp-specialized kernel.
+    // Measured on 512 MiB batches: side 32 0.48 -> 0.61 of HBM, side 64 (one
+    // operand stage per phase) 0.29 -> 0.49; side 16 runs 0.73 on k_tc_split
+    // (eight CTAs per SM) against 0.52 here, where the hand-offs of its 8 KiB
+    // tiles stay exposed.
+    if constexpr (N == 32 || N == 64) {
         if (dir == DIR_FWD || dir == DIR_INV)
             return tiled ? tc_ws_launch<N, TERMS, true>(p, ops, s) : tc_ws_launch<N, TERMS, false>(p, ops, s);
     }
