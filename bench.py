@@ -208,18 +208,19 @@ def source_key(kernel_key: str) -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_from_profiles(kernel_key: str):
-    """DRAM bytes per launch recorded by an ncu capture, if the kernel's
-    sources have not changed since (the record stores their source key)."""
+def traffic_from_profiles(kernel_key: str, column: int = 1):
+    """DRAM bytes per launch recorded by an ncu capture (column 1), or the L2
+    write bytes beside it (column 3), if the kernel's sources have not
+    changed since (the record stores their source key)."""
     p = os.path.join(ROOT, "profiles", "traffic_per_launch.txt")
     if not os.path.exists(p):
         return None
     key = source_key(kernel_key)
     for ln in open(p):
         parts = ln.split()
-        if len(parts) >= 3 and parts[0] == kernel_key and not ln.startswith("#"):
+        if len(parts) > max(2, column) and parts[0] == kernel_key and not ln.startswith("#"):
             if parts[2] == key:
-                return float(parts[1])
+                return float(parts[column])
     return None
 
 
@@ -377,6 +378,8 @@ def run_ours(args):
     achieved = elems * 8 / (dom_avg * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic_from_profiles(dom_key),
+                # the written output reaches L2 within the launch and DRAM after it
+                "traffic_l2_write": traffic_from_profiles(dom_key, 3),
                 "kernel": dom_key, "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
                 "avg_launch_us": {"forward": fwd_avg * 1e3, "inverse": inv_avg * 1e3},
                 "timing": "K back-to-back launches of the kernel alone (CUDA graph), same rotating pool"}
