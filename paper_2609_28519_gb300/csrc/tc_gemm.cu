@@ -61,7 +61,7 @@ struct TgCfg {
     static constexpr int B_TERM = NT * kTgKC * 2;    // bytes of one BF16 term of the operator chunk
     static constexpr int STAGE = 3 * A_TERM + 3 * B_TERM;
     static constexpr size_t SMEM = (size_t)kTgStages * STAGE + 4 * 8 + 16;
-    static constexpr int TMEM_COLS = 2 * NT < 32 ? 32 : 2 * NT;  // two chunk accumulators
+    static constexpr int TMEM_COLS = tmem_alloc_cols(2 * NT);  // two chunk accumulators
 };
 
 struct TgParams {
@@ -371,6 +371,7 @@ constexpr int kTg2Stages = 2;
 // TMEM partial accumulators (kTg2Acc x 128 columns of the 512): the MMA lane
 // may run kTg2Acc - 1 chunks ahead of the epilogue warps' reads
 constexpr int kTg2Acc = 4;
+static_assert(tmem_alloc_cols(kTg2Acc * 128) == kTg2Acc * 128 && kTg2Acc * 128 <= 512, "TMEM allocation");
 constexpr int kTg2AStage = 3 * 128 * kTgKC * 2;       // bytes of the input terms of a chunk
 constexpr int kTg2BStage = 3 * kTg2NT * kTgKC * 2;    // bytes of the operator terms of a chunk
 constexpr int kTg2Stage = kTg2AStage + kTg2BStage;

@@ -79,6 +79,15 @@ __device__ __forceinline__ void split3(float x, __nv_bfloat16 (&t)[3])
     }
 }
 
+// TMEM columns for an allocation of at least `cols`: tcgen05.alloc takes a
+// power of two from 32 to 512 (any other count is an illegal instruction).
+__host__ __device__ constexpr int tmem_alloc_cols(int cols)
+{
+    int c = 32;
+    while (c < cols) c *= 2;
+    return c;
+}
+
 // Byte offset of element (r, k) of a K-major operand with K = kdim columns,
 // in the no-swizzle canonical layout: core matrices of 8 rows x 16 bytes
 // stored as 128 contiguous bytes, K-adjacent cores 128 bytes apart (the

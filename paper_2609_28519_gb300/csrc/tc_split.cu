@@ -50,7 +50,7 @@ struct TcCfg {
     static constexpr int KSTEPS = N / 16;
     static constexpr int KMAJ_SBO = (N / 8) * 128;  // M/N-adjacent core stride, K-major
     static constexpr int MN_LBO = 16 * 128;         // K-adjacent core stride, MN-major (M = 128)
-    static constexpr int TMEM_COLS = 2 * N < 32 ? 32 : 2 * N;
+    static constexpr int TMEM_COLS = tmem_alloc_cols(2 * N);
 };
 
 struct TcParams {
@@ -343,7 +343,7 @@ struct WsCfg {
     static constexpr int THREADS = 14 * 32;
     // operand stages and accumulators per phase (a deeper ring where tiles are
     // small; side 64 fits one)
-    static constexpr int NS = N <= 16 ? 4 : (N == 32 ? 2 : 1);
+    static constexpr int NS = N <= 16 ? 4 : (N == 32 ? 3 : 1);
     static constexpr int NBAR = 8 * NS + 1;  // eight barriers per stage and the operator barrier
     // input rows in flight per loading thread (cp.async into its own padded
     // row slots: pitch N + 4 floats keeps a warp's 16-byte reads conflict-free)
@@ -351,7 +351,8 @@ struct WsCfg {
     static constexpr int XP = N + 4;
     static constexpr int X_BYTES = D * 128 * XP * 4;
     static constexpr size_t SMEM = (size_t)2 * NS * A_STAGE + B_BYTES + X_BYTES + NBAR * 8 + 16;
-    static constexpr int TMEM_COLS = 2 * NS * N < 32 ? 32 : 2 * NS * N;  // NS T and NS Y accumulators
+    static constexpr int TMEM_COLS = tmem_alloc_cols(2 * NS * N);  // NS T and NS Y accumulators
+    static_assert(TMEM_COLS <= 512, "TMEM");
 };
 
 template <int N, int TERMS, bool TILED>
