@@ -546,6 +546,251 @@ __global__ void __launch_bounds__(192, 1) k_tcg2(const Tg2Params p)
                      : "memory");
 }
 
+// ------------------------------------------------------------ 8 x 8 arrays
+// One product per direction with the 64 x 64 Kronecker operator over the
+// vectorized array (row-major 8 x 8 = 64 values), warp-specialized like
+// k_tcg2: tiles of 128 arrays (the MMA's M), K = N = 64.
+//   warps 0-3: each thread owns one array of the tile: cp.async copies of its
+//     64 values two tiles ahead into a padded row slot, the BF16 split into
+//     the K-major operand (row = array);
+//   warp 4, lane 0: the six products of a tile into one of two TMEM
+//     accumulators;
+//   warps 5-8: read the array's 64 outputs from TMEM (lane quadrant warp % 4),
+//     optionally times the diagonal, and store them (256 contiguous bytes).
+struct KronParams {
+    const float *src;
+    float *dst;
+    const long long *src_off, *dst_off;
+    long long count;                 // arrays
+    int ntiles;
+    const __nv_bfloat16 *ops;        // three terms of the 64 x 64 operator, K-major
+    const float *lam;                // optional: output n of an array times lam[n]
+    unsigned int *status;
+};
+
+constexpr int kKronNS = 2;                        // operand stages and accumulators
+constexpr int kKronD = 2;                         // input tiles in flight per loading thread
+constexpr int kKronATerm = 128 * 64 * 2;          // bytes of one BF16 term of a tile
+constexpr int kKronBBytes = 3 * 64 * 64 * 2;
+constexpr int kKronXP = 68;                       // padded row slot (floats)
+constexpr int kKronXBytes = kKronD * 128 * kKronXP * 4;
+constexpr int kKronNBar = 4 * kKronNS + 1;
+constexpr size_t kKronSmem = (size_t)kKronNS * 3 * kKronATerm + kKronBBytes + kKronXBytes + kKronNBar * 8 + 16;
+constexpr int kKronTmem = tmem_alloc_cols(kKronNS * 64);
+
+template <int TERMS>
+__global__ void __launch_bounds__(288, 1) k_tc_kron(const KronParams p)
+{
+    extern __shared__ __align__(1024) uint8_t ksm[];
+    uint8_t *abuf = ksm;
+    uint8_t *bop = ksm + kKronNS * 3 * kKronATerm;
+    float *xring = reinterpret_cast<float *>(bop + kKronBBytes);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(reinterpret_cast<uint8_t *>(xring) + kKronXBytes);
+    uint64_t *a_full = bar, *a_empty = bar + kKronNS, *d_full = bar + 2 * kKronNS, *d_empty = bar + 3 * kKronNS;
+    uint64_t *b_full = bar + 4 * kKronNS;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + kKronNBar);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int i = 0; i < kKronNS; ++i) {
+            mbar_init(&a_full[i], 128);
+            mbar_init(&a_empty[i], 1);
+            mbar_init(&d_full[i], 1);
+            mbar_init(&d_empty[i], 128);
+        }
+        mbar_init(b_full, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 4) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kKronTmem)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    pdl_launch_dependents();
+    pdl_wait_prerequisites();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int ntl = p.ntiles > (int)blockIdx.x ? (p.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x
+                                               : 0;
+    bool ok = true;
+    long long last_commit = -1;
+
+    if (warp < 4) {
+        // ---- loading and splitting: thread tid owns array (tile * 128 + tid)
+        auto arr_of = [&](int t) -> long long { return ((long long)blockIdx.x + (long long)t * gridDim.x) * 128 + tid; };
+        auto issue = [&](int t) {
+            if (t < ntl) {
+                const long long a = arr_of(t);
+                if (a < p.count) {
+                    const float *src = p.src + (p.src_off ? p.src_off[a] : a * 64);
+                    float *dst = xring + ((t % kKronD) * 128 + tid) * kKronXP;
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) cp_async16(dst + 4 * q, src + 4 * q);
+                }
+            }
+            cp_async_commit();  // one group per tile, empty past the end
+        };
+#pragma unroll 1
+        for (int t = 0; t < kKronD; ++t) issue(t);
+        float v[64];
+        for (int t = 0; t < ntl; ++t) {
+            cp_async_wait_group<kKronD - 1>();
+            if (arr_of(t) < p.count) {
+                const float4 *q4 = reinterpret_cast<const float4 *>(xring + ((t % kKronD) * 128 + tid) * kKronXP);
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const float4 x = q4[q];
+                    v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 64; ++j) v[j] = 0.0f;
+            }
+            issue(t + kKronD);
+            const int s = t % kKronNS;
+            if (t >= kKronNS && !mbar_wait_bounded(&a_empty[s], (uint32_t)(t / kKronNS - 1) & 1u)) { ok = false; break; }
+            if (*abort_flag) { ok = false; break; }
+            uint8_t *st = abuf + s * 3 * kKronATerm;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                __nv_bfloat16 tt[TERMS][8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    __nv_bfloat16 sp[3];
+                    split3<TERMS>(v[8 * q + e], sp);
+#pragma unroll
+                    for (int k = 0; k < TERMS; ++k) tt[k][e] = sp[k];
+                }
+                const int off = kmaj_off_bytes(tid, 8 * q, 64);
+#pragma unroll
+                for (int k = 0; k < TERMS; ++k)
+                    *reinterpret_cast<uint4 *>(st + k * kKronATerm + off) = *reinterpret_cast<const uint4 *>(tt[k]);
+            }
+            fence_proxy_async_smem();
+            mbar_arrive(&a_full[s]);
+        }
+        cp_async_wait_all();
+    } else if (warp == 4) {
+        // ---- MMA issue
+        if (lane == 0) {
+            mbar_arrive_expect_tx(b_full, kKronBBytes);
+            bulk_load(bop, p.ops, kKronBBytes, b_full);
+            if (!mbar_wait_bounded(b_full, 0)) ok = false;
+            constexpr uint32_t idesc = tc_idesc(64, false);
+            constexpr uint32_t sbo = 8 * 128;  // K = 64: eight core matrices along K
+            constexpr int pa[6] = {2, 1, 0, 1, 0, 0};
+            constexpr int pb[6] = {0, 1, 2, 0, 1, 0};
+            constexpr int first = TERMS == 3 ? 0 : (TERMS == 2 ? 3 : 5);
+            const uint32_t b0 = smem_u32(bop);
+            for (int t = 0; ok && t < ntl; ++t) {
+                const int s = t % kKronNS;
+                if (!mbar_wait_bounded(&a_full[s], (uint32_t)(t / kKronNS) & 1u) ||
+                    (t >= kKronNS && !mbar_wait_bounded(&d_empty[s], (uint32_t)(t / kKronNS - 1) & 1u)) || *abort_flag) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t a0 = smem_u32(abuf + s * 3 * kKronATerm);
+                const uint32_t d = tmem + (uint32_t)(s * 64);
+#pragma unroll
+                for (int pr = first; pr < 6; ++pr)
+#pragma unroll
+                    for (int ks = 0; ks < 4; ++ks)
+                        tc_mma(d, smem_desc(a0 + pa[pr] * kKronATerm + ks * 256, 128, sbo),
+                               smem_desc(b0 + pb[pr] * (64 * 64 * 2) + ks * 256, 128, sbo), idesc,
+                               (pr > first || ks > 0) ? 1u : 0u);
+                tc_commit(&a_empty[s]);
+                tc_commit(&d_full[s]);
+                last_commit = t;
+            }
+        }
+    } else {
+        // ---- TMEM read and store: thread = array (32 * (warp % 4) + lane) of the tile
+        const int row = 32 * (warp & 3) + lane;
+        const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+        float y[64];
+        for (int t = 0; t < ntl; ++t) {
+            const int s = t % kKronNS;
+            bool w = mbar_wait_bounded(&d_full[s], (uint32_t)(t / kKronNS) & 1u) && !*abort_flag;
+            w = __all_sync(0xffffffffu, w);
+            if (!w) { ok = false; break; }
+            tc_fence_after();
+#pragma unroll
+            for (int c = 0; c < 4; ++c) tmem_ld16(tmem + (uint32_t)(s * 64) + lane_off + 16 * c, y + 16 * c);
+            tc_fence_before();
+            mbar_arrive(&d_empty[s]);
+            const long long a = ((long long)blockIdx.x + (long long)t * gridDim.x) * 128 + row;
+            if (a < p.count) {
+                if (p.lam) {
+#pragma unroll
+                    for (int j = 0; j < 64; ++j) y[j] *= __ldg(p.lam + j);
+                }
+                float4 *d4 = reinterpret_cast<float4 *>(p.dst + (p.dst_off ? p.dst_off[a] : a * 64));
+#pragma unroll
+                for (int q = 0; q < 16; ++q) d4[q] = make_float4(y[4 * q], y[4 * q + 1], y[4 * q + 2], y[4 * q + 3]);
+            }
+        }
+    }
+    if (!ok) {
+        *abort_flag = 1;
+        if (lane == 0) record_timeout(p.status);
+    }
+    // error path: the MMA lane waits (bounded) for the operator copy and its
+    // last committed products before shared memory and TMEM are released
+    if (warp == 4 && lane == 0 && !ok) {
+        mbar_wait_bounded(b_full, 0);
+        if (last_commit >= 0)
+            mbar_wait_bounded(&d_full[last_commit % kKronNS], (uint32_t)(last_commit / kKronNS) & 1u);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 4)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kKronTmem) : "memory");
+}
+
+template <int TERMS>
+static cudaError_t kron_launch(const KronParams &p0, cudaStream_t stream)
+{
+    static DeviceLaunchCache cache;
+    int dev = 0, bps = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    auto kern = k_tc_kron<TERMS>;
+    e = cache.get(
+        dev,
+        [&](int d, int &b, int &n) {
+            cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kKronSmem);
+            if (r == cudaSuccess) r = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d);
+            b = 1;
+            if (r == cudaSuccess && debug_enabled())
+                fprintf(stderr, "[bdct] k_tc_kron<%d>: 1 CTA/SM x 288 threads, smem %zu B, TMEM %d cols\n", TERMS,
+                        kKronSmem, kKronTmem);
+            return r;
+        },
+        &bps, &sms);
+    if (e != cudaSuccess) return e;
+    KronParams p = p0;
+    long long grid = sms;
+    if (grid > p.ntiles) grid = p.ntiles;
+    if (grid <= 0) return cudaSuccess;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(288);
+    cfg.dynamicSmemBytes = kKronSmem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, p);
+}
+
 // ------------------------------------------------------------ operator tables
 // Operator M (N = K = n, or the 64 x 64 Kronecker operator of 8 x 8 arrays)
 // for direction 1 (forward: M[f][j] = s_f cos(pi (2j+1) f / 2n)) or 2
@@ -761,6 +1006,18 @@ cudaError_t tg_pass(const float *src, float *dst, const long long *src_off, cons
     const int NT = tg_nt(N), KC = tg_kc(K);
     if (!NT || !KC || R < 1) return cudaErrorInvalidValue;
     if (src == dst) return cudaErrorInvalidValue;  // a pass never runs in place
+    if (R == 1 && K == 64) {
+        // 8 x 8 arrays: the Kronecker pass (the table of a 64-point operator
+        // is one block: the three terms in the K-major layout)
+        const long long nt = (count + 127) / 128;
+        if (nt > 0x7ff00000LL) return cudaErrorInvalidValue;
+        KronParams kp{src, dst, src_off, dst_off, count, (int)nt, ops, lam, status};
+        switch (terms) {
+            case 3: return kron_launch<3>(kp, stream);
+            case 2: return kron_launch<2>(kp, stream);
+            default: return kron_launch<1>(kp, stream);
+        }
+    }
     if (tg_use_v2(K)) {
         if (!abuf) return cudaErrorInvalidValue;
         Tg2Params p{};
