@@ -689,406 +689,6 @@ __global__ void __launch_bounds__(RingCfg<H, W, DIR>::THREADS, 1) k_ring(const _
     }
 }
 
-// ---------------------------------------------------------------- 128 x 128 on CTA pairs
-// The 128 x 128 ring kernel is bound by the warps whose latency overlaps:
-// three 64 KiB slots fill shared memory and feed one group of eight warps.
-// Here an array is shared by the two CTAs of a cluster, each holding half of
-// it (32 KiB), so each SM runs three groups of four warps over six slots:
-//  1. each CTA loads its column half (columns 64 r .. 64 r + 63, all 128
-//     rows; TMA boxes of 32 columns x 128 rows) and transforms its 64
-//     columns (128-point lines, two threads each);
-//  2. the CTAs swap quarters through distributed shared memory: CTA r keeps
-//     rows 64 r .. 64 r + 63 of its columns and sends the other 64 rows to
-//     the partner, receiving the partner's columns of its own rows into the
-//     space it sent from.  With 32-column boxes of 64 rows placed at byte
-//     offset (g & 1) * 16 KiB + (g >> 1) * 8 KiB for column group g, the
-//     kept quarters stay where the load put them and each received quarter
-//     lands on the swizzle pattern its rows need (rows keep their index mod
-//     8), so the swap is two plain 8 KiB copies per direction;
-//  3. each CTA transforms its 64 rows (128-point lines, two threads each),
-//     writing natural column order, and stores them (TMA boxes of 32 columns
-//     x 64 rows).
-// Every thread of a group arrives on the partner's barrier (release at
-// cluster scope) after reading what it sends and again after writing it; the
-// partner's threads wait with acquire at cluster scope, so each read and
-// write is ordered with the other side's.  Contiguous batches, forward and
-// inverse (the round trip keeps the one-CTA kernel: its role cores need more
-// registers than three groups of four warps can have).
-
-constexpr int kRcS = 6;                       // half-array slots per CTA
-constexpr int kRcNG = 3;                      // consumer groups of four warps
-constexpr int kRcThreads = (kRcNG * 4 + 1) * 32;
-constexpr int kRcSlot = 32768;
-constexpr size_t kRcSmem = 1024 + (size_t)kRcS * kRcSlot + 4 * kRcS * 8;
-
-__device__ __forceinline__ uint32_t cluster_rank()
-{
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-
-// Cluster-wide barrier of every thread (the non-aligned form: a warp may reach
-// it from divergent paths).
-__device__ __forceinline__ void cluster_sync_all()
-{
-    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
-}
-
-// shared::cluster address of the same shared-memory location in CTA `rank`
-__device__ __forceinline__ uint32_t map_rank(uint32_t saddr, uint32_t rank)
-{
-    uint32_t r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
-    return r;
-}
-
-__device__ __forceinline__ void st_cluster_f4(uint32_t caddr, float4 v)
-{
-    asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(caddr), "f"(v.x), "f"(v.y), "f"(v.z),
-                 "f"(v.w)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_cluster(uint32_t caddr)
-{
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(caddr) : "memory");
-}
-
-// Bounded wait with acquire at cluster scope (the arrivals come from the
-// partner CTA).
-__device__ __forceinline__ bool mbar_wait_cluster(uint64_t *bar, uint32_t parity)
-{
-    const unsigned long long t0 = global_ns();
-    while (true) {
-        uint32_t ok;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(ok)
-            : "r"(smem_u32(bar)), "r"(parity), "r"(100000u)
-            : "memory");
-        if (ok) return true;
-        if (global_ns() - t0 > kWaitLimitNs) return false;
-    }
-}
-
-// Column pass of a 128-row x 64-column half (boxes of 32 columns x 128 rows),
-// natural positions in and out.
-template <int DIR>
-__device__ __forceinline__ void cl_cols(char *slot, int gt, int bar, AxisScale s)
-{
-    const int role = role_of(gt);
-    const int ln = line_of(gt);  // column 0..63 of the half
-    const ColView<128> cv(ln);
-    float v[64];
-    if constexpr (DIR == DIR_INV) {
-        // even rows (role 0) or odd rows (role 1)
-        if (role == 0) {
-#pragma unroll
-            for (int m = 0; m < 64; ++m) v[m] = at<float>(slot, 2 * m * 128 + cv.o[(2 * m) & 7]);
-        } else {
-#pragma unroll
-            for (int m = 0; m < 64; ++m) v[m] = at<float>(slot, (2 * m + 1) * 128 + cv.o[(2 * m + 1) & 7]);
-        }
-        scale_from<64>(v, role ? s.s1 : s.s0, s.s1);
-    } else {
-        const float sg = role ? -1.0f : 1.0f;
-#pragma unroll
-        for (int i = 0; i < 64; ++i)
-            v[i] = fmaf(sg, at<float>(slot, (127 - i) * 128 + cv.o[(127 - i) & 7]), at<float>(slot, i * 128 + cv.o[i & 7]));
-    }
-    group_sync(bar, 128);  // every read done before anything is overwritten
-    float y[64];
-    role_core<DIR>(role, v, y, s);
-    if constexpr (DIR == DIR_FWD) {
-        // rows 2m (role 0) or 2m + 1 (role 1)
-        if (role == 0) {
-#pragma unroll
-            for (int m = 0; m < 64; ++m) at<float>(slot, 2 * m * 128 + cv.o[(2 * m) & 7]) = y[m];
-        } else {
-#pragma unroll
-            for (int m = 0; m < 64; ++m) at<float>(slot, (2 * m + 1) * 128 + cv.o[(2 * m + 1) & 7]) = y[m];
-        }
-    } else {
-        if (role == 0) {
-#pragma unroll
-            for (int j = 0; j < 64; ++j) at<float>(slot, j * 128 + cv.o[j & 7]) = y[j];  // a_j at row j
-        } else {
-#pragma unroll
-            for (int j = 0; j < 64; ++j) at<float>(slot, (127 - j) * 128 + cv.o[(127 - j) & 7]) = y[j];  // b_j at 127-j
-        }
-        group_sync(bar, 128);
-        // x_j = a_j + b_j, x_{127-j} = a_j - b_j; two threads per column, 32 pairs each
-        auto comb = [&](int j) {
-            const uint32_t oa = j * 128 + cv.o[j & 7], ob = (127 - j) * 128 + cv.o[(127 - j) & 7];
-            const float a = at<float>(slot, oa), b = at<float>(slot, ob);
-            at<float>(slot, oa) = a + b;
-            at<float>(slot, ob) = a - b;
-        };
-        if (role == 0) {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) comb(j);
-        } else {
-#pragma unroll
-            for (int j = 32; j < 64; ++j) comb(j);
-        }
-    }
-    group_sync(bar, 128);
-}
-
-// Byte offset of the 64-row box of column group g (32 columns) in the row half.
-__device__ __forceinline__ uint32_t cl_goff(int g) { return (uint32_t)((g & 1) * 16384 + (g >> 1) * 8192); }
-
-// Row pass of a 64-row x 128-column half, natural positions in and out.
-template <int DIR>
-__device__ __forceinline__ void cl_rows(char *slot, int gt, int bar, AxisScale s)
-{
-    const int role = role_of(gt);
-    const int r = line_of(gt);  // row 0..63 of the half
-    const RowView rv(r);
-    float v[64];
-    if constexpr (DIR == DIR_INV) {
-        // role 0: even coefficients, role 1: odd coefficients
-#pragma unroll
-        for (int k = 0; k < 32; ++k) {
-            const float4 t = at<float4>(slot, cl_goff(k >> 3) + rv.o[k & 7]);
-            v[2 * k] = role ? t.y : t.x;
-            v[2 * k + 1] = role ? t.w : t.z;
-        }
-        scale_from<64>(v, role ? s.s1 : s.s0, s.s1);
-    } else {
-        // sums (role 0) or differences (role 1) of x_j and x_{127-j}
-        const float sg = role ? -1.0f : 1.0f;
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            const float4 a = at<float4>(slot, cl_goff(k >> 3) + rv.o[k & 7]);
-            const float4 b = at<float4>(slot, cl_goff((31 - k) >> 3) + rv.o[(31 - k) & 7]);
-            v[4 * k] = fmaf(sg, b.w, a.x);
-            v[4 * k + 1] = fmaf(sg, b.z, a.y);
-            v[4 * k + 2] = fmaf(sg, b.y, a.z);
-            v[4 * k + 3] = fmaf(sg, b.x, a.w);
-        }
-    }
-    group_sync(bar, 128);
-    float y[64];
-    role_core<DIR>(role, v, y, s);
-    if constexpr (DIR == DIR_FWD) {
-        // Y_{2m} (role 0) at position 2m, Y_{2m+1} (role 1) at 2m + 1
-#pragma unroll
-        for (int m = 0; m < 64; ++m) {
-            const int pos = 2 * m + role, k = pos >> 2;
-            at<float>(slot, cl_goff(k >> 3) + rv.o[k & 7] + 4 * (pos & 3)) = y[m];
-        }
-    } else {
-        // a_j (role 0) at position j, b_j (role 1) at 64 + j, then combined in
-        // place: x_j = a_j + b_j at j, x_{127-j} = a_j - b_j at 127 - j.  One
-        // thread takes the chunks of j and of j' = 60 - j (4 values each): the
-        // four chunks it reads are exactly the four it writes.
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            const int kk = 16 * role + k;
-            at<float4>(slot, cl_goff(kk >> 3) + rv.o[kk & 7]) = make_float4(y[4 * k], y[4 * k + 1], y[4 * k + 2], y[4 * k + 3]);
-        }
-        group_sync(bar, 128);
-#pragma unroll
-        for (int t = gt; t < 64 * 8; t += 128) {
-            const int rr = t >> 3, q = t & 7;  // row, pair (chunks q and 15 - q)
-            const RowView w(rr);
-            const uint32_t oa = cl_goff(q >> 3) + w.o[q & 7];
-            const uint32_t ob = cl_goff((16 + q) >> 3) + w.o[(16 + q) & 7];
-            const uint32_t oa2 = cl_goff((15 - q) >> 3) + w.o[(15 - q) & 7];
-            const uint32_t ob2 = cl_goff((31 - q) >> 3) + w.o[(31 - q) & 7];
-            const float4 a = at<float4>(slot, oa), b = at<float4>(slot, ob);
-            const float4 a2 = at<float4>(slot, oa2), b2 = at<float4>(slot, ob2);
-            at<float4>(slot, oa) = make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
-            at<float4>(slot, oa2) = make_float4(a2.x + b2.x, a2.y + b2.y, a2.z + b2.z, a2.w + b2.w);
-            // positions 124 - 4q .. 127 - 4q (chunk 31 - q): x_{127-j} .. x_{124-j} reversed
-            at<float4>(slot, ob2) = make_float4(a.w - b.w, a.z - b.z, a.y - b.y, a.x - b.x);
-            at<float4>(slot, ob) = make_float4(a2.w - b2.w, a2.z - b2.z, a2.y - b2.y, a2.x - b2.x);
-        }
-    }
-    group_sync(bar, 128);
-}
-
-struct RingCParams {
-    CUtensorMap map_in, map_out;  // boxes of 32 columns x 128 rows (loads) and x 64 rows (stores)
-    long long count;
-    DirScales sc;
-    unsigned int *status;
-};
-
-template <int DIR>
-__global__ void __launch_bounds__(kRcThreads, 1) k_ring_cl(const __grid_constant__ RingCParams p)
-{
-    extern __shared__ __align__(1024) unsigned char rc_raw[];
-    const uint32_t raw = smem_u32(rc_raw);
-    char *smem = reinterpret_cast<char *>(rc_raw) + (((raw + 1023u) & ~1023u) - raw);
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + kRcS * kRcSlot);
-    uint64_t *done = full + kRcS, *xfree = done + kRcS, *xfull = xfree + kRcS;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t rank = cluster_rank(), partner = rank ^ 1u;
-    const long long ncl = gridDim.x >> 1, cl = blockIdx.x >> 1;
-    const int n = cl < p.count ? (int)((p.count - cl + ncl - 1) / ncl) : 0;
-
-    if (tid == 0) {
-        for (int s = 0; s < kRcS; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&done[s], 1);
-            mbar_init(&xfree[s], 128);  // every thread of the partner's group
-            mbar_init(&xfull[s], 128);
-        }
-        fence_mbar_init();
-    }
-    pdl_launch_dependents();
-    pdl_wait_prerequisites();
-    cluster_sync_all();  // the partner's barriers exist before anyone arrives on them
-
-    if (warp == kRcNG * 4) {
-        // ---------------- producer (lane 0): column halves in, row halves out
-        if (lane == 0) {
-            bool ok = true;
-            int filled = 0, consumed = 0;
-            auto fill = [&](int j) {
-                const int s = j % kRcS;
-                char *slot = smem + s * kRcSlot;
-                const int y = (int)((cl + (long long)j * ncl) * 128);
-                mbar_arrive_expect_tx(&full[s], (uint32_t)kRcSlot);
-                tensor_load_2d(slot, &p.map_in, 64 * (int)rank, y, &full[s]);
-                tensor_load_2d(slot + 16384, &p.map_in, 64 * (int)rank + 32, y, &full[s]);
-            };
-            const int pro = n < kRcS ? n : kRcS;
-            for (int j = 0; j < pro; ++j) fill(j);
-            filled = pro;
-            for (int j = 0; j < n; ++j) {
-                const int s = j % kRcS;
-                if (!mbar_wait_bounded(&done[s], (uint32_t)((j / kRcS) & 1))) {
-                    record_timeout(p.status);
-                    ok = false;
-                    break;
-                }
-                consumed = j + 1;
-                const char *slot = smem + s * kRcSlot;
-                const int y = (int)((cl + (long long)j * ncl) * 128) + 64 * (int)rank;
-#pragma unroll
-                for (int g = 0; g < 4; ++g) tensor_store_2d(&p.map_out, 32 * g, y, slot + cl_goff(g));
-                bulk_commit();
-                if (j >= 1 && j - 1 + kRcS < n) {
-                    bulk_wait_read<1>();
-                    fill(j - 1 + kRcS);
-                    filled = j + kRcS;
-                }
-            }
-            bulk_wait<0>();
-            if (!ok)  // loads issued for halves never consumed land (bounded) before the CTA exits
-                for (int j = consumed; j < filled; ++j)
-                    if (!mbar_wait_bounded(&full[j % kRcS], (uint32_t)((j / kRcS) & 1))) break;
-        }
-    } else {
-        // ---------------- consumers
-        const int g = warp / 4;
-        const int gt = tid - 128 * g;
-        const int bar = 1 + g;
-        const uint32_t send0 = 8192u * (1u - rank), recv0 = 8192u * rank;
-        for (int j = g; j < n; j += kRcNG) {
-            const int s = j % kRcS;
-            const uint32_t ph = (uint32_t)((j / kRcS) & 1);
-            bool ok = mbar_wait_bounded(&full[s], ph);
-            ok = group_and(bar, 128, ok);
-            if (!ok) {
-                if (gt == 0) record_timeout(p.status);
-                break;
-            }
-            char *slot = smem + s * kRcSlot;
-            cl_cols<DIR>(slot, gt, bar, p.sc.h);
-            // ---- swap the quarters with the partner (two 8 KiB regions)
-            float4 q[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int e = gt + 128 * i;  // 16-byte unit of the 16 KiB sent
-                q[i] = at<float4>(slot, (e < 512 ? send0 : send0 + 16384u) + (uint32_t)(e & 511) * 16u);
-            }
-            mbar_arrive_cluster(map_rank(smem_u32(&xfree[s]), partner));
-            ok = mbar_wait_cluster(&xfree[s], ph);  // the partner has read what it sends
-            ok = group_and(bar, 128, ok);
-            if (!ok) {
-                if (gt == 0) record_timeout(p.status);
-                break;
-            }
-            const uint32_t base = map_rank(smem_u32(slot), partner);
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int e = gt + 128 * i;
-                st_cluster_f4(base + (e < 512 ? recv0 : recv0 + 16384u) + (uint32_t)(e & 511) * 16u, q[i]);
-            }
-            mbar_arrive_cluster(map_rank(smem_u32(&xfull[s]), partner));
-            ok = mbar_wait_cluster(&xfull[s], ph);  // the partner's quarter is in place
-            ok = group_and(bar, 128, ok);
-            if (!ok) {
-                if (gt == 0) record_timeout(p.status);
-                break;
-            }
-            cl_rows<DIR>(slot, gt, bar, p.sc.w);
-            fence_proxy_async_smem();  // the TMA store reads the slot through the async proxy
-            group_sync(bar, 128);
-            if (gt == 0) mbar_arrive(&done[s]);
-        }
-    }
-    // no CTA leaves while its partner may still write into it or arrive on it
-    cluster_sync_all();
-}
-
-template <int DIR>
-static cudaError_t ring_cl_launch(const DirScales &sc, const ExecGeom &g, unsigned int *status, cudaStream_t stream)
-{
-    auto kern = k_ring_cl<DIR>;
-    static DeviceLaunchCache cache;
-    int dev = 0, bps = 0, sms = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    e = cache.get(
-        dev,
-        [&](int d, int &b, int &n) {
-            cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRcSmem);
-            if (r == cudaSuccess) r = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d);
-            b = 1;
-            if (r == cudaSuccess && debug_enabled())
-                fprintf(stderr, "[bdct] k_ring_cl<%d>: CTA pairs, %d half slots, %d groups x 4 warps + producer, smem %zu B\n",
-                        DIR, kRcS, kRcNG, kRcSmem);
-            return r;
-        },
-        &bps, &sms);
-    if (e != cudaSuccess) return e;
-    if (g.count <= 0) return cudaSuccess;
-    RingCParams p{};
-    p.count = g.count;
-    p.sc = sc;
-    p.status = status;
-    const unsigned long long rows = (unsigned long long)g.count * 128;
-    e = tma_map_2d(&p.map_in, g.in, rows, 128, 128, 128);
-    if (e == cudaSuccess) e = tma_map_2d(&p.map_out, g.out, rows, 128, 128, 64);
-    if (e != cudaSuccess) return e;
-    long long clusters = sms / 2;
-    if (clusters > g.count) clusters = g.count;
-    if ((g.count + clusters - 1) / clusters > 0x7fffff00LL) return cudaErrorInvalidValue;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(2 * clusters));
-    cfg.blockDim = dim3(kRcThreads);
-    cfg.dynamicSmemBytes = kRcSmem;
-    cfg.stream = stream;
-    cudaLaunchAttribute attr[2];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[1].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 2;
-    return cudaLaunchKernelEx(&cfg, kern, p);
-}
-
 // ---------------------------------------------------------------- host side
 template <int H, int W, int DIR>
 static cudaError_t ring_launch_one(const DirScales &sc, const ExecGeom &g, unsigned int *status,
@@ -1175,14 +775,7 @@ cudaError_t ring_launch(int rows, int cols, Dir dir, const DirScales &sc, const 
     if (rows == 64 && cols == 64) return ring_dir<64, 64>(dir, sc, g, status, stream);
     if (rows == 64 && cols == 128) return ring_dir<64, 128>(dir, sc, g, status, stream);
     if (rows == 128 && cols == 64) return ring_dir<128, 64>(dir, sc, g, status, stream);
-    if (rows == 128 && cols == 128) {
-        // contiguous forward and inverse on CTA pairs (round trips, image tiles
-        // and indexed arrays on the one-CTA kernel)
-        if (!g.tiled && !g.in_off && !g.out_off && (dir == DIR_FWD || dir == DIR_INV))
-            return dir == DIR_FWD ? ring_cl_launch<DIR_FWD>(sc, g, status, stream)
-                                  : ring_cl_launch<DIR_INV>(sc, g, status, stream);
-        return ring_dir<128, 128>(dir, sc, g, status, stream);
-    }
+    if (rows == 128 && cols == 128) return ring_dir<128, 128>(dir, sc, g, status, stream);
     return cudaErrorInvalidValue;
 }
 
