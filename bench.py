@@ -440,6 +440,7 @@ def run_ours(args):
             "square_sweep_512MiB": sweep_summary(dev, [8, 16, 32, 64, 128, 256], 512, ("auto", "split_tc"),
                                                  check=not args.no_check),
             "ragged_4096": ragged_summary(dev),
+            "odd_sides_256MiB": odd_sides_summary(dev, check=not args.no_check),
             "boundary_diagnostics": boundary_summary(dev) if not args.no_check else None,
             "large_arrays": large_summary(dev),
         }
@@ -491,6 +492,42 @@ def _time_calls(fn, stream, reps, warm=3):
     b.record(stream)
     torch.cuda.synchronize()
     return a.elapsed_time(b) / reps
+
+
+def odd_sides_summary(dev, shapes=((26, 32), (24, 40), (48, 48)), mib=256, check=True):
+    """Small arrays with non-power-of-two sides (the paper's 26 among them),
+    which no fused kernel covers: forward / inverse / round trip on a
+    uniform[-1,1] batch of about mib MiB, sampled outputs against the FP64
+    oracle."""
+    import torch
+    import oracle
+    from paper_2609_28519_gb300 import Plan
+    peak, _ = _peaks()
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for h, w in shapes:
+        batch = max(1, (mib << 20) // (4 * h * w))
+        x = torch.empty((batch, h, w), dtype=torch.float32, device=dev)
+        x.uniform_(-1.0, 1.0, generator=torch.Generator(device=dev).manual_seed(3500 + h + w))
+        y = torch.empty_like(x)
+        plan = Plan(h, w, path="fp32")
+        ent = {"batch": batch, "variant": plan.info().variant, "workspace_bytes": plan.info().workspace_bytes}
+        for kind in ("forward", "inverse", "roundtrip"):
+            ms = _time_calls(lambda st: plan.execute(kind, x, y, st), stream, 5)
+            gbs = batch * h * w * 8 / (ms * 1e-3) / 1e9
+            ent[kind] = {"ms": ms, "GB/s": gbs, "frac": gbs / peak}
+            if check:
+                idx = np.array([0, batch // 2, batch - 1])
+                xs = x[idx].cpu().numpy()
+                ys = y[idx].cpu().numpy()
+                ref = {"forward": lambda a: oracle.forward(a, 0), "inverse": lambda a: oracle.inverse(a, 0),
+                       "roundtrip": lambda a: a.astype(np.float64)}[kind](xs)
+                m = oracle.metrics(ys, ref, xs)
+                ent[kind]["e_rel_max"] = m["e_rel_max"]
+                ent[kind]["accepted"] = bool(oracle.accept(m))
+        out[f"{h}x{w}"] = ent
+        plan.close()
+    return out
 
 
 def sweep_summary(dev, sizes, mib=512, paths=("auto",), check=True, emit=None):

@@ -159,8 +159,10 @@ int bdct_execute(const bdct_plan *plan, unsigned kind, const float *in, float *o
  * the same block of `out` (leading dimension ld_out).  img_rows and img_cols
  * must be multiples of the plan's rows and cols; ld_in and ld_out multiples
  * of 4.  in == out with ld_in == ld_out is exact in place; any other overlap
- * is BDCT_ERR_ALIAS.  Only fused on-chip and tensor-core variants support it
- * (else BDCT_ERR_PATH).                                                     */
+ * is BDCT_ERR_ALIAS.  The on-chip kernels support it: the fused FP32 and
+ * tensor-core variants, and the dense route of small blocks (variant 2 with
+ * both sides at most 64, e.g. 24 x 40 blocks); other plans return
+ * BDCT_ERR_PATH.                                                            */
 int bdct_execute_tiled(const bdct_plan *plan, unsigned kind, const float *in, float *out,
                        int img_rows, int img_cols, size_t ld_in, size_t ld_out, void *stream);
 
@@ -193,8 +195,10 @@ typedef struct bdct_plan_info {
     unsigned kind;
     int norm;
     int path;              /* resolved path (never AUTO) */
-    int variant;           /* kernel family: 1 fused register tile, 2 separable passes, 3 tensor core
-                              on chip, 4 tensor-core separable passes */
+    int variant;           /* kernel family: 1 fused register tile, 2 separable passes (FFT line
+                              engine, dense passes, or -- both sides at most 64 and no fused kernel
+                              -- the dense operators applied in shared memory, one read and one
+                              write), 3 tensor core on chip, 4 tensor-core separable passes */
     size_t workspace_bytes;
     size_t table_bytes;
 } bdct_plan_info;
@@ -209,8 +213,9 @@ int bdct_plan_get_info(const bdct_plan *plan, bdct_plan_info *info);
  * the intermediate from L2 instead of HBM, while every chunk costs two pass
  * launches with their ramp-up and drain (which measured the larger effect).
  * The default is 256 MiB; the ragged autotuner picks it per shape class.
- * No work using the plan may be queued.  Other variants keep no workspace
- * and ignore the call (BDCT_OK).                                           */
+ * No work using the plan may be queued.  Other variants (and the on-chip
+ * dense route of small arrays) keep no workspace and ignore the call
+ * (BDCT_OK).                                                               */
 int bdct_plan_set_chunk_bytes(bdct_plan *plan, size_t bytes);
 
 /* Synchronize the device and return the plan's device-side status: BDCT_OK,

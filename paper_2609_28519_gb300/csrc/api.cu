@@ -13,6 +13,7 @@
 
 #include "bdct_internal.h"
 #include "plan.h"
+#include "small_dense.h"
 
 using namespace bdct;
 
@@ -301,14 +302,19 @@ extern "C" int bdct_plan_create(bdct_plan **plan, int rows, int cols, unsigned k
             (void)ih; (void)iw;  // located at fh + per_dir
         }
         if (e != cudaSuccess) { plan_free(p); return cuda_fail(e); }
-        const size_t arr_bytes = (size_t)rows * cols * sizeof(float);
-        long long chunk = (long long)(kChunkBytes / arr_bytes);
-        if (chunk < 1) chunk = 1;
-        p->chunk_arrays = chunk;
-        const int nbuf = (kind & (BDCT_ROUNDTRIP | BDCT_SPECTRAL)) ? 2 : 1;
-        p->work_bytes = (size_t)chunk * arr_bytes * nbuf;
-        e = cudaMalloc(&p->work, p->work_bytes);
-        if (e != cudaSuccess) { plan_free(p); t_last_cuda_error = (int)e; return BDCT_ERR_NO_MEMORY; }
+        if (small_dense_supported(rows, cols)) {
+            // every pass in shared memory (small_dense.cu): no workspace
+            p->small = true;
+        } else {
+            const size_t arr_bytes = (size_t)rows * cols * sizeof(float);
+            long long chunk = (long long)(kChunkBytes / arr_bytes);
+            if (chunk < 1) chunk = 1;
+            p->chunk_arrays = chunk;
+            const int nbuf = (kind & (BDCT_ROUNDTRIP | BDCT_SPECTRAL)) ? 2 : 1;
+            p->work_bytes = (size_t)chunk * arr_bytes * nbuf;
+            e = cudaMalloc(&p->work, p->work_bytes);
+            if (e != cudaSuccess) { plan_free(p); t_last_cuda_error = (int)e; return BDCT_ERR_NO_MEMORY; }
+        }
     }
     e = cudaDeviceSynchronize();
     if (e != cudaSuccess) { plan_free(p); return cuda_fail(e); }
@@ -366,9 +372,31 @@ static int run_lines(const bdct_plan *p, Dir dir, const DirScales &sc, const flo
     return BDCT_OK;
 }
 
+// The dense route in shared memory (both sides at most 64): rows then
+// columns (forward, inverse), and for the round trip and the spectral
+// direction the adjoint columns then rows after them, Lambda in between --
+// the passes of run_separable without the workspace.
+static int run_small(const bdct_plan *p, Dir dir, const ExecGeom &g, cudaStream_t s)
+{
+    const int h = p->rows, w = p->cols;
+    const Dir mdir = dir == DIR_SPEC ? DIR_RT : dir;  // the spectral direction uses the orthonormal pair
+    const float *oph = p->ops + p->op_h_off[mdir];
+    const float *opw = p->ops + p->op_w_off[mdir];
+    const size_t per_dir = (size_t)h * h + (size_t)w * w;
+    const bool pair = dir == DIR_RT || dir == DIR_SPEC;
+    const int axis[4] = {0, 1, 1, 0};
+    const float *ops[4] = {opw, oph, oph + per_dir, opw + per_dir};
+    cudaError_t e = small_dense_run(h, w, pair ? 4 : 2, axis, ops, dir == DIR_SPEC ? p->spec_plain : nullptr, g, s);
+    return e == cudaSuccess ? BDCT_OK : cuda_fail(e);
+}
+
 static int run_separable(const bdct_plan *p, Dir dir, const float *in, const long long *in_off, float *out,
                          const long long *out_off, long long count, cudaStream_t s)
 {
+    if (p->small) {
+        ExecGeom g{in, out, count, 0, 0, 0, 0, in_off, out_off};
+        return run_small(p, dir, g, s);
+    }
     const int h = p->rows, w = p->cols;
     const long long hw = (long long)h * w;
     const Dir mdir = dir == DIR_SPEC ? DIR_RT : dir;  // the spectral direction uses the orthonormal pair
@@ -611,7 +639,7 @@ extern "C" int bdct_execute_tiled(const bdct_plan *plan, unsigned kind, const fl
     if (img_rows % plan->rows || img_cols % plan->cols) return BDCT_ERR_UNSUPPORTED_SHAPE;
     if (ld_in < (size_t)img_cols || ld_out < (size_t)img_cols) return BDCT_ERR_INVALID_ARG;
     if ((((uintptr_t)in | (uintptr_t)out) & 15u) || (ld_in % 4) || (ld_out % 4)) return BDCT_ERR_ALIGN;
-    if (plan->variant != 1 && plan->variant != 3) return BDCT_ERR_PATH;
+    if (plan->variant != 1 && plan->variant != 3 && !plan->small) return BDCT_ERR_PATH;
     const size_t span_in = ((size_t)(img_rows - 1) * ld_in + img_cols) * sizeof(float);
     const size_t span_out = ((size_t)(img_rows - 1) * ld_out + img_cols) * sizeof(float);
     if (in != out) {
@@ -624,7 +652,11 @@ extern "C" int bdct_execute_tiled(const bdct_plan *plan, unsigned kind, const fl
     const int tpr = img_cols / plan->cols;
     const long long tiles = (long long)(img_rows / plan->rows) * tpr;
     ExecGeom g{in, out, tiles, 1, tpr, (long long)ld_in, (long long)ld_out};
-    if (!plan->rp_bits) return run_onchip(plan, dir, g, (cudaStream_t)stream);
+    auto run_tiles = [&](const ExecGeom &gg) {
+        return plan->small ? run_small(plan, dir, gg, (cudaStream_t)stream)
+                           : run_onchip(plan, dir, gg, (cudaStream_t)stream);
+    };
+    if (!plan->rp_bits) return run_tiles(g);
     // range protection: scale every block into the output, transform there in
     // place, scale back
     if (tiles > plan->rp_cap) return BDCT_ERR_UNSUPPORTED_SHAPE;
@@ -633,7 +665,7 @@ extern "C" int bdct_execute_tiled(const bdct_plan *plan, unsigned kind, const fl
     ExecGeom gi = g;
     gi.in = out;
     gi.ld_in = (long long)ld_out;
-    st = run_onchip(plan, dir, gi, (cudaStream_t)stream);
+    st = run_tiles(gi);
     if (st != BDCT_OK) return st;
     e = range_postscale(g, plan->rows, plan->cols, plan->rp_bits, (cudaStream_t)stream);
     return e == cudaSuccess ? BDCT_OK : cuda_fail(e);
@@ -726,7 +758,7 @@ extern "C" int bdct_plan_get_info(const bdct_plan *plan, bdct_plan_info *info)
 extern "C" int bdct_plan_set_chunk_bytes(bdct_plan *plan, size_t bytes)
 {
     if (!plan) return BDCT_ERR_INVALID_ARG;
-    if (plan->variant != 2 && plan->variant != 4) return BDCT_OK;
+    if ((plan->variant != 2 && plan->variant != 4) || plan->small) return BDCT_OK;
     const size_t arr_bytes = (size_t)plan->rows * plan->cols * sizeof(float);
     long long chunk = (long long)(bytes / arr_bytes);
     if (chunk < 1) chunk = 1;

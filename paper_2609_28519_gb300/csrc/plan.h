@@ -16,6 +16,7 @@ struct bdct_plan {
     int path = 0;
     int variant = 0;  // 1 fused register tile, 2 separable passes, 3 tensor core, 4 tensor-core passes
     bool lines = false;  // separable passes through the FFT line engine (else dense GEMM passes)
+    bool small = false;  // dense route on chip (both sides at most 64): no workspace
     float2 *line_tw = nullptr;        // line engine twiddles: w axis at 0, h axis at line_tw_h
     size_t line_tw_h = 0;
     int device = -1;

@@ -141,6 +141,71 @@ def test_separable_shapes(oracle_mod, cuda_dev, h, w, norm):
         _assert_parity(oracle_mod, y, _ref(oracle_mod, kind, x, norm), x, norm, kind, (h, w, norm, kind))
 
 
+SMALL_DENSE_SHAPES = [(26, 32), (24, 40), (40, 24), (1, 4), (5, 8), (3, 12), (12, 12), (20, 20), (36, 60),
+                      (48, 48), (60, 60), (64, 24), (24, 64), (63, 64)]
+
+
+@pytest.mark.parametrize("h,w", SMALL_DENSE_SHAPES)
+@pytest.mark.parametrize("norm", [0, 1])
+def test_small_dense_shapes(oracle_mod, cuda_dev, h, w, norm):
+    """Sides up to 64 without a fused kernel (non-power-of-two sides, the
+    paper's 26 among them): the dense operators applied in shared memory, one
+    read and one write, no workspace; batches large enough for several
+    iterations per CTA (26 x 32, 60 x 60) and a ragged last group."""
+    from paper_2609_28519_gb300 import Plan
+    plan = Plan(h, w, norm=norm, path="fp32")
+    info = plan.info()
+    assert info.variant == 2 and info.workspace_bytes == 0
+    batch = min(5000, max(7, 2_000_000 // (h * w))) + 3
+    x = inputs.gaussian(8100 + 7 * h + w + norm, batch, h, w)
+    for kind in KINDS:
+        y = _run(plan, kind, x, cuda_dev)
+        _assert_parity(oracle_mod, y, _ref(oracle_mod, kind, x, norm), x, norm, kind, ("small", h, w, norm, kind))
+
+
+def test_small_dense_inplace_and_tiles(oracle_mod, cuda_dev):
+    """The on-chip dense route in place, on image tiles (leading dimensions
+    wider than the image, the margin untouched) and with range protection on
+    tiles."""
+    import ctypes
+    import torch
+    from paper_2609_28519_gb300 import Plan, native
+    h, w = 24, 40
+    plan = Plan(h, w)
+    x = inputs.uniform(8200, 333, h, w)
+    d = torch.from_numpy(x).to(cuda_dev)
+    plan.execute("forward", d, d)
+    torch.cuda.synchronize()
+    _assert_parity(oracle_mod, d.cpu().numpy(), oracle_mod.forward(x, 0), x, 0, "forward", "small-inplace")
+    rows, cols = h * 20, w * 12
+    img = inputs.ramp_image(8201, rows, cols)
+    ld = cols + 36
+    src = torch.zeros(rows, ld, device=cuda_dev)
+    src[:, :cols] = torch.from_numpy(img).to(cuda_dev)
+    dst = torch.full_like(src, float("nan"))
+    L = native.lib()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    blocks = inputs.image_to_blocks(img, h, w)
+    for kind, code, ref in (("forward", 1, oracle_mod.forward(blocks, 0)), ("inverse", 2, oracle_mod.inverse(blocks, 0))):
+        st = L.bdct_execute_tiled(plan.handle, code, ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(dst.data_ptr()),
+                                  rows, cols, ld, ld, stream)
+        assert st == 0
+        torch.cuda.synchronize()
+        assert torch.isnan(dst[:, cols:]).all()  # the margin beyond the image is untouched
+        got = inputs.image_to_blocks(dst[:, :cols].cpu().numpy(), h, w)
+        _assert_parity(oracle_mod, got, ref, blocks, 0, kind, ("small-tiled", kind))
+    plan.set_range_protection(True)
+    big = (img * np.float32(1e35)).astype(np.float32)
+    src[:, :cols] = torch.from_numpy(big).to(cuda_dev)
+    st = L.bdct_execute_tiled(plan.handle, 1, ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(dst.data_ptr()),
+                              rows, cols, ld, ld, stream)
+    assert st == 0
+    torch.cuda.synchronize()
+    bb = inputs.image_to_blocks(big, h, w)
+    got = inputs.image_to_blocks(dst[:, :cols].cpu().numpy(), h, w)
+    _assert_parity(oracle_mod, got, oracle_mod.forward(bb, 0), bb, 0, "forward", "small-tiled-protected")
+
+
 def test_paper_input_categories(oracle_mod, cuda_dev):
     """Section 6 categories: impulses, cosine modes, cancellation, neighbouring
     floats, weak perturbations, amplitudes 2^-100..2^90, constant, zero."""
