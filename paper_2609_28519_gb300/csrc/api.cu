@@ -471,6 +471,12 @@ static int run_onchip(const bdct_plan *p, Dir dir, const ExecGeom &g0, cudaStrea
         e = fused_launch(p->rows, p->cols, DIR_SPEC, p->scales[DIR_RT], g, p->status, s);
         return e == cudaSuccess ? BDCT_OK : cuda_fail(e);
     }
+    if (p->rows == 64 && p->cols == 64) {
+        // fused in the ring kernel: one read, one write
+        g.lam = p->spec_fold;
+        e = ring_launch(64, 64, DIR_SPEC, p->scales[DIR_RT], g, p->status, s);
+        return e == cudaSuccess ? BDCT_OK : cuda_fail(e);
+    }
     e = fused_launch(p->rows, p->cols, DIR_FWD, ortho_scales(p, DIR_FWD), g, p->status, s);
     if (e == cudaSuccess) e = spectral_scale(g, p->rows, p->cols, p->spec_plain, s);
     if (e == cudaSuccess) {

@@ -73,7 +73,9 @@ struct RingCfg {
     static constexpr int SLOT_BYTES = H * W * 4;
     static constexpr int SLOT_FLOATS = H * W;
     static constexpr int BOX_BYTES = H * 128;  // 32 columns x H rows
-    static constexpr int S_MAX = (kRingMaxSmem - 2048) / SLOT_BYTES;
+    // spectral direction (64 x 64 only): the folded diagonal staged once per CTA
+    static constexpr int LAM_BYTES = DIR == DIR_SPEC ? H * W * 4 : 0;
+    static constexpr int S_MAX = (kRingMaxSmem - 2048 - LAM_BYTES) / SLOT_BYTES;
     // about three slots per group, so that a group's next arrays load while
     // it computes; the slot count is a multiple of the group count (a group
     // always reuses slots it consumed itself, which the slot barriers' parity
@@ -82,18 +84,23 @@ struct RingCfg {
     // slots each: 64 x 64 seven groups, 0.67 -> 0.76 of HBM, while forward
     // and inverse measured 0.90 -> 0.81 that way; the rectangles three groups,
     // 0.26 -> 0.30 / 0.33)
+    // (the spectral direction, four 1D cores per line pair like the round
+    // trip plus the diagonal, runs six groups over the thirteen slots left
+    // beside the diagonal, two each)
     static constexpr int NG = (H == 64 && W == 64 && DIR == DIR_RT) ? 7
+                              : (H == 64 && W == 64 && DIR == DIR_SPEC) ? 6
                               : (H != W && DIR == DIR_RT)             ? 3
                                                                       : (S_MAX / 3 < 1 ? 1 : S_MAX / 3);
     static constexpr int S = (S_MAX / NG) * NG;
     static constexpr int PROD_WARP = NG * GW;
     static constexpr int THREADS = (NG * GW + 1) * 32;
     // slots start 1024-byte aligned (128-byte swizzle atoms)
-    static constexpr size_t SMEM = 1024 + (size_t)S * SLOT_BYTES + (size_t)2 * S * 8;
+    static constexpr size_t SMEM = 1024 + (size_t)S * SLOT_BYTES + (size_t)2 * S * 8 + LAM_BYTES;
     static_assert(H * TR == W * TC, "both passes use the whole group");
     static_assert(GT % 32 == 0 && S >= 2 && S % NG == 0, "ring shape");
     static_assert(SMEM <= (size_t)kRingMaxSmem, "shared memory");
     static_assert(BOX_BYTES % 1024 == 0, "swizzle atoms");
+    static_assert(DIR != DIR_SPEC || (H == 64 && W == 64), "the fused spectral direction is 64 x 64 only");
 };
 
 // Named barrier over the threads of one consumer group.
@@ -361,18 +368,25 @@ __device__ __forceinline__ void ring_rect(char *slot, int gt, int bar, const Dir
 // For h = w the two passes run in one loop, so that the 1D cores (the largest
 // part of the code) exist once: pass 0 takes rows, pass 1 columns.  Same
 // arithmetic, layouts and barriers as ring_rows / ring_cols.
+//
+// The spectral direction (64 x 64, Prop. 1 / Eq. 4 with a general diagonal)
+// takes three passes with the unscaled cores: rows forward; columns forward,
+// times the column's entries of the folded diagonal lam_s (E_h Lambda E_w
+// with every scale of both axes in it), adjoint; rows adjoint.
 template <int N, int DIR>
-__device__ __forceinline__ void ring_square(char *slot, int gt, int bar, const DirScales &sc)
+__device__ __forceinline__ void ring_square(char *slot, int gt, int bar, const DirScales &sc,
+                                            const float *lam_s = nullptr)
 {
     using C = RingCfg<N, N>;
     constexpr int BB = C::BOX_BYTES;
+    constexpr int NPASS = DIR == DIR_SPEC ? 3 : 2;
 #pragma unroll 1
-    for (int pass = 0; pass < 2; ++pass) {
-        const AxisScale s = pass ? sc.h : sc.w;
+    for (int pass = 0; pass < NPASS; ++pass) {
+        const AxisScale s = (pass & 1) ? sc.h : sc.w;
         if constexpr (N == 64) {
-            // one thread per line; row r (pass 0) or column c (pass 1), in place
+            // one thread per line; row r (passes 0 and 2) or column c (pass 1), in place
             float x[64];
-            if (pass == 0) {
+            if ((pass & 1) == 0) {
                 const RowView rv(gt);
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
@@ -384,8 +398,21 @@ __device__ __forceinline__ void ring_square(char *slot, int gt, int bar, const D
 #pragma unroll
                 for (int i = 0; i < 64; ++i) x[i] = at<float>(slot, i * 128 + cv.o[i & 7]);
             }
-            line_op<64, DIR>(x, s);
-            if (pass == 0) {
+            if constexpr (DIR == DIR_SPEC) {
+                if (pass == 1) {
+                    line_op<64, CORE_FWD>(x, s);
+#pragma unroll
+                    for (int k = 0; k < 64; ++k) x[k] *= lam_s[k * 64 + gt];
+                    line_op<64, CORE_INV>(x, s);
+                } else if (pass == 0) {
+                    line_op<64, CORE_FWD>(x, s);
+                } else {
+                    line_op<64, CORE_INV>(x, s);
+                }
+            } else {
+                line_op<64, DIR>(x, s);
+            }
+            if ((pass & 1) == 0) {
                 const RowView rv(gt);
 #pragma unroll
                 for (int k = 0; k < 16; ++k)
@@ -532,6 +559,7 @@ struct RingParams {
     DirScales sc;
     unsigned int *status;
     const long long *in_off, *out_off;
+    const float *lam;         // spectral direction: the folded diagonal (H x W), else null
 };
 
 // TMA coordinates (x: column, y: row) of the first element of array or tile a.
@@ -558,6 +586,7 @@ __global__ void __launch_bounds__(RingCfg<H, W, DIR>::THREADS, 1) k_ring(const _
     char *smem = reinterpret_cast<char *>(smem_raw) + (((raw + 1023u) & ~1023u) - raw);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + C::S * C::SLOT_BYTES);
     uint64_t *done = full + C::S;
+    float *lam_s = reinterpret_cast<float *>(done + C::S);  // spectral only (16-byte aligned)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long grid = gridDim.x;
     const long long first = blockIdx.x;
@@ -572,6 +601,9 @@ __global__ void __launch_bounds__(RingCfg<H, W, DIR>::THREADS, 1) k_ring(const _
     }
     pdl_launch_dependents();
     pdl_wait_prerequisites();
+    if constexpr (DIR == DIR_SPEC) {
+        for (int e = tid; e < H * W; e += C::THREADS) lam_s[e] = __ldg(p.lam + e);
+    }
     __syncthreads();
 
     if (warp == C::PROD_WARP) {
@@ -681,7 +713,7 @@ __global__ void __launch_bounds__(RingCfg<H, W, DIR>::THREADS, 1) k_ring(const _
             break;
         }
         char *slot = smem + s * C::SLOT_BYTES;
-        if constexpr (H == W) ring_square<H, DIR>(slot, gt, bar, p.sc);  // both end with a group barrier
+        if constexpr (H == W) ring_square<H, DIR>(slot, gt, bar, p.sc, lam_s);  // both end with a group barrier
         else ring_rect<H, W, DIR>(slot, gt, bar, p.sc);
         fence_proxy_async_smem();  // the TMA store reads the slot through the async proxy
         group_sync(bar, C::GT);
@@ -728,6 +760,8 @@ static cudaError_t ring_launch_one(const DirScales &sc, const ExecGeom &g, unsig
     p.status = status;
     p.in_off = g.in_off;
     p.out_off = g.out_off;
+    p.lam = g.lam;
+    if (DIR == DIR_SPEC && !g.lam) return cudaErrorInvalidValue;
     p.indexed = (g.in_off != nullptr || g.out_off != nullptr) ? 1 : 0;
     if (p.indexed) {
         if (!g.in_off || !g.out_off) return cudaErrorInvalidValue;
@@ -765,6 +799,9 @@ static cudaError_t ring_dir(Dir dir, const DirScales &sc, const ExecGeom &g, uns
     switch (dir) {
         case DIR_FWD: return ring_launch_one<H, W, DIR_FWD>(sc, g, st, s);
         case DIR_INV: return ring_launch_one<H, W, DIR_INV>(sc, g, st, s);
+        case DIR_SPEC:
+            if constexpr (H == 64 && W == 64) return ring_launch_one<H, W, DIR_SPEC>(sc, g, st, s);
+            else return cudaErrorInvalidValue;  // composed by the caller
         default: return ring_launch_one<H, W, DIR_RT>(sc, g, st, s);
     }
 }
