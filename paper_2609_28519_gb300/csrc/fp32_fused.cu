@@ -389,19 +389,30 @@ __device__ __forceinline__ void row_pass(float *stage, int n, int warp, int lane
     }
 }
 
-template <int H, int W, int DIR, bool TILED>
-__global__ void __launch_bounds__(FusedCfg<H, W, TILED>::THREADS, FusedCfg<H, W, TILED>::MIN_CTAS) k_fused(const FusedParams p)
+// NST: stages of the ring (0: the configuration's count).  The single-stage
+// form serves 16 x 16 image strips whose chunks all get a CTA of their own
+// in one wave of seven CTAs per SM (at most 73 registers; the launch pads
+// its shared memory so that no eighth CTA lands on an SM): with two stages
+// six CTAs fit, and a 2048^2 image's 1024 chunks left 112 CTAs a second
+// chunk after the first wave.  Measured on that image: 8.59 -> 8.26 us per
+// inverse launch, 14.65 -> 14.0 us per forward-then-inverse step.
+constexpr int kOneWaveCtas = 7;
+
+template <int H, int W, int DIR, bool TILED, int NST = 0>
+__global__ void __launch_bounds__(FusedCfg<H, W, TILED>::THREADS,
+                                  NST == 1 ? kOneWaveCtas : FusedCfg<H, W, TILED>::MIN_CTAS) k_fused(const FusedParams p)
 {
     using C = FusedCfg<H, W, TILED>;
+    constexpr int STAGES = NST ? NST : C::STAGES;
     extern __shared__ __align__(128) float smem[];
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + C::STAGES * C::STAGE_FLOATS);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * C::STAGE_FLOATS);
     // spectral only: the folded diagonal, 16-byte aligned after the barriers
-    float *lam_s = reinterpret_cast<float *>(full + ((C::STAGES + 1) & ~1));
+    float *lam_s = reinterpret_cast<float *>(full + ((STAGES + 1) & ~1));
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int grid = (int)gridDim.x;
 
     if (tid == 0) {
-        for (int s = 0; s < C::STAGES; ++s) mbar_init(&full[s], 1);
+        for (int s = 0; s < STAGES; ++s) mbar_init(&full[s], 1);
         fence_mbar_init();
     }
     // the next kernel may start launching; global memory is touched only
@@ -416,7 +427,7 @@ __global__ void __launch_bounds__(FusedCfg<H, W, TILED>::THREADS, FusedCfg<H, W,
     // prologue: fill every stage (chunk k of this CTA uses stage k mod STAGES,
     // phase (k / STAGES) mod 2)
     if (warp == 0) {
-        for (int s = 0; s < C::STAGES; ++s) {
+        for (int s = 0; s < STAGES; ++s) {
             const int c = (int)blockIdx.x + s * grid;
             if (c < p.nchunks)
                 issue_fill<H, W, TILED>(p, chunk_geom<H, W, TILED>(p, c), smem + s * C::STAGE_FLOATS, &full[s], lane);
@@ -424,7 +435,7 @@ __global__ void __launch_bounds__(FusedCfg<H, W, TILED>::THREADS, FusedCfg<H, W,
     }
     // refill policy (see the end of the loop): the round trip and the spectral
     // direction carry twice the arithmetic of one direction
-    constexpr bool DEFER = C::STAGES >= 3 || (DIR != DIR_RT && DIR != DIR_SPEC);
+    constexpr bool DEFER = STAGES >= 3 || (STAGES == 2 && DIR != DIR_RT && DIR != DIR_SPEC);
 
     int failed_at = -1;   // iteration whose stage wait expired, if any
     int s = 0;            // stage of the current chunk
@@ -472,7 +483,7 @@ __global__ void __launch_bounds__(FusedCfg<H, W, TILED>::THREADS, FusedCfg<H, W,
             // inverse lose more to the wait on the stores than they gain.
             if constexpr (DEFER) {
                 if (k >= 1) {
-                    const int cn = c + (C::STAGES - 1) * grid;
+                    const int cn = c + (STAGES - 1) * grid;
                     if (cn < p.nchunks) {
                         bulk_wait_read<1>();
                         __syncwarp();
@@ -483,7 +494,7 @@ __global__ void __launch_bounds__(FusedCfg<H, W, TILED>::THREADS, FusedCfg<H, W,
             } else {
                 // refill this stage as soon as its stores have read it, so that the
                 // chunk after next loads while the next is transformed
-                const int cn = c + C::STAGES * grid;
+                const int cn = c + STAGES * grid;
                 if (cn < p.nchunks) {
                     bulk_wait_read<0>();
                     __syncwarp();
@@ -492,7 +503,7 @@ __global__ void __launch_bounds__(FusedCfg<H, W, TILED>::THREADS, FusedCfg<H, W,
             }
         }
         prev_s = s;
-        if (++s == C::STAGES) { s = 0; phase ^= 1u; }
+        if (++s == STAGES) { s = 0; phase ^= 1u; }
     }
     if (failed_at >= 0 && tid == 0) {
         record_timeout(p.status);
@@ -500,9 +511,9 @@ __global__ void __launch_bounds__(FusedCfg<H, W, TILED>::THREADS, FusedCfg<H, W,
         // refill per finished iteration (from the second on when deferred)
         const int k = failed_at;
         const int n_own = (p.nchunks - (int)blockIdx.x + grid - 1) / grid;
-        int issued = DEFER ? (k + C::STAGES - 1 > C::STAGES ? k + C::STAGES - 1 : C::STAGES) : k + C::STAGES;
+        int issued = DEFER ? (k + STAGES - 1 > STAGES ? k + STAGES - 1 : STAGES) : k + STAGES;
         if (issued > n_own) issued = n_own;
-        drain_fills(full, C::STAGES, k, issued);
+        drain_fills(full, STAGES, k, issued);
     }
     if (warp == 0) bulk_wait<0>();
 }
@@ -608,19 +619,58 @@ static cudaError_t launch_one(const DirScales &sc, const ExecGeom &g, unsigned i
     // persistent: as many CTAs as fit on the device
     long long grid = (long long)blocks_per_sm * num_sms;
     if (grid > p.nchunks) grid = p.nchunks;
+    auto launch_kern = kern;
+    size_t launch_smem = smem;
+    if constexpr (TILED && H == 16 && W == 16 && C::STAGES > 1) {
+        // one single-stage CTA per chunk when all of them fit in one wave of
+        // kOneWaveCtas per SM (and the default configuration would not)
+        auto kern1 = k_fused<H, W, DIR, TILED, 1>;
+        constexpr size_t need1 = (size_t)C::STAGE_BYTES + 8 + (DIR == DIR_SPEC ? C::LAM_BYTES : 0);
+        static DeviceLaunchCache cache1;
+        static size_t smem1_dev[64];
+        int bps1 = 0, sms1 = 0;
+        e = cache1.get(
+            dev,
+            [&](int d, int &bps, int &sms) {
+                // the shared memory of one of kOneWaveCtas CTAs (less the
+                // 1 KiB the SM reserves per CTA), so that no more fit
+                int per_sm = 0;
+                cudaError_t r = cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, d);
+                size_t sm1 = need1;
+                if (r == cudaSuccess) {
+                    const size_t cap = ((size_t)per_sm / kOneWaveCtas - 1024) & ~(size_t)127;
+                    if (cap > sm1) sm1 = cap;
+                    smem1_dev[d] = sm1;
+                }
+                if (r == cudaSuccess) r = cudaFuncSetAttribute(kern1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+                if (r == cudaSuccess) r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern1, C::THREADS, sm1);
+                if (r == cudaSuccess) r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
+                if (r == cudaSuccess && debug_enabled())
+                    fprintf(stderr, "[bdct] k_fused<%d,%d,%d,%d> single stage: %d CTAs/SM, smem %zu B\n", H, W, DIR,
+                            (int)TILED, bps, sm1);
+                return r;
+            },
+            &bps1, &sms1);
+        if (e != cudaSuccess) return e;
+        if (p.nchunks > grid && bps1 == kOneWaveCtas && (long long)p.nchunks <= (long long)bps1 * sms1) {
+            launch_kern = kern1;
+            launch_smem = smem1_dev[dev];
+            grid = p.nchunks;
+        }
+    }
     // programmatic dependent launch: this grid may be scheduled while the
     // previous kernel in the stream drains; it waits for it before any access
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(C::THREADS);
-    cfg.dynamicSmemBytes = smem;
+    cfg.dynamicSmemBytes = launch_smem;
     cfg.stream = stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, p);
+    return cudaLaunchKernelEx(&cfg, launch_kern, p);
 }
 
 template <int H, int W>

@@ -85,6 +85,26 @@ def test_fused_tiled_all_shapes(oracle_mod, cuda_dev, h, w):
         assert torch.isnan(dst[:, cols:]).all(), (h, w, kind)
 
 
+@pytest.mark.parametrize("h,w,rows,cols", [(16, 16, 2048, 2048), (16, 16, 2048, 1920), (8, 16, 1024, 2048)])
+def test_tiled_one_wave_images(oracle_mod, cuda_dev, h, w, rows, cols):
+    """Images whose strip chunks all fit in one wave of single-stage CTAs but
+    not of the default two-stage ones (the 2048^2 image of 16 x 16 blocks is
+    1024 chunks), next to neighbouring sizes: every direction against the
+    oracle on every block."""
+    import torch
+    from paper_2609_28519_gb300 import Plan
+    img = inputs.ramp_image(2600 + rows + cols + h, rows, cols)
+    blocks = inputs.image_to_blocks(img, h, w)
+    src = torch.from_numpy(img).to(cuda_dev)
+    plan = Plan(h, w, path="fp32")
+    for kind in KINDS:
+        dst = torch.full_like(src, float("nan"))
+        plan.execute_tiled(kind, src, dst)
+        torch.cuda.synchronize()
+        got = inputs.image_to_blocks(dst.cpu().numpy(), h, w)
+        _assert_parity(oracle_mod, got, _ref(oracle_mod, kind, blocks, 0), blocks, 0, kind, ("wave", h, w, rows, cols, kind))
+
+
 @pytest.mark.parametrize("h,w", RING_SHAPES)
 @pytest.mark.parametrize("norm", [0, 1])
 def test_ring_shapes_all_kinds(oracle_mod, cuda_dev, h, w, norm):
