@@ -268,7 +268,7 @@ def test_config_image_16x16_tiles(oracle_mod, cuda_dev):
     ref = oracle_mod.forward(blocks, 0)
     _assert_parity(oracle_mod, spec_b, ref, blocks, 0, "forward", "tiled-forward")
     back_b = inputs.image_to_blocks(back.cpu().numpy(), 16, 16)
-    # inverse judged against the oracle inverse of the GPU spectrum
+    # inverse compared with the oracle inverse of the GPU spectrum
     ref_i = oracle_mod.inverse(spec_b, 0)
     _assert_parity(oracle_mod, back_b, ref_i, spec_b, 0, "inverse", "tiled-inverse")
     # forward then inverse returns the image within two FP32 transforms
