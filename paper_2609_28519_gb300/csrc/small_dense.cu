@@ -357,9 +357,18 @@ cudaError_t small_dense_run(int h, int w, int npass, const int *axis, const floa
     const long long groups = (p.count + G - 1) / G;
     long long grid = (long long)per_sm * sms;
     if (grid > groups) grid = groups;
-    if (debug_enabled())
-        fprintf(stderr, "[bdct] k_small_dense %dx%d: %d passes, %d arrays per iteration, %d CTAs/SM, smem %zu B\n", h,
-                w, npass, G, per_sm, smem);
+    if (debug_enabled()) {
+        // once per configuration, not per launch
+        static std::mutex mu;
+        static long long last = -1;
+        const long long key = ((long long)h << 20) | ((long long)w << 8) | npass;
+        std::lock_guard<std::mutex> lock(mu);
+        if (key != last) {
+            last = key;
+            fprintf(stderr, "[bdct] k_small_dense %dx%d: %d passes, %d arrays per iteration, %d CTAs/SM, smem %zu B\n",
+                    h, w, npass, G, per_sm, smem);
+        }
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(kSmThreads);
