@@ -14,6 +14,7 @@
 #include "bdct_internal.h"
 #include "plan.h"
 #include "small_dense.h"
+#include "fp32_ring.h"
 
 using namespace bdct;
 
@@ -477,8 +478,12 @@ static int run_onchip(const bdct_plan *p, Dir dir, const ExecGeom &g0, cudaStrea
         e = ring_launch(64, 64, DIR_SPEC, p->scales[DIR_RT], g, p->status, s);
         return e == cudaSuccess ? BDCT_OK : cuda_fail(e);
     }
-    e = fused_launch(p->rows, p->cols, DIR_FWD, ortho_scales(p, DIR_FWD), g, p->status, s);
-    if (e == cudaSuccess) e = spectral_scale(g, p->rows, p->cols, p->spec_plain, s);
+    // the other ring shapes: the orthonormal forward multiplying its
+    // coefficients by Lambda as it stores them, then the orthonormal inverse
+    // in place
+    g.lam = p->spec_plain;
+    e = ring_forward_lam(p->rows, p->cols, ortho_scales(p, DIR_FWD), g, p->status, s);
+    g.lam = nullptr;
     if (e == cudaSuccess) {
         ExecGeom gi = g;
         gi.in = g.out;

@@ -49,6 +49,7 @@
 #include "bdct_internal.h"
 #include "dct_cores.cuh"
 #include "ptx.cuh"
+#include "fp32_ring.h"
 
 namespace bdct {
 
@@ -216,8 +217,12 @@ __device__ __forceinline__ void role_core(int role, const float (&v)[64], float 
 // (roles), the 64 side's lines take one thread each; both passes (rows, then
 // columns) run in one loop body around a single call of role_core (role 0 is
 // the whole 64-point transform), so the 1D cores exist once in the code.
-template <int H, int W, int DIR>
-__device__ __forceinline__ void ring_rect(char *slot, int gt, int bar, const DirScales &sc)
+// LAMF (forward only): the coefficients are multiplied by the diagonal lam
+// (H x W, row k = frequency along h) as the column pass stores them -- the
+// first half of the spectral composition of Prop. 1 for these shapes.
+template <int H, int W, int DIR, bool LAMF = false>
+__device__ __forceinline__ void ring_rect(char *slot, int gt, int bar, const DirScales &sc,
+                                          const float *lam = nullptr)
 {
     using C = RingCfg<H, W>;
     constexpr int BB = C::BOX_BYTES;
@@ -322,6 +327,11 @@ __device__ __forceinline__ void ring_rect(char *slot, int gt, int bar, const Dir
             }
         } else {
             const ColView<H> dst(ln);
+            if constexpr (LAMF) {
+                // coefficient row (2m + role for split lines, m otherwise) of column ln
+#pragma unroll
+                for (int m = 0; m < 64; ++m) y[m] *= __ldg(lam + (split ? 2 * m + role : m) * W + ln);
+            }
             if (!split) {
 #pragma unroll
                 for (int i = 0; i < 64; ++i) at<float>(slot, i * 128 + dst.o[i & 7]) = y[i];
@@ -373,9 +383,9 @@ __device__ __forceinline__ void ring_rect(char *slot, int gt, int bar, const Dir
 // takes three passes with the unscaled cores: rows forward; columns forward,
 // times the column's entries of the folded diagonal lam_s (E_h Lambda E_w
 // with every scale of both axes in it), adjoint; rows adjoint.
-template <int N, int DIR>
+template <int N, int DIR, bool LAMF = false>
 __device__ __forceinline__ void ring_square(char *slot, int gt, int bar, const DirScales &sc,
-                                            const float *lam_s = nullptr)
+                                            const float *lam_s = nullptr, const float *lam = nullptr)
 {
     using C = RingCfg<N, N>;
     constexpr int BB = C::BOX_BYTES;
@@ -508,6 +518,11 @@ __device__ __forceinline__ void ring_square(char *slot, int gt, int bar, const D
                 }
             } else {
                 const ColView<N> dst(r);
+                if constexpr (LAMF) {
+                    // coefficient rows 2m + role of column r, times the diagonal
+#pragma unroll
+                    for (int m = 0; m < 64; ++m) y[m] *= __ldg(lam + (2 * m + role) * N + r);
+                }
                 if constexpr (DIR == DIR_FWD) {
                     if (role == 0) {
 #pragma unroll
@@ -576,7 +591,7 @@ __device__ __forceinline__ void ring_coords(const RingParams &p, long long a, in
     }
 }
 
-template <int H, int W, int DIR>
+template <int H, int W, int DIR, bool LAMF = false>
 __global__ void __launch_bounds__(RingCfg<H, W, DIR>::THREADS, 1) k_ring(const __grid_constant__ RingParams p)
 {
     using C = RingCfg<H, W, DIR>;
@@ -713,8 +728,8 @@ __global__ void __launch_bounds__(RingCfg<H, W, DIR>::THREADS, 1) k_ring(const _
             break;
         }
         char *slot = smem + s * C::SLOT_BYTES;
-        if constexpr (H == W) ring_square<H, DIR>(slot, gt, bar, p.sc, lam_s);  // both end with a group barrier
-        else ring_rect<H, W, DIR>(slot, gt, bar, p.sc);
+        if constexpr (H == W) ring_square<H, DIR, LAMF>(slot, gt, bar, p.sc, lam_s, p.lam);  // both end with a group barrier
+        else ring_rect<H, W, DIR, LAMF>(slot, gt, bar, p.sc, p.lam);
         fence_proxy_async_smem();  // the TMA store reads the slot through the async proxy
         group_sync(bar, C::GT);
         if (gt == 0) mbar_arrive(&done[s]);
@@ -722,12 +737,12 @@ __global__ void __launch_bounds__(RingCfg<H, W, DIR>::THREADS, 1) k_ring(const _
 }
 
 // ---------------------------------------------------------------- host side
-template <int H, int W, int DIR>
+template <int H, int W, int DIR, bool LAMF = false>
 static cudaError_t ring_launch_one(const DirScales &sc, const ExecGeom &g, unsigned int *status,
                                    cudaStream_t stream)
 {
     using C = RingCfg<H, W, DIR>;
-    auto kern = k_ring<H, W, DIR>;
+    auto kern = k_ring<H, W, DIR, LAMF>;
     static DeviceLaunchCache cache;
     int dev = 0, bps_dev = 0, num_sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -761,7 +776,7 @@ static cudaError_t ring_launch_one(const DirScales &sc, const ExecGeom &g, unsig
     p.in_off = g.in_off;
     p.out_off = g.out_off;
     p.lam = g.lam;
-    if (DIR == DIR_SPEC && !g.lam) return cudaErrorInvalidValue;
+    if ((DIR == DIR_SPEC || LAMF) && !g.lam) return cudaErrorInvalidValue;
     p.indexed = (g.in_off != nullptr || g.out_off != nullptr) ? 1 : 0;
     if (p.indexed) {
         if (!g.in_off || !g.out_off) return cudaErrorInvalidValue;
@@ -804,6 +819,15 @@ static cudaError_t ring_dir(Dir dir, const DirScales &sc, const ExecGeom &g, uns
             else return cudaErrorInvalidValue;  // composed by the caller
         default: return ring_launch_one<H, W, DIR_RT>(sc, g, st, s);
     }
+}
+
+cudaError_t ring_forward_lam(int rows, int cols, const DirScales &sc, const ExecGeom &g, unsigned int *status,
+                             cudaStream_t stream)
+{
+    if (rows == 64 && cols == 128) return ring_launch_one<64, 128, DIR_FWD, true>(sc, g, status, stream);
+    if (rows == 128 && cols == 64) return ring_launch_one<128, 64, DIR_FWD, true>(sc, g, status, stream);
+    if (rows == 128 && cols == 128) return ring_launch_one<128, 128, DIR_FWD, true>(sc, g, status, stream);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t ring_launch(int rows, int cols, Dir dir, const DirScales &sc, const ExecGeom &g, unsigned int *status,
