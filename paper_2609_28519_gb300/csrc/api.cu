@@ -15,6 +15,7 @@
 #include "plan.h"
 #include "small_dense.h"
 #include "fp32_ring.h"
+#include "fp32_lines.h"
 
 using namespace bdct;
 
@@ -354,7 +355,8 @@ static bool ranges_partially_overlap(const void *a, const void *b, size_t bytes)
 }
 
 static int run_lines(const bdct_plan *p, Dir dir, const DirScales &sc, const float *in, const long long *in_off,
-                     float *out, const long long *out_off, long long count, cudaStream_t s)
+                     float *out, const long long *out_off, long long count, cudaStream_t s,
+                     const float *lam = nullptr)
 {
     const int h = p->rows, w = p->cols;
     const long long hw = (long long)h * w;
@@ -366,8 +368,8 @@ static int run_lines(const bdct_plan *p, Dir dir, const DirScales &sc, const flo
         cudaError_t e = lines_pass(src, p->work, h, w, nb, dir, sc.w, p->line_tw, p->status, s,
                                    in_off ? in_off + b0 : nullptr, nullptr);
         if (e == cudaSuccess)
-            e = lines_pass(p->work, dst, w, h, nb, dir, sc.h, p->line_tw + p->line_tw_h, p->status, s,
-                           nullptr, out_off ? out_off + b0 : nullptr, true);
+            e = lines_pass_lam(p->work, dst, w, h, nb, dir, sc.h, p->line_tw + p->line_tw_h, p->status, s,
+                               nullptr, out_off ? out_off + b0 : nullptr, true, lam);
         if (e != cudaSuccess) return cuda_fail(e);
     }
     return BDCT_OK;
@@ -592,13 +594,10 @@ static int execute_dir(const bdct_plan *p, Dir dir, const float *in, const long 
     if (p->variant == 4) return run_tg(p, dir, in, in_off, out, out_off, count, s);
     if (p->lines) {
         if (dir != DIR_SPEC) return run_lines(p, dir, p->scales[dir], in, in_off, out, out_off, count, s);
-        int st = run_lines(p, DIR_FWD, ortho_scales(p, DIR_FWD), in, in_off, out, out_off, count, s);
-        if (st == BDCT_OK) {
-            ExecGeom g{out, out, count, 0, 0, 0, 0, out_off, out_off};
-            cudaError_t e = spectral_scale(g, p->rows, p->cols, p->spec_plain, s);
-            if (e != cudaSuccess) return cuda_fail(e);
-            st = run_lines(p, DIR_INV, ortho_scales(p, DIR_INV), out, out_off, out, out_off, count, s);
-        }
+        // the orthonormal forward, its second pass storing the spectrum times
+        // Lambda, then the orthonormal inverse in place
+        int st = run_lines(p, DIR_FWD, ortho_scales(p, DIR_FWD), in, in_off, out, out_off, count, s, p->spec_plain);
+        if (st == BDCT_OK) st = run_lines(p, DIR_INV, ortho_scales(p, DIR_INV), out, out_off, out, out_off, count, s);
         return st;
     }
     return run_separable(p, dir, in, in_off, out, out_off, count, s);

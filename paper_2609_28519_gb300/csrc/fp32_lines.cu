@@ -33,6 +33,7 @@
 
 #include "dct_cores.cuh"
 #include "ptx.cuh"
+#include "fp32_lines.h"
 
 namespace bdct {
 
@@ -429,6 +430,8 @@ struct LinesParams {
     const float2 *tw;    // the plan's tables for N (lines_gen_table), generated in FP64
     int reverse;         // take panels last to first (the second pass reads the
                          // intermediate the first pass wrote last, still in L2, first)
+    const float *lam;    // or null: every output element (k, r) of array b is
+                         // multiplied by lam[k * rows + r] as it is stored
 };
 
 template <int N, int DIR>
@@ -553,17 +556,32 @@ __global__ void __launch_bounds__(LineCfg<N>::THREADS) k_lines(const LinesParams
             constexpr int SQ = C::SEG / 4;          // row quads per segment
             constexpr int KPI = C::THREADS / SQ;    // columns per step
             const int qd = tid % SQ, kk = tid / SQ;
-            float *g = dstb + (long long)kk * p.rows + rr + 4 * qd;
+            const long long e0 = (long long)kk * p.rows + rr + 4 * qd;  // element offset in the array
+            float *g = dstb + e0;
             const long long gstep = (long long)KPI * p.rows;
 #pragma unroll 1
             for (int lb = 0; lb < C::PR; lb += C::SEG) {
                 const float *sp = panel + (lb + 4 * qd) * C::PP + kk;
                 float *gp = g + lb;
+                if (p.lam) {
+                    // the spectrum times the diagonal (Prop. 1), four rows of one column
+                    const float *lp = p.lam + e0 + lb;
 #pragma unroll 4
-                for (int k = kk; k < N; k += KPI) {
-                    *reinterpret_cast<float4 *>(gp) = make_float4(sp[0], sp[C::PP], sp[2 * C::PP], sp[3 * C::PP]);
-                    sp += KPI;
-                    gp += gstep;
+                    for (int k = kk; k < N; k += KPI) {
+                        const float4 l = __ldg(reinterpret_cast<const float4 *>(lp));
+                        *reinterpret_cast<float4 *>(gp) =
+                            make_float4(sp[0] * l.x, sp[C::PP] * l.y, sp[2 * C::PP] * l.z, sp[3 * C::PP] * l.w);
+                        sp += KPI;
+                        gp += gstep;
+                        lp += gstep;
+                    }
+                } else {
+#pragma unroll 4
+                    for (int k = kk; k < N; k += KPI) {
+                        *reinterpret_cast<float4 *>(gp) = make_float4(sp[0], sp[C::PP], sp[2 * C::PP], sp[3 * C::PP]);
+                        sp += KPI;
+                        gp += gstep;
+                    }
                 }
             }
         }
@@ -681,8 +699,16 @@ cudaError_t lines_pass(const float *src, float *dst, int rows, int n, long long 
                        const float2 *tw, unsigned int *status, cudaStream_t stream, const long long *src_off,
                        const long long *dst_off, bool reverse)
 {
+    return lines_pass_lam(src, dst, rows, n, count, dir, sc, tw, status, stream, src_off, dst_off, reverse, nullptr);
+}
+
+cudaError_t lines_pass_lam(const float *src, float *dst, int rows, int n, long long count, Dir dir, AxisScale sc,
+                           const float2 *tw, unsigned int *status, cudaStream_t stream, const long long *src_off,
+                           const long long *dst_off, bool reverse, const float *lam)
+{
     (void)status;
     LinesParams p{};
+    p.lam = lam;
     p.reverse = reverse ? 1 : 0;
     p.src = src;
     p.dst = dst;
