@@ -880,9 +880,10 @@ def test_radix3_lines_against_oracle(oracle_mod, cuda_dev, h, w, norm):
 
 
 def test_spectral_ring_tiled_and_chunk_sizes(oracle_mod, cuda_dev):
-    """The composed spectral direction on image blocks of the ring shapes, in
-    place; and the workspace chunk of the separable routes changes nothing
-    but the launch count (bit-equal results for 1-array and default chunks)."""
+    """The spectral direction on image blocks of the ring shapes, in place;
+    and the workspace chunk of the separable routes changes nothing but the
+    launch count (bit-equal results for 1-array and default chunks, the
+    spectral direction included)."""
     import torch
     from paper_2609_28519_gb300 import Plan
     img = inputs.ramp_image(11, 256, 384)
@@ -902,9 +903,11 @@ def test_spectral_ring_tiled_and_chunk_sizes(oracle_mod, cuda_dev):
     for (h, w, path) in [(256, 256, "fp32"), (384, 192, "fp32"), (24, 40, "fp32"), (256, 128, "split_tc")]:
         x = torch.from_numpy(inputs.uniform(9700 + h + w, 7, h, w)).to(cuda_dev)
         plan = Plan(h, w, path=path)
-        ref = {k: plan.execute(k, x) for k in KINDS}
+        plan.set_spectral(inputs.random_diagonal(9800 + h + w, h, w, -1.0, 2.0))
+        kinds = KINDS + ["spectral"]
+        ref = {k: plan.execute(k, x) for k in kinds}
         plan.set_chunk_bytes(1)  # one array per chunk: seven rounds of passes
-        for k in KINDS:
+        for k in kinds:
             y = plan.execute(k, x)
             torch.cuda.synchronize()
             assert torch.equal(y, ref[k]), (h, w, path, k)
