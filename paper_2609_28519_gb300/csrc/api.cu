@@ -16,6 +16,7 @@
 #include "small_dense.h"
 #include "fp32_ring.h"
 #include "fp32_lines.h"
+#include "dense_passes.h"
 
 using namespace bdct;
 
@@ -426,12 +427,10 @@ static int run_separable(const bdct_plan *p, Dir dir, const float *in, const lon
         } else {
             // forward core, then the adjoint core (orthonormal pair)
             const float *ioph = oph + per_dir, *iopw = opw + per_dir;
-            if (e == cudaSuccess) e = dense_pass_cols(w1, w2, oph, h, w, nb, s);
-            if (e == cudaSuccess && dir == DIR_SPEC) {
-                // the orthonormal spectrum of the chunk, times Lambda (Eq. 4)
-                ExecGeom gw{w2, w2, nb, 0, 0, 0, 0};
-                e = spectral_scale(gw, h, w, p->spec_plain, s);
-            }
+            // the orthonormal spectrum of the chunk (times Lambda as it is
+            // stored, for the spectral direction: Eq. 4)
+            if (e == cudaSuccess)
+                e = dense_pass_cols_lam(w1, w2, oph, h, w, nb, dir == DIR_SPEC ? p->spec_plain : nullptr, s);
             if (e == cudaSuccess) e = dense_pass_cols(w2, w1, ioph, h, w, nb, s);
             if (e == cudaSuccess) {
                 if (ooff) e = dense_pass_rows_out_indexed(w1, out, ooff, iopw, h, w, nb, s);

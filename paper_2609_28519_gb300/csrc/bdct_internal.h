@@ -155,9 +155,6 @@ cudaError_t tc_launch(int n, Dir dir, int terms, const ExecGeom &g, const __nv_b
 // e_n = the squared scales of Eq. 1 (1/n at index 0, 2/n elsewhere), both
 // rounded once to FP32.
 cudaError_t spectral_gen_tables(const double *lam, float *plain, float *fold, int h, int w, cudaStream_t s);
-// Multiply every h x w array of the call's OUTPUT geometry (contiguous,
-// indexed through out_off, or tiles of an image) by lam elementwise, in place.
-cudaError_t spectral_scale(const ExecGeom &g, int h, int w, const float *lam, cudaStream_t s);
 
 // Copy `count` contiguous h x w arrays from src into the call's OUTPUT
 // geometry g (contiguous or indexed through out_off).

@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include "bdct_internal.h"
+#include "dense_passes.h"
 
 namespace bdct {
 
@@ -67,6 +68,7 @@ struct GemmArgs {
     // indexed batch: batch element b of A / B / C starts at off[b] (element offsets)
     const long long *aoff = nullptr, *boff = nullptr, *coff = nullptr;
     long long b0 = 0;  // index of this launch's first batch element in the offset arrays
+    const float *lam = nullptr;  // or null: C[b][m][n] *= lam[m * N + n] as it is stored
 };
 
 __global__ void __launch_bounds__(256) k_gemm_strided(GemmArgs g)
@@ -117,7 +119,7 @@ __global__ void __launch_bounds__(256) k_gemm_strided(GemmArgs g)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int gm = m0 + tm + i, gn = n0 + tn + j;
-            if (gm < g.M && gn < g.N) C[gm * g.sCm + gn * g.sCn] = acc[i][j];
+            if (gm < g.M && gn < g.N) C[gm * g.sCm + gn * g.sCn] = g.lam ? acc[i][j] * g.lam[gm * g.N + gn] : acc[i][j];
         }
 }
 
@@ -160,8 +162,15 @@ cudaError_t dense_pass_rows(const float *in, float *out, const float *op_w, int 
 cudaError_t dense_pass_cols(const float *in, float *out, const float *op_h, int h, int w,
                             long long count, cudaStream_t stream)
 {
+    return dense_pass_cols_lam(in, out, op_h, h, w, count, nullptr, stream);
+}
+
+cudaError_t dense_pass_cols_lam(const float *in, float *out, const float *op_h, int h, int w, long long count,
+                                const float *lam, cudaStream_t stream)
+{
     const long long hw = (long long)h * w;
     GemmArgs g{op_h, 0, h, 1, in, hw, w, 1, out, hw, w, 1, h, w, h};
+    g.lam = lam;
     return gemm(g, count, stream);
 }
 

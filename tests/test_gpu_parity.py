@@ -646,7 +646,7 @@ def _assert_spectral(o, y, x, lam, tag):
 
 SPECTRAL_CASES = [(h, w, "fp32") for (h, w) in FUSED_SHAPES[:9]] + [
     (64, 64, "fp32"), (128, 128, "fp32"), (64, 128, "fp32"), (16, 16, "split_tc"), (32, 32, "split_tc"),
-    (64, 64, "split_tc"), (256, 256, "fp32"), (64, 256, "fp32"), (24, 40, "fp32")]
+    (64, 64, "split_tc"), (256, 256, "fp32"), (64, 256, "fp32"), (24, 40, "fp32"), (40, 100, "fp32")]
 
 
 @pytest.mark.parametrize("h,w,path", SPECTRAL_CASES)
