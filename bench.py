@@ -441,6 +441,7 @@ def run_ours(args):
                                                  check=not args.no_check),
             "ragged_4096": ragged_summary(dev),
             "odd_sides_256MiB": odd_sides_summary(dev, check=not args.no_check),
+            "spectral_sweep_512MiB": spectral_sweep_summary(dev, check=not args.no_check),
             "boundary_diagnostics": boundary_summary(dev) if not args.no_check else None,
             "large_arrays": large_summary(dev),
         }
@@ -526,6 +527,40 @@ def odd_sides_summary(dev, shapes=((26, 32), (24, 40), (48, 48)), mib=256, check
                 ent[kind]["e_rel_max"] = m["e_rel_max"]
                 ent[kind]["accepted"] = bool(oracle.accept(m))
         out[f"{h}x{w}"] = ent
+        plan.close()
+    return out
+
+
+def spectral_sweep_summary(dev, sizes=(16, 64, 128, 256), mib=512, check=True):
+    """Transform -- Poisson diagonal -- inverse (Prop. 1, Eq. 4) on square
+    batches of about mib MiB (one read and one write counted per element):
+    fused on chip where a kernel holds the whole array, forward times the
+    diagonal then inverse elsewhere; sampled arrays against the oracle."""
+    import torch
+    import oracle
+    from paper_2609_28519_gb300 import Plan, inputs, native
+    peak, _ = _peaks()
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for n in sizes:
+        batch = max(1, (mib << 20) // (4 * n * n))
+        x = torch.empty((batch, n, n), dtype=torch.float32, device=dev)
+        x.uniform_(-1.0, 1.0, generator=torch.Generator(device=dev).manual_seed(3700 + n))
+        y = torch.empty_like(x)
+        lam = inputs.poisson_diagonal(n, n)
+        plan = Plan(n, n, kind=native.SPECTRAL, path="fp32")
+        plan.set_spectral(lam)
+        ms = _time_calls(lambda st: plan.execute("spectral", x, y, st), stream, 5)
+        gbs = batch * n * n * 8 / (ms * 1e-3) / 1e9
+        ent = {"batch": batch, "variant": plan.info().variant, "ms": ms, "GB/s": gbs, "frac": gbs / peak}
+        if check:
+            idx = np.array([0, batch // 2, batch - 1])
+            xs = x[idx].cpu().numpy()
+            ys = y[idx].cpu().numpy()
+            sc = float(np.max(np.abs(lam)))
+            m = oracle.metrics(ys / sc, oracle.spectral(xs, lam) / sc, xs)
+            ent.update({"e_rel_max": m["e_rel_max"], "accepted": bool(oracle.accept(m))})
+        out[str(n)] = ent
         plan.close()
     return out
 
