@@ -355,7 +355,10 @@ struct WsCfg {
     static_assert(TMEM_COLS <= 512, "TMEM");
 };
 
-template <int N, int TERMS, bool TILED>
+// LAMF: every stored coefficient is multiplied by the diagonal p.lam (N x N,
+// row k = frequency along h): the first half of the spectral composition of
+// Prop. 1 (Eq. 4), whose second half is the orthonormal inverse in place.
+template <int N, int TERMS, bool TILED, bool LAMF = false>
 __global__ void __launch_bounds__(WsCfg<N>::THREADS, 1) k_tc_ws(const TcParams p)
 {
     using C = WsCfg<N>;
@@ -531,6 +534,10 @@ __global__ void __launch_bounds__(WsCfg<N>::THREADS, 1) k_tc_ws(const TcParams p
                 int n, t0;
                 tile_geom<N, TILED>(p, tile, first, n, brow, t0);
                 if (b_local < n) {
+                    if constexpr (LAMF) {
+#pragma unroll
+                        for (int k = 0; k < N; ++k) v[k] *= __ldg(p.lam + k * N + r_local);
+                    }
 #pragma unroll
                     for (int k = 0; k < N; ++k) {
                         float *dst;
@@ -687,11 +694,12 @@ static cudaError_t tc_launch_one(const TcParams &p0, const __nv_bfloat16 *ops, c
     return cudaLaunchKernelEx(&cfg, kern, p);
 }
 
-template <int N, int TERMS, bool TILED>
+template <int N, int TERMS, bool TILED, bool LAMF = false>
 static cudaError_t tc_ws_launch(const TcParams &p0, const __nv_bfloat16 *ops, cudaStream_t stream)
 {
     using C = WsCfg<N>;
-    auto kern = k_tc_ws<N, TERMS, TILED>;
+    auto kern = k_tc_ws<N, TERMS, TILED, LAMF>;
+    if (LAMF && !p0.lam) return cudaErrorInvalidValue;
     static DeviceLaunchCache cache;
     int dev = 0, bps = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -759,6 +767,20 @@ static cudaError_t tc_launch_nt(Dir dir, const TcParams &p, const __nv_bfloat16 
             pi.ld_in = p.ld_out;
             const __nv_bfloat16 *inv = ops + 3 * N * N;
             cudaError_t e = tiled ? tc_ws_launch<N, TERMS, true>(p, ops, s) : tc_ws_launch<N, TERMS, false>(p, ops, s);
+            if (e == cudaSuccess)
+                e = tiled ? tc_ws_launch<N, TERMS, true>(pi, inv, s) : tc_ws_launch<N, TERMS, false>(pi, inv, s);
+            return e;
+        }
+        if (dir == DIR_SPEC) {
+            // likewise, the forward storing its coefficients times Lambda
+            TcParams pi = p;
+            pi.in = p.out;
+            pi.in_off = p.out_off;
+            pi.ld_in = p.ld_out;
+            pi.lam = nullptr;
+            const __nv_bfloat16 *inv = ops + 3 * N * N;
+            cudaError_t e = tiled ? tc_ws_launch<N, TERMS, true, true>(p, ops, s)
+                                  : tc_ws_launch<N, TERMS, false, true>(p, ops, s);
             if (e == cudaSuccess)
                 e = tiled ? tc_ws_launch<N, TERMS, true>(pi, inv, s) : tc_ws_launch<N, TERMS, false>(pi, inv, s);
             return e;
