@@ -162,11 +162,16 @@ __device__ __forceinline__ void small_pass(const SmallParams &p, const float *op
                     *reinterpret_cast<float4 *>(g + (long long)(r0 + r) * ld + 4 * lt) =
                         make_float4(acc[r][0].x, acc[r][0].y, acc[r][1].x, acc[r][1].y);
         } else {
+            // padding rows (h not a multiple of 4) are stored as zeros, not as
+            // their sums: a non-finite input would make those 0 * inf = NaN,
+            // and the buffer goes on to hold the CTA's later arrays, whose
+            // sums take the padding rows in with zero weights (0 * NaN)
             float *da = dst + (size_t)a * hp * pitch;
 #pragma unroll
             for (int r = 0; r < 4; ++r)
                 *reinterpret_cast<float4 *>(da + (r0 + r) * pitch + 4 * lt) =
-                    make_float4(acc[r][0].x, acc[r][0].y, acc[r][1].x, acc[r][1].y);
+                    r0 + r < p.h ? make_float4(acc[r][0].x, acc[r][0].y, acc[r][1].x, acc[r][1].y)
+                                 : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         }
     }
 }
@@ -231,8 +236,9 @@ __global__ void __launch_bounds__(kSmThreads) k_small_dense(const SmallParams p)
             o[e] = v;
         }
     }
-    // zero the buffers once: padding rows and columns stay zero (the copies
-    // and the passes write only the arrays' own rows and columns, or zeros)
+    // zero the buffers once: padding rows stay zero (the copies write only
+    // the arrays' own rows, the passes zeros into the padding rows; the
+    // width is a multiple of 4, so there are no padding columns)
     for (size_t e = tid; e < 3 * buf; e += kSmThreads) ssm[e] = 0.0f;
     pdl_wait_prerequisites();
     __syncthreads();

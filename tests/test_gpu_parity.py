@@ -183,6 +183,25 @@ def test_small_dense_shapes(oracle_mod, cuda_dev, h, w, norm):
         _assert_parity(oracle_mod, y, _ref(oracle_mod, kind, x, norm), x, norm, kind, ("small", h, w, norm, kind))
 
 
+def test_small_dense_nonfinite_arrays_stay_apart(oracle_mod, cuda_dev):
+    """A non-finite value in some arrays of a batch (26 rows: two zero
+    padding rows in shared memory) leaves every other array exact, through
+    the several groups each CTA transforms in turn with the same buffers."""
+    import torch
+    from paper_2609_28519_gb300 import Plan
+    h, w = 26, 32
+    x = inputs.gaussian(8300, 6001, h, w)
+    bad = np.arange(0, 6001, 97)
+    x[bad, 3, 5] = np.inf
+    x[bad[1::2], 7, 9] = np.nan
+    plan = Plan(h, w)
+    good = np.setdiff1d(np.arange(6001), bad)
+    for kind in KINDS:
+        y = _run(plan, kind, x, cuda_dev)
+        _assert_parity(oracle_mod, y[good], _ref(oracle_mod, kind, x[good], 0), x[good], 0, kind,
+                       ("small-nonfinite", kind))
+
+
 def test_small_dense_inplace_and_tiles(oracle_mod, cuda_dev):
     """The on-chip dense route in place, on image tiles (leading dimensions
     wider than the image, the margin untouched) and with range protection on
