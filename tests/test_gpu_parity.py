@@ -183,6 +183,29 @@ def test_small_dense_shapes(oracle_mod, cuda_dev, h, w, norm):
         _assert_parity(oracle_mod, y, _ref(oracle_mod, kind, x, norm), x, norm, kind, ("small", h, w, norm, kind))
 
 
+@pytest.mark.parametrize("h,w,path,batch", [(8, 8, "fp32", 3001), (16, 16, "fp32", 3001), (32, 16, "fp32", 1201),
+                                            (64, 64, "fp32", 701), (128, 128, "fp32", 331), (256, 256, "fp32", 41),
+                                            (100, 100, "fp32", 61), (16, 16, "split_tc", 2001),
+                                            (32, 32, "split_tc", 1201), (8, 8, "split_tc", 3001),
+                                            (256, 128, "split_tc", 41)])
+def test_nonfinite_arrays_stay_apart_all_routes(oracle_mod, cuda_dev, h, w, path, batch):
+    """Every route: arrays holding inf or NaN give non-finite results of
+    their own, and every other array of the batch stays exact (forward and
+    round trip), over batches that take several chunks, tiles or slots per
+    CTA."""
+    from paper_2609_28519_gb300 import Plan
+    x = inputs.gaussian(8400 + h + w + len(path), batch, h, w)
+    bad = np.arange(0, batch, 13)
+    x[bad, h // 2, w // 3] = np.inf
+    x[bad[1::2], h - 1, 0] = np.nan
+    good = np.setdiff1d(np.arange(batch), bad)
+    plan = Plan(h, w, path=path)
+    for kind in ("forward", "roundtrip"):
+        y = _run(plan, kind, x, cuda_dev)
+        _assert_parity(oracle_mod, y[good], _ref(oracle_mod, kind, x[good], 0), x[good], 0, kind,
+                       ("nonfinite-apart", h, w, path, kind))
+
+
 def test_small_dense_nonfinite_arrays_stay_apart(oracle_mod, cuda_dev):
     """A non-finite value in some arrays of a batch (26 rows: two zero
     padding rows in shared memory) leaves every other array exact, through
