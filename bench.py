@@ -189,7 +189,27 @@ def run_reference(args):
 # Sources of each captured kernel's translation unit (the kernel file and the
 # headers it includes).
 KERNEL_SOURCES = {"k_fused": ["fp32_fused.cu", "dct_cores.cuh", "ptx.cuh", "bdct_internal.h"],
+                  "k_strip16_wave": ["fp32_fused.cu", "dct_cores.cuh", "ptx.cuh", "bdct_internal.h"],
                   "k_tc_split": ["tc_split.cu", "tc_ptx.cuh", "ptx.cuh", "bdct_internal.h"]}
+
+# CTAs per SM of the FP32 route's one-wave strip kernel (16 x 16 image
+# strips, shared memory bound)
+STRIP_WAVE_CTAS = 7
+
+
+def dominant_kernel(variant: int, direction: str, sms: int) -> str:
+    """The kernel that one tiled launch over the IMG^2 image of BLK x BLK
+    blocks runs: on the FP32 route, the one-wave strip kernel when the
+    image's chunks of 16 tiles fit one wave of STRIP_WAVE_CTAS per SM, else
+    the persistent fused kernel."""
+    if variant == 3:
+        return f"k_tc_split<16,16,{direction},tiled>"
+    if variant != 1:
+        return f"dense<16,16,{direction},tiled>"
+    chunks = (IMG // BLK) * -(-(IMG // BLK) // 16)
+    if chunks <= STRIP_WAVE_CTAS * sms:
+        return f"k_strip16_wave<{direction}>"
+    return f"k_fused<16,16,{direction},tiled>"
 
 
 def source_key(kernel_key: str) -> str:
@@ -213,7 +233,7 @@ def traffic_from_profiles(kernel_key: str, column: int = 1):
     write bytes beside it (column 3), if the kernel's sources have not
     changed since (the record stores their source key)."""
     p = os.path.join(ROOT, "profiles", "traffic_per_launch.txt")
-    if not os.path.exists(p):
+    if not os.path.exists(p) or kernel_key.split("<")[0] not in KERNEL_SOURCES:
         return None
     key = source_key(kernel_key)
     for ln in open(p):
@@ -368,12 +388,10 @@ def run_ours(args):
     elems = IMG * IMG
     step_bytes = elems * BYTES_PER_ELEM_STEP
     value = job_value_gbs(ms_total, args.steps, step_bytes, world)
-    kern = {1: "k_fused", 3: "k_tc_split"}.get(info.variant, "dense")
-
     # ---- dominant kernel roofline (8 B/element/launch)
     fwd_avg, inv_avg = kt["forward"], kt["inverse"]
-    dom_key, dom_avg = (f"{kern}<16,16,FWD,tiled>", fwd_avg) if fwd_avg >= inv_avg else \
-        (f"{kern}<16,16,INV,tiled>", inv_avg)
+    dom_dir, dom_avg = ("FWD", fwd_avg) if fwd_avg >= inv_avg else ("INV", inv_avg)
+    dom_key = dominant_kernel(info.variant, dom_dir, torch.cuda.get_device_properties(dev).multi_processor_count)
     peak, peak_kind = _peaks()
     achieved = elems * 8 / (dom_avg * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -389,21 +389,81 @@ __device__ __forceinline__ void row_pass(float *stage, int n, int warp, int lane
     }
 }
 
-// NST: stages of the ring (0: the configuration's count).  The single-stage
-// form serves 16 x 16 image strips whose chunks all get a CTA of their own
-// in one wave of seven CTAs per SM (at most 73 registers; the launch pads
-// its shared memory so that no eighth CTA lands on an SM): with two stages
-// six CTAs fit, and a 2048^2 image's 1024 chunks left 112 CTAs a second
-// chunk after the first wave.  Measured on that image: 8.59 -> 8.26 us per
-// inverse launch, 14.65 -> 14.0 us per forward-then-inverse step.
+// One wave of 16 x 16 image strips: every chunk gets a CTA of its own, seven
+// CTAs per SM (at most 73 registers; the launch pads the shared memory so
+// that no eighth CTA lands on an SM; with the two-stage ring six CTAs fit,
+// and a 2048^2 image's 1024 chunks left 112 CTAs a second chunk).  Warp w
+// owns tiles 4w .. 4w + 3 of the chunk in both passes -- strip columns
+// 64w .. 64w + 63: pass 1 gives each lane one column pair, pass 2 rows r and
+// r + 8 of one of the four tiles -- so each warp loads, transforms and
+// stores its quarter on an mbarrier of its own and never waits for the rest
+// of the chunk.  Measured on a 2048^2 image: 8.59 us per inverse launch with
+// the two-stage ring, 8.26 with one wave of whole-chunk CTAs, 7.57 with
+// warp-owned quarters (14.65 -> 14.0 -> 12.98 us per forward-then-inverse
+// step).
 constexpr int kOneWaveCtas = 7;
 
-template <int H, int W, int DIR, bool TILED, int NST = 0>
-__global__ void __launch_bounds__(FusedCfg<H, W, TILED>::THREADS,
-                                  NST == 1 ? kOneWaveCtas : FusedCfg<H, W, TILED>::MIN_CTAS) k_fused(const FusedParams p)
+template <int DIR>
+__global__ void __launch_bounds__(FusedCfg<16, 16, true>::THREADS, kOneWaveCtas) k_strip16_wave(const FusedParams p)
+{
+    constexpr int H = 16, W = 16;
+    using C = FusedCfg<H, W, true>;
+    static_assert(C::PAIR1 && C::J1 == 1 && C::J2 == 2 && C::NW * 4 == C::G, "warp-owned quarters");
+    extern __shared__ __align__(128) float smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + C::STAGE_FLOATS) + warp;
+    // spectral only: the folded diagonal, after the warps' barriers
+    float *lam_s = reinterpret_cast<float *>(smem + C::STAGE_FLOATS) + 2 * C::NW;
+    const ChunkGeom g = chunk_geom<H, W, true>(p, (int)blockIdx.x);
+    int nq = g.n - 4 * warp;  // tiles of this warp
+    nq = nq < 0 ? 0 : (nq > 4 ? 4 : nq);
+    if (lane == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    pdl_launch_dependents();
+    pdl_wait_prerequisites();
+    if constexpr (DIR == DIR_SPEC) {
+        for (int e = threadIdx.x; e < H * W; e += C::THREADS) lam_s[(e / W) * C::LAM_P + e % W] = __ldg(p.lam + e);
+        __syncthreads();
+    }
+    if (nq == 0) return;
+    float *qs = smem + 64 * warp;  // the warp's columns of strip row 0
+    const long long c0 = (long long)(g.t0 + 4 * warp) * W;
+    if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)(nq * H * W * 4));
+    __syncwarp();
+    if (lane < H) bulk_load(qs + lane * C::SP, p.in + (g.brow * H + lane) * p.ld_in + c0, (uint32_t)(nq * W * 4), bar);
+    if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar, 0))) {
+        // nothing is stored; the copies land (bounded wait) before the exit
+        if (lane == 0) {
+            record_timeout(p.status);
+            mbar_wait_bounded(bar, 0);
+        }
+        return;
+    }
+    col_pass<H, W, true, DIR == DIR_SPEC ? CORE_FWD : DIR>(smem, g.n, warp, lane, p.sc.h);
+    __syncwarp();
+    row_pass<H, W, true, DIR>(smem, g.n, warp, lane, p.sc.w, lam_s);
+    if constexpr (DIR == DIR_SPEC) {
+        __syncwarp();
+        col_pass<H, W, true, CORE_INV>(smem, g.n, warp, lane, p.sc.h);
+    }
+    fence_proxy_async_smem();
+    __syncwarp();
+    if (lane < H) {
+        bulk_store(p.out + (g.brow * H + lane) * p.ld_out + c0, qs + lane * C::SP, (uint32_t)(nq * W * 4));
+        bulk_commit();
+        bulk_wait<0>();
+    }
+}
+
+template <int H, int W, int DIR, bool TILED>
+__global__ void __launch_bounds__(FusedCfg<H, W, TILED>::THREADS, FusedCfg<H, W, TILED>::MIN_CTAS)
+    k_fused(const FusedParams p)
 {
     using C = FusedCfg<H, W, TILED>;
-    constexpr int STAGES = NST ? NST : C::STAGES;
+    constexpr int STAGES = C::STAGES;
     extern __shared__ __align__(128) float smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * C::STAGE_FLOATS);
     // spectral only: the folded diagonal, 16-byte aligned after the barriers
@@ -622,10 +682,10 @@ static cudaError_t launch_one(const DirScales &sc, const ExecGeom &g, unsigned i
     auto launch_kern = kern;
     size_t launch_smem = smem;
     if constexpr (TILED && H == 16 && W == 16 && C::STAGES > 1) {
-        // one single-stage CTA per chunk when all of them fit in one wave of
-        // kOneWaveCtas per SM (and the default configuration would not)
-        auto kern1 = k_fused<H, W, DIR, TILED, 1>;
-        constexpr size_t need1 = (size_t)C::STAGE_BYTES + 8 + (DIR == DIR_SPEC ? C::LAM_BYTES : 0);
+        // one CTA per chunk (k_strip16_wave) whenever all of them fit in one
+        // wave of kOneWaveCtas per SM; the persistent ring for more
+        auto kern1 = k_strip16_wave<DIR>;
+        constexpr size_t need1 = (size_t)C::STAGE_BYTES + 8 * C::NW + (DIR == DIR_SPEC ? C::LAM_BYTES : 0);
         static DeviceLaunchCache cache1;
         static size_t smem1_dev[64];
         int bps1 = 0, sms1 = 0;
@@ -646,13 +706,12 @@ static cudaError_t launch_one(const DirScales &sc, const ExecGeom &g, unsigned i
                 if (r == cudaSuccess) r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern1, C::THREADS, sm1);
                 if (r == cudaSuccess) r = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
                 if (r == cudaSuccess && debug_enabled())
-                    fprintf(stderr, "[bdct] k_fused<%d,%d,%d,%d> single stage: %d CTAs/SM, smem %zu B\n", H, W, DIR,
-                            (int)TILED, bps, sm1);
+                    fprintf(stderr, "[bdct] k_strip16_wave<%d>: %d CTAs/SM, smem %zu B\n", DIR, bps, sm1);
                 return r;
             },
             &bps1, &sms1);
         if (e != cudaSuccess) return e;
-        if (p.nchunks > grid && bps1 == kOneWaveCtas && (long long)p.nchunks <= (long long)bps1 * sms1) {
+        if (bps1 == kOneWaveCtas && (long long)p.nchunks <= (long long)bps1 * sms1) {
             launch_kern = kern1;
             launch_smem = smem1_dev[dev];
             grid = p.nchunks;

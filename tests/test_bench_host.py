@@ -45,6 +45,33 @@ def test_source_key_tracks_code_not_comments(tmp_path, monkeypatch):
     assert bench.source_key("k_tc_split<16,tiled>") == tc
 
 
+def test_dominant_kernel_names_the_route_the_image_takes(tmp_path, monkeypatch):
+    """The 2048^2 image of 16 x 16 blocks is 1024 chunks of 16 tiles: with
+    at least 1024 / 7 SMs they fit one wave of the one-wave kernel's 7 CTAs
+    per SM, so the FP32 route runs that kernel; with fewer it is the
+    persistent kernel."""
+    assert bench.dominant_kernel(1, "FWD", 152) == "k_strip16_wave<FWD>"
+    assert bench.dominant_kernel(1, "INV", 147) == "k_strip16_wave<INV>"
+    assert bench.dominant_kernel(1, "FWD", 400) == "k_strip16_wave<FWD>"
+    assert bench.dominant_kernel(1, "FWD", 146) == "k_fused<16,16,FWD,tiled>"   # 1022 < 1024 chunks
+    assert bench.dominant_kernel(3, "INV", 152) == "k_tc_split<16,16,INV,tiled>"
+    assert bench.dominant_kernel(2, "FWD", 152) == "dense<16,16,FWD,tiled>"
+    # one source key for the whole file; no record for a kernel without sources
+    assert bench.source_key("k_strip16_wave<FWD>") == bench.source_key("k_fused<16,16,FWD,tiled>")
+    assert bench.traffic_from_profiles("dense<16,16,FWD,tiled>") is None
+    # a record whose key is stale is not used
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    key = bench.source_key("k_strip16_wave<FWD>")
+    (prof / "traffic_per_launch.txt").write_text(
+        f"# header\nk_strip16_wave<FWD> 123 {key} 456\nk_strip16_wave<INV> 789 0000000000000000 1\n")
+    _copy_sources(tmp_path)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.traffic_from_profiles("k_strip16_wave<FWD>") == 123.0
+    assert bench.traffic_from_profiles("k_strip16_wave<FWD>", 3) == 456.0
+    assert bench.traffic_from_profiles("k_strip16_wave<INV>") is None
+
+
 
 def _rank_main(rank, world, port, ms_local, out_q):
     import os

@@ -85,12 +85,15 @@ def test_fused_tiled_all_shapes(oracle_mod, cuda_dev, h, w):
         assert torch.isnan(dst[:, cols:]).all(), (h, w, kind)
 
 
-@pytest.mark.parametrize("h,w,rows,cols", [(16, 16, 2048, 2048), (16, 16, 2048, 1920), (8, 16, 1024, 2048)])
+@pytest.mark.parametrize("h,w,rows,cols", [(16, 16, 2048, 2048), (16, 16, 2048, 1920), (16, 16, 2048, 1840),
+                                           (8, 16, 1024, 2048)])
 def test_tiled_one_wave_images(oracle_mod, cuda_dev, h, w, rows, cols):
-    """Images whose strip chunks all fit in one wave of single-stage CTAs but
-    not of the default two-stage ones (the 2048^2 image of 16 x 16 blocks is
-    1024 chunks), next to neighbouring sizes: every direction against the
-    oracle on every block."""
+    """Images of 16 x 16 blocks whose strip chunks all fit in one wave of
+    one-chunk CTAs but not of the persistent two-stage ones (the 2048^2 image
+    is 1024 chunks of 16 tiles; each warp owns four tiles of a chunk): full
+    last chunks, 8 tiles (two warps idle) and 3 tiles (one warp with a
+    partial quarter), next to a neighbouring shape; every direction, and for
+    16 x 16 the spectral step, against the oracle on every block."""
     import torch
     from paper_2609_28519_gb300 import Plan
     img = inputs.ramp_image(2600 + rows + cols + h, rows, cols)
@@ -103,6 +106,14 @@ def test_tiled_one_wave_images(oracle_mod, cuda_dev, h, w, rows, cols):
         torch.cuda.synchronize()
         got = inputs.image_to_blocks(dst.cpu().numpy(), h, w)
         _assert_parity(oracle_mod, got, _ref(oracle_mod, kind, blocks, 0), blocks, 0, kind, ("wave", h, w, rows, cols, kind))
+    if h == w == 16:
+        lam = inputs.poisson_diagonal(h, w)
+        plan.set_spectral(lam)
+        dst = torch.full_like(src, float("nan"))
+        plan.execute_tiled("spectral", src, dst)
+        torch.cuda.synchronize()
+        got = inputs.image_to_blocks(dst.cpu().numpy(), h, w)
+        _assert_spectral(oracle_mod, got, blocks, lam, ("wave-spectral", rows, cols))
 
 
 @pytest.mark.parametrize("h,w", RING_SHAPES)
