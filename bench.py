@@ -460,6 +460,7 @@ def run_ours(args):
             "ragged_4096": ragged_summary(dev),
             "odd_sides_256MiB": odd_sides_summary(dev, check=not args.no_check),
             "spectral_sweep_512MiB": spectral_sweep_summary(dev, check=not args.no_check),
+            "tiled_images_4096": tiled_images_summary(dev, check=not args.no_check),
             "boundary_diagnostics": boundary_summary(dev) if not args.no_check else None,
             "large_arrays": large_summary(dev),
         }
@@ -539,6 +540,56 @@ def odd_sides_summary(dev, shapes=((26, 32), (24, 40), (48, 48)), mib=256, check
                 idx = np.array([0, batch // 2, batch - 1])
                 xs = x[idx].cpu().numpy()
                 ys = y[idx].cpu().numpy()
+                ref = {"forward": lambda a: oracle.forward(a, 0), "inverse": lambda a: oracle.inverse(a, 0),
+                       "roundtrip": lambda a: a.astype(np.float64)}[kind](xs)
+                m = oracle.metrics(ys, ref, xs)
+                ent[kind]["e_rel_max"] = m["e_rel_max"]
+                ent[kind]["accepted"] = bool(oracle.accept(m))
+        out[f"{h}x{w}"] = ent
+        plan.close()
+    return out
+
+
+def tiled_images_summary(dev, shapes=((8, 8), (8, 16), (16, 8), (16, 16), (32, 32)), n=4096, check=True):
+    """The tiled view on n x n images (N(0,1) plus the 0.01 (i + j) ramp) cut
+    into blocks of each shape: forward / inverse / round trip over three
+    images in turn (inputs and outputs together more than twice the L2),
+    the calls captured once into a CUDA graph and replayed back to back;
+    sampled blocks against the FP64 oracle."""
+    import torch
+    import oracle
+    from paper_2609_28519_gb300 import Plan, inputs
+    peak, _ = _peaks()
+    stream = torch.cuda.current_stream(dev)
+    srcs = [torch.from_numpy(inputs.ramp_image(4100 + i, n, n)).to(dev) for i in range(3)]
+    dsts = [torch.empty_like(srcs[0]) for _ in range(3)]
+    reps = 24
+    out = {}
+    for h, w in shapes:
+        plan = Plan(h, w, path="fp32")
+        ent = {"variant": plan.info().variant}
+        for kind in ("forward", "inverse", "roundtrip"):
+            for i in range(3):
+                plan.execute_tiled(kind, srcs[i], dsts[i], stream)
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            cs = torch.cuda.Stream(dev)
+            cs.wait_stream(stream)
+            with torch.cuda.graph(g, stream=cs):
+                for i in range(reps):
+                    plan.execute_tiled(kind, srcs[i % 3], dsts[i % 3], cs.cuda_stream)
+            torch.cuda.synchronize()
+            g.replay()
+            torch.cuda.synchronize()
+            ms = min(replay_ms(g, stream) for _ in range(3)) / reps
+            del g
+            gbs = n * n * 8 / (ms * 1e-3) / 1e9
+            ent[kind] = {"us": ms * 1e3, "GB/s": gbs, "frac": gbs / peak}
+            if check:
+                nb_r, nb_c = n // h, n // w
+                picks = [(0, 0), (nb_r // 2, nb_c // 2 + 1), (nb_r - 1, nb_c - 1)]
+                xs = np.stack([srcs[0][r * h:(r + 1) * h, c * w:(c + 1) * w].cpu().numpy() for r, c in picks])
+                ys = np.stack([dsts[0][r * h:(r + 1) * h, c * w:(c + 1) * w].cpu().numpy() for r, c in picks])
                 ref = {"forward": lambda a: oracle.forward(a, 0), "inverse": lambda a: oracle.inverse(a, 0),
                        "roundtrip": lambda a: a.astype(np.float64)}[kind](xs)
                 m = oracle.metrics(ys, ref, xs)

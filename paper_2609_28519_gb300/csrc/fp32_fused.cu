@@ -57,11 +57,14 @@ template <int H, int W, bool TILED>
 struct FusedCfg {
     static constexpr int HW = H * W;
     static constexpr int LAYOUT = TILED ? LAY_STRIP : LAY_SLOT;
-    // arrays per chunk (image strips of 16-wide tiles take 16 tiles so that
-    // every thread gets a column pair in pass 1; contiguous batches of
-    // 256-element arrays take 16, measured 0.82 -> 0.94 of HBM for 16 x 16)
+    // arrays per chunk: contiguous batches of 256-element arrays take 16
+    // (measured 0.82 -> 0.94 of HBM for 16 x 16); image strips of tiles at
+    // most 16 wide and 256 elements take 16 (16-wide tiles: a column pair per
+    // thread in pass 1; 16 x 8 tiles on a 4096^2 image 0.60 -> 0.81 of HBM,
+    // 32 x 8 0.58 -> 0.63 against 8 tiles, whose CTAs had two warps), 32 x 16
+    // tiles stay at 8 (no better with 16)
     static constexpr int G = (HW <= 64 || (LAYOUT == LAY_SLOT && HW == 256)) ? 16
-                             : (LAYOUT == LAY_STRIP && W == 16 && H <= 16 ? 16 : 8);
+                             : (LAYOUT == LAY_STRIP && W <= 16 && HW <= 256 ? 16 : 8);
     // pass 1 on two adjacent columns per thread (8-byte loads), run as one
     // packed line (float2 cores).  Pairing halves the warps of a CTA; measured
     // on contiguous batches it pays for 32 x 32 only (other shapes lose more

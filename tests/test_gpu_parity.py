@@ -67,7 +67,7 @@ def test_fused_tiled_all_shapes(oracle_mod, cuda_dev, h, w):
     must stay untouched."""
     import torch
     from paper_2609_28519_gb300 import Plan
-    g = 16 if (h * w <= 64 or (w == 16 and h <= 16)) else 8  # tiles per chunk of a strip
+    g = 16 if (h * w <= 64 or (w <= 16 and h * w <= 256)) else 8  # tiles per chunk of a strip
     tpr = 2 * g + 3
     rows, cols = 3 * h, tpr * w
     img = inputs.gaussian(2500 + h + 5 * w, 1, rows, cols)[0]
@@ -83,6 +83,38 @@ def test_fused_tiled_all_shapes(oracle_mod, cuda_dev, h, w):
         got = inputs.image_to_blocks(dst[:, :cols].cpu().numpy(), h, w)
         _assert_parity(oracle_mod, got, _ref(oracle_mod, kind, blocks, 0), blocks, 0, kind, ("strip", h, w, kind))
         assert torch.isnan(dst[:, cols:]).all(), (h, w, kind)
+
+
+@pytest.mark.parametrize("h,w,extra", [(8, 8, 3), (8, 16, 6), (16, 8, 3), (16, 16, 6), (32, 8, 6), (32, 16, 3)])
+def test_tiled_persistent_many_chunks(oracle_mod, cuda_dev, h, w, extra):
+    """Image strips on images of more than 8000 chunks, so that every CTA of
+    the persistent ring takes several chunks and every stage's barrier turns
+    over more than once; each block row ends in a partial chunk of 3 or 6
+    tiles.  Every direction, and the spectral step, against the oracle on
+    every block."""
+    import torch
+    from paper_2609_28519_gb300 import Plan
+    g = 16 if (h * w <= 64 or (w <= 16 and h * w <= 256)) else 8  # tiles per chunk of a strip
+    tpr = 2 * g + extra
+    rows, cols = 2752 * h, tpr * w
+    img = inputs.gaussian(2700 + h + 5 * w, 1, rows, cols)[0]
+    blocks = inputs.image_to_blocks(img, h, w)
+    src = torch.from_numpy(img).to(cuda_dev)
+    plan = Plan(h, w, path="fp32")
+    assert plan.info().variant == 1
+    for kind in KINDS:
+        dst = torch.full_like(src, float("nan"))
+        plan.execute_tiled(kind, src, dst)
+        torch.cuda.synchronize()
+        got = inputs.image_to_blocks(dst.cpu().numpy(), h, w)
+        _assert_parity(oracle_mod, got, _ref(oracle_mod, kind, blocks, 0), blocks, 0, kind, ("persistent", h, w, kind))
+    lam = inputs.poisson_diagonal(h, w)
+    plan.set_spectral(lam)
+    dst = torch.full_like(src, float("nan"))
+    plan.execute_tiled("spectral", src, dst)
+    torch.cuda.synchronize()
+    got = inputs.image_to_blocks(dst.cpu().numpy(), h, w)
+    _assert_spectral(oracle_mod, got, blocks, lam, ("persistent-spectral", h, w))
 
 
 @pytest.mark.parametrize("h,w,rows,cols", [(16, 16, 2048, 2048), (16, 16, 2048, 1920), (16, 16, 2048, 1840),
