@@ -138,6 +138,11 @@ def test_tiled_one_wave_images(oracle_mod, cuda_dev, h, w, rows, cols):
         torch.cuda.synchronize()
         got = inputs.image_to_blocks(dst.cpu().numpy(), h, w)
         _assert_parity(oracle_mod, got, _ref(oracle_mod, kind, blocks, 0), blocks, 0, kind, ("wave", h, w, rows, cols, kind))
+        # in place: each warp reads its whole quarter before it writes it back
+        same = src.clone()
+        plan.execute_tiled(kind, same, same)
+        torch.cuda.synchronize()
+        assert torch.equal(same, dst), ("wave in place", h, w, rows, cols, kind)
     if h == w == 16:
         lam = inputs.poisson_diagonal(h, w)
         plan.set_spectral(lam)
