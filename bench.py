@@ -322,6 +322,75 @@ def time_path(path, work, dev, stream, steps, warmup):
     return plan, info, graphs
 
 
+def image_step_extras(plan, graphs, graph_steps, work, dev, stream, steps, peak, check=True):
+    """Beside the contract's single timed region, on the same image pool: the
+    spread of the forward-then-inverse step over 21 replays of its graph
+    (median and a 95% bootstrap interval of the median), the fused round trip
+    of every block (one launch, 8 B per element), and forward / inverse of the
+    same blocks laid out as a contiguous batch of 16384 arrays."""
+    import ctypes
+    import torch
+    import oracle
+    from paper_2609_28519_gb300 import native, inputs
+    elems = IMG * IMG
+    per_step = np.array([replay_ms(graphs["steps"], stream) / graph_steps for _ in range(21)])
+    rng = np.random.default_rng(0)
+    boot = np.median(rng.choice(per_step, size=(2000, per_step.size), replace=True), axis=1)
+    out = {"step_repeats": {"replays": int(per_step.size), "steps_per_replay": graph_steps,
+                            "median_us": float(np.median(per_step) * 1e3),
+                            "ci95_us": [float(np.percentile(boot, 2.5) * 1e3), float(np.percentile(boot, 97.5) * 1e3)],
+                            "min_us": float(per_step.min() * 1e3), "max_us": float(per_step.max() * 1e3)}}
+
+    def capture(fn):
+        g = torch.cuda.CUDAGraph()
+        cs = torch.cuda.Stream(dev)
+        cs.wait_stream(stream)
+        with torch.cuda.graph(g, stream=cs):
+            fn(cs)
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        return g
+
+    pool = work.pool
+    L = native.lib()
+
+    def rt_fn(cs):
+        for i in range(steps):
+            k = i % pool
+            if L.bdct_execute_tiled(plan.handle, native.ROUNDTRIP, ctypes.c_void_p(work.imgs[k].data_ptr()),
+                                    ctypes.c_void_p(work.outs[k].data_ptr()), IMG, IMG, IMG, IMG,
+                                    ctypes.c_void_p(cs.cuda_stream)):
+                raise RuntimeError("bdct_execute_tiled failed")
+
+    rt_us = min(replay_ms(capture(rt_fn), stream) for _ in range(3)) / steps * 1e3
+    rt = {"us_per_launch": rt_us, "GB/s": elems * 8 / (rt_us * 1e-6) / 1e9}
+    rt["frac"] = rt["GB/s"] / peak
+    if check:
+        src = inputs.image_to_blocks(work.imgs[0].cpu().numpy(), BLK, BLK)
+        got = inputs.image_to_blocks(work.outs[0].cpu().numpy(), BLK, BLK)
+        idx = np.random.default_rng(7).choice(src.shape[0], 256, replace=False)
+        m = oracle.metrics(got[idx], src[idx].astype(np.float64), src[idx])
+        rt.update({"e_rel_max": m["e_rel_max"], "accepted": bool(oracle.accept(m))})
+    out["fused_roundtrip"] = rt
+
+    # the same blocks as a contiguous batch (set up outside the timing)
+    nb = IMG // BLK
+    bx = [t.view(nb, BLK, nb, BLK).permute(0, 2, 1, 3).contiguous().view(nb * nb, BLK, BLK) for t in work.imgs]
+    by = [torch.empty_like(bx[0]) for _ in range(pool)]
+    batch = {}
+    for kind in ("forward", "inverse"):
+        def fn(cs, kind=kind):
+            for i in range(steps):
+                k = i % pool
+                plan.execute(kind, bx[k], by[k], cs)
+        us = min(replay_ms(capture(fn), stream) for _ in range(3)) / steps * 1e3
+        batch[kind] = {"us_per_launch": us, "frac": elems * 8 / (us * 1e-6) / 1e9 / peak}
+    out["contiguous_batch_16384"] = batch
+    del bx, by
+    return out
+
+
 def replay_ms(g, stream):
     import torch
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -447,6 +516,11 @@ def run_ours(args):
                "how": "bdct_execute_tiled_host: pinned host image in, forward then inverse on the device, "
                       "pinned host image out; 4 MiB bands, copies overlapped with the kernels"}
 
+    image_extra = None
+    if rank == 0 and not args.no_extra:
+        image_extra = image_step_extras(plan, graphs, args.steps, work, dev, stream, min(args.steps, 200), peak,
+                                        check=not args.no_check)
+
     # the other workloads of the metric, as compact summaries (rank 0 only):
     # the square sweep (fractions per size, errors per distribution), the
     # ragged batch and the large whole arrays
@@ -490,6 +564,7 @@ def run_ours(args):
             "clocks": clocks,
             "parity": parity,
             "paths": paths,
+            "image_extra": image_extra,
             "workloads": workloads,
         }
         print(json.dumps(line), flush=True)
