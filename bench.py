@@ -391,6 +391,59 @@ def image_step_extras(plan, graphs, graph_steps, work, dev, stream, steps, peak,
     return out
 
 
+def small_batch_summary(dev, stream, batch=1024, n=8, launches=256, check=True):
+    """1024 8x8 arrays, uniform[-1,1] (256 KiB, a latency-bound launch):
+    forward / inverse / round trip per launch, in a CUDA graph of `launches`
+    launches, once on one L2-resident buffer pair and once over a rotating
+    pool of buffer pairs larger than 2.5 times the L2; sampled against the
+    FP64 oracle."""
+    import torch
+    import oracle
+    from paper_2609_28519_gb300 import Plan, inputs
+    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+    nbytes = batch * n * n * 4
+    pool = int(np.ceil(2.5 * l2 / (2 * nbytes)))
+    x0 = torch.from_numpy(inputs.uniform(1, batch, n, n)).to(dev)
+    xs = [x0] + [torch.empty_like(x0).uniform_(-1.0, 1.0) for _ in range(pool - 1)]
+    ys = [torch.empty_like(x0) for _ in range(pool)]
+    plan = Plan(n, n, path="fp32")
+    out = {"batch": batch, "shape": f"{n}x{n}", "variant": plan.info().variant, "pool_buffers": pool}
+
+    def graph_us(kind, rotate):
+        for i in range(3):
+            plan.execute(kind, xs[i % pool], ys[i % pool], stream)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        cs = torch.cuda.Stream(dev)
+        cs.wait_stream(stream)
+        with torch.cuda.graph(g, stream=cs):
+            for i in range(launches):
+                k = i % pool if rotate else 0
+                plan.execute(kind, xs[k], ys[k], cs)
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        return min(replay_ms(g, stream) for _ in range(3)) / launches * 1e3
+
+    for kind in ("forward", "inverse", "roundtrip"):
+        ent = {}
+        for name, rotate in (("l2_resident", False), ("rotating_pool", True)):
+            us = graph_us(kind, rotate)
+            ent[name] = {"us_per_launch": us, "elements_per_s": batch * n * n / (us * 1e-6),
+                         "GB/s": nbytes * 2 / (us * 1e-6) / 1e9}
+        if check:
+            plan.execute(kind, xs[0], ys[0], stream)
+            torch.cuda.synchronize()
+            xin = xs[0].cpu().numpy()
+            ref = {"forward": lambda a: oracle.forward(a, 0), "inverse": lambda a: oracle.inverse(a, 0),
+                   "roundtrip": lambda a: a.astype(np.float64)}[kind](xin)
+            m = oracle.metrics(ys[0].cpu().numpy(), ref, xin)
+            ent.update({"e_rel_max": m["e_rel_max"], "accepted": bool(oracle.accept(m))})
+        out[kind] = ent
+    plan.close()
+    return out
+
+
 def replay_ms(g, stream):
     import torch
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -531,6 +584,7 @@ def run_ours(args):
                                                                    check=not args.no_check),
             "square_sweep_512MiB": sweep_summary(dev, [8, 16, 32, 64, 128, 256], 512, ("auto", "split_tc"),
                                                  check=not args.no_check),
+            "batch_1024_8x8": small_batch_summary(dev, stream, check=not args.no_check),
             "ragged_4096": ragged_summary(dev),
             "odd_sides_256MiB": odd_sides_summary(dev, check=not args.no_check),
             "spectral_sweep_512MiB": spectral_sweep_summary(dev, check=not args.no_check),
