@@ -128,13 +128,13 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def cpu_oracle_sample(target_s: float = 1.5):
+def cpu_oracle_sample(target_s: float = 1.5, threads: int = 0):
     """Time the FP64 oracle on forward-then-inverse of a bounded slice of the
-    image workload; returns (GB/s on the metric's algorithmic bytes, threads,
-    description)."""
+    image workload on `threads` host threads (0: all cores); returns (GB/s on
+    the metric's algorithmic bytes, threads, seconds, description)."""
     import oracle
     from paper_2609_28519_gb300 import inputs
-    threads = oracle.default_threads()
+    threads = threads or oracle.default_threads()
     img = inputs.ramp_image(2)
     blocks = inputs.image_to_blocks(img, BLK, BLK)
     # whole image per repeat; repeat until the sample has run target_s of wall time
@@ -149,7 +149,7 @@ def cpu_oracle_sample(target_s: float = 1.5):
             break
     gbs = reps * len(blocks) * BLK * BLK * BYTES_PER_ELEM_STEP / dt / 1e9
     return gbs, threads, dt, (f"{reps} passes over the 16384 16x16 blocks of the 2048x2048 image, "
-                              f"F then I, {dt:.2f} s wall on {threads} threads")
+                              f"F then I, {dt:.2f} s wall on {threads} thread{'s' if threads > 1 else ''}")
 
 
 def run_reference(args):
@@ -597,6 +597,8 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         gbs, threads, dt, desc = cpu_oracle_sample()
         cpu = {"value": gbs, "unit": "GB/s", "cores": threads, "kind": "oracle", "sample": desc}
+        gbs1, _, _, desc1 = cpu_oracle_sample(threads=1)
+        cpu["one_core"] = {"value": gbs1, "unit": "GB/s", "cores": 1, "sample": desc1}
 
     if rank == 0:
         line = {

@@ -439,6 +439,35 @@ def test_ring_tiled_image(oracle_mod, cuda_dev, h, w):
         _assert_parity(oracle_mod, got, _ref(oracle_mod, kind, blocks, 0), blocks, 0, kind, ("tiled", h, w, kind))
 
 
+def test_graph_capture_equals_direct_calls(cuda_dev):
+    """Calls captured by the user into a CUDA graph and replayed give the same
+    bits as the same calls made directly: the one-wave image route, a
+    persistent fused batch, the ring kernel and the two-pass line engine
+    (workspace reused inside the graph)."""
+    import torch
+    from paper_2609_28519_gb300 import Plan
+    img = torch.from_numpy(inputs.ramp_image(31, 2048, 2048)).to(cuda_dev)
+    cases = [(Plan(16, 16, path="fp32"), "tiled", img)]
+    for (h, w, b) in [(16, 16, 4096), (64, 64, 300), (256, 256, 40)]:
+        cases.append((Plan(h, w, path="fp32"), "batch", torch.from_numpy(inputs.uniform(32 + h, b, h, w)).to(cuda_dev)))
+    for plan, mode, x in cases:
+        for kind in KINDS:
+            direct = torch.empty_like(x)
+            replayed = torch.full_like(x, float("nan"))
+            call = (lambda o, st=None: plan.execute_tiled(kind, x, o, st)) if mode == "tiled" else \
+                   (lambda o, st=None: plan.execute(kind, x, o, st))
+            call(direct)
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            cs = torch.cuda.Stream(cuda_dev)
+            cs.wait_stream(torch.cuda.current_stream(cuda_dev))
+            with torch.cuda.graph(g, stream=cs):
+                call(replayed, cs)
+            g.replay()
+            torch.cuda.synchronize()
+            assert torch.equal(direct, replayed), (mode, tuple(x.shape), kind)
+
+
 def test_inplace_and_tail_and_guards(oracle_mod, cuda_dev):
     import torch
     from paper_2609_28519_gb300 import Plan
