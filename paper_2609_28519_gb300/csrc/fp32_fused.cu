@@ -437,27 +437,52 @@ __global__ void __launch_bounds__(FusedCfg<16, 16, true>::THREADS, kOneWaveCtas)
     if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)(nq * H * W * 4));
     __syncwarp();
     if (lane < H) bulk_load(qs + lane * C::SP, p.in + (g.brow * H + lane) * p.ld_in + c0, (uint32_t)(nq * W * 4), bar);
-    if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar, 0))) {
-        // nothing is stored; the copies land (bounded wait) before the exit
-        if (lane == 0) {
-            record_timeout(p.status);
-            mbar_wait_bounded(bar, 0);
-        }
-        return;
+    const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar, 0));
+    if (!ok && lane == 0) {
+        // nothing of this quarter is stored; its copies land (bounded wait)
+        // before the warp goes on
+        record_timeout(p.status);
+        mbar_wait_bounded(bar, 0);
     }
-    col_pass<H, W, true, DIR == DIR_SPEC ? CORE_FWD : DIR>(smem, g.n, warp, lane, p.sc.h);
-    __syncwarp();
-    row_pass<H, W, true, DIR>(smem, g.n, warp, lane, p.sc.w, lam_s);
-    if constexpr (DIR == DIR_SPEC) {
+    if (ok) {
+        col_pass<H, W, true, DIR == DIR_SPEC ? CORE_FWD : DIR>(smem, g.n, warp, lane, p.sc.h);
         __syncwarp();
-        col_pass<H, W, true, CORE_INV>(smem, g.n, warp, lane, p.sc.h);
+        row_pass<H, W, true, DIR>(smem, g.n, warp, lane, p.sc.w, lam_s);
+        if constexpr (DIR == DIR_SPEC) {
+            __syncwarp();
+            col_pass<H, W, true, CORE_INV>(smem, g.n, warp, lane, p.sc.h);
+        }
+        fence_proxy_async_smem();
     }
-    fence_proxy_async_smem();
-    __syncwarp();
-    if (lane < H) {
-        bulk_store(p.out + (g.brow * H + lane) * p.ld_out + c0, qs + lane * C::SP, (uint32_t)(nq * W * 4));
-        bulk_commit();
-        bulk_wait<0>();
+    if constexpr (DIR == DIR_INV) {
+        // The inverse stores the whole chunk from warp 0, in whole 1 KiB
+        // rows, once every warp with tiles is done (named barrier 1 over those
+        // warps, which also ANDs their outcomes: a warp whose wait expired
+        // still arrives, and then nothing is stored).  Measured on a 2048^2
+        // image: 7.50 -> 7.40 us per inverse launch; the forward keeps its
+        // per-warp stores (7.38 us either way).
+        uint32_t all_ok;
+        asm volatile(
+            "{\n\t.reg .pred p, q;\n\t"
+            "setp.ne.u32 p, %1, 0;\n\t"
+            "bar.red.and.pred q, 1, %2, p;\n\t"
+            "selp.u32 %0, 1, 0, q;\n\t}"
+            : "=r"(all_ok)
+            : "r"((uint32_t)ok), "r"(32 * ((g.n + 3) / 4))
+            : "memory");
+        if (all_ok && warp == 0 && lane < H) {
+            bulk_store(p.out + (g.brow * H + lane) * p.ld_out + (long long)g.t0 * W, smem + lane * C::SP,
+                       (uint32_t)(g.n * W * 4));
+            bulk_commit();
+            bulk_wait<0>();
+        }
+    } else {
+        __syncwarp();
+        if (ok && lane < H) {
+            bulk_store(p.out + (g.brow * H + lane) * p.ld_out + c0, qs + lane * C::SP, (uint32_t)(nq * W * 4));
+            bulk_commit();
+            bulk_wait<0>();
+        }
     }
 }
 
