@@ -437,14 +437,16 @@ __global__ void __launch_bounds__(FusedCfg<16, 16, true>::THREADS, kOneWaveCtas)
     if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)(nq * H * W * 4));
     __syncwarp();
     if (lane < H) bulk_load(qs + lane * C::SP, p.in + (g.brow * H + lane) * p.ld_in + c0, (uint32_t)(nq * W * 4), bar);
-    const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar, 0));
-    if (!ok && lane == 0) {
-        // nothing of this quarter is stored; its copies land (bounded wait)
-        // before the warp goes on
-        record_timeout(p.status);
-        mbar_wait_bounded(bar, 0);
-    }
-    if (ok) {
+    if constexpr (DIR != DIR_INV) {
+        // each warp stores its own quarter
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar, 0))) {
+            // nothing is stored; the copies land (bounded wait) before the exit
+            if (lane == 0) {
+                record_timeout(p.status);
+                mbar_wait_bounded(bar, 0);
+            }
+            return;
+        }
         col_pass<H, W, true, DIR == DIR_SPEC ? CORE_FWD : DIR>(smem, g.n, warp, lane, p.sc.h);
         __syncwarp();
         row_pass<H, W, true, DIR>(smem, g.n, warp, lane, p.sc.w, lam_s);
@@ -453,8 +455,25 @@ __global__ void __launch_bounds__(FusedCfg<16, 16, true>::THREADS, kOneWaveCtas)
             col_pass<H, W, true, CORE_INV>(smem, g.n, warp, lane, p.sc.h);
         }
         fence_proxy_async_smem();
-    }
-    if constexpr (DIR == DIR_INV) {
+        __syncwarp();
+        if (lane < H) {
+            bulk_store(p.out + (g.brow * H + lane) * p.ld_out + c0, qs + lane * C::SP, (uint32_t)(nq * W * 4));
+            bulk_commit();
+            bulk_wait<0>();
+        }
+    } else {
+        const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar, 0));
+        if (!ok && lane == 0) {
+            // nothing is stored; this quarter's copies land (bounded wait)
+            record_timeout(p.status);
+            mbar_wait_bounded(bar, 0);
+        }
+        if (ok) {
+            col_pass<H, W, true, DIR>(smem, g.n, warp, lane, p.sc.h);
+            __syncwarp();
+            row_pass<H, W, true, DIR>(smem, g.n, warp, lane, p.sc.w, lam_s);
+            fence_proxy_async_smem();
+        }
         // The inverse stores the whole chunk from warp 0, in whole 1 KiB
         // rows, once every warp with tiles is done (named barrier 1 over those
         // warps, which also ANDs their outcomes: a warp whose wait expired
@@ -473,13 +492,6 @@ __global__ void __launch_bounds__(FusedCfg<16, 16, true>::THREADS, kOneWaveCtas)
         if (all_ok && warp == 0 && lane < H) {
             bulk_store(p.out + (g.brow * H + lane) * p.ld_out + (long long)g.t0 * W, smem + lane * C::SP,
                        (uint32_t)(g.n * W * 4));
-            bulk_commit();
-            bulk_wait<0>();
-        }
-    } else {
-        __syncwarp();
-        if (ok && lane < H) {
-            bulk_store(p.out + (g.brow * H + lane) * p.ld_out + c0, qs + lane * C::SP, (uint32_t)(nq * W * 4));
             bulk_commit();
             bulk_wait<0>();
         }
