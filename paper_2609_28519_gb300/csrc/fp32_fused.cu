@@ -437,7 +437,7 @@ __global__ void __launch_bounds__(FusedCfg<16, 16, true>::THREADS, kOneWaveCtas)
     if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)(nq * H * W * 4));
     __syncwarp();
     if (lane < H) bulk_load(qs + lane * C::SP, p.in + (g.brow * H + lane) * p.ld_in + c0, (uint32_t)(nq * W * 4), bar);
-    if constexpr (DIR != DIR_INV) {
+    if constexpr (DIR != DIR_INV && DIR != DIR_RT) {
         // each warp stores its own quarter
         if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar, 0))) {
             // nothing is stored; the copies land (bounded wait) before the exit
@@ -474,12 +474,13 @@ __global__ void __launch_bounds__(FusedCfg<16, 16, true>::THREADS, kOneWaveCtas)
             row_pass<H, W, true, DIR>(smem, g.n, warp, lane, p.sc.w, lam_s);
             fence_proxy_async_smem();
         }
-        // The inverse stores the whole chunk from warp 0, in whole 1 KiB
-        // rows, once every warp with tiles is done (named barrier 1 over those
-        // warps, which also ANDs their outcomes: a warp whose wait expired
-        // still arrives, and then nothing is stored).  Measured on a 2048^2
-        // image: 7.50 -> 7.40 us per inverse launch; the forward keeps its
-        // per-warp stores (7.38 us either way).
+        // The inverse and the round trip store the whole chunk from warp 0, in
+        // whole 1 KiB rows, once every warp with tiles is done (named barrier
+        // 1 over those warps, which also ANDs their outcomes: a warp whose
+        // wait expired still arrives, and then nothing is stored).  Measured
+        // on a 2048^2 image: inverse 7.50 -> 7.40 us per launch, round trip
+        // 8.24 -> 8.02; the forward keeps its per-warp stores (7.38 us either
+        // way) and so does the spectral form, at the 72-register ceiling.
         uint32_t all_ok;
         asm volatile(
             "{\n\t.reg .pred p, q;\n\t"
