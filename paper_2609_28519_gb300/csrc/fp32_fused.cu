@@ -406,6 +406,21 @@ __device__ __forceinline__ void row_pass(float *stage, int n, int warp, int lane
 // step).
 constexpr int kOneWaveCtas = 7;
 
+// Named barrier 1 over `nthreads` threads that also ANDs v over them.
+__device__ __forceinline__ bool part_sync_and(bool v, int nthreads)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
+
 template <int DIR>
 __global__ void __launch_bounds__(FusedCfg<16, 16, true>::THREADS, kOneWaveCtas) k_strip16_wave(const FusedParams p)
 {
@@ -437,7 +452,34 @@ __global__ void __launch_bounds__(FusedCfg<16, 16, true>::THREADS, kOneWaveCtas)
     if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)(nq * H * W * 4));
     __syncwarp();
     if (lane < H) bulk_load(qs + lane * C::SP, p.in + (g.brow * H + lane) * p.ld_in + c0, (uint32_t)(nq * W * 4), bar);
-    if constexpr (DIR != DIR_INV && DIR != DIR_RT) {
+    if constexpr (DIR == DIR_SPEC) {
+        // the chunk is stored from warp 0 as in the inverse below; a warp
+        // whose wait expired still arrives at the barrier (with false), so
+        // that nothing is stored and no warp is left waiting
+        // (the barrier's thread count is recomputed where it is used: held
+        // across the passes it took a register, and this form sits at the
+        // 72-register ceiling)
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar, 0))) {
+            if (lane == 0) {
+                record_timeout(p.status);
+                mbar_wait_bounded(bar, 0);
+            }
+            part_sync_and(false, 32 * ((g.n + 3) / 4));
+            return;
+        }
+        col_pass<H, W, true, CORE_FWD>(smem, g.n, warp, lane, p.sc.h);
+        __syncwarp();
+        row_pass<H, W, true, DIR>(smem, g.n, warp, lane, p.sc.w, lam_s);
+        __syncwarp();
+        col_pass<H, W, true, CORE_INV>(smem, g.n, warp, lane, p.sc.h);
+        fence_proxy_async_smem();
+        if (part_sync_and(true, 32 * ((g.n + 3) / 4)) && warp == 0 && lane < H) {
+            bulk_store(p.out + (g.brow * H + lane) * p.ld_out + (long long)g.t0 * W, smem + lane * C::SP,
+                       (uint32_t)(g.n * W * 4));
+            bulk_commit();
+            bulk_wait<0>();
+        }
+    } else if constexpr (DIR == DIR_FWD) {
         // each warp stores its own quarter
         if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar, 0))) {
             // nothing is stored; the copies land (bounded wait) before the exit
@@ -447,13 +489,9 @@ __global__ void __launch_bounds__(FusedCfg<16, 16, true>::THREADS, kOneWaveCtas)
             }
             return;
         }
-        col_pass<H, W, true, DIR == DIR_SPEC ? CORE_FWD : DIR>(smem, g.n, warp, lane, p.sc.h);
+        col_pass<H, W, true, DIR>(smem, g.n, warp, lane, p.sc.h);
         __syncwarp();
         row_pass<H, W, true, DIR>(smem, g.n, warp, lane, p.sc.w, lam_s);
-        if constexpr (DIR == DIR_SPEC) {
-            __syncwarp();
-            col_pass<H, W, true, CORE_INV>(smem, g.n, warp, lane, p.sc.h);
-        }
         fence_proxy_async_smem();
         __syncwarp();
         if (lane < H) {
@@ -479,18 +517,12 @@ __global__ void __launch_bounds__(FusedCfg<16, 16, true>::THREADS, kOneWaveCtas)
         // 1 over those warps, which also ANDs their outcomes: a warp whose
         // wait expired still arrives, and then nothing is stored).  Measured
         // on a 2048^2 image: inverse 7.50 -> 7.40 us per launch, round trip
-        // 8.24 -> 8.02; the forward keeps its per-warp stores (7.38 us either
-        // way) and so does the spectral form, at the 72-register ceiling.
-        uint32_t all_ok;
-        asm volatile(
-            "{\n\t.reg .pred p, q;\n\t"
-            "setp.ne.u32 p, %1, 0;\n\t"
-            "bar.red.and.pred q, 1, %2, p;\n\t"
-            "selp.u32 %0, 1, 0, q;\n\t}"
-            : "=r"(all_ok)
-            : "r"((uint32_t)ok), "r"(32 * ((g.n + 3) / 4))
-            : "memory");
-        if (all_ok && warp == 0 && lane < H) {
+        // 8.24 -> 8.02, the spectral form above 9.40 -> 9.14; the forward
+        // keeps its per-warp stores (7.38 us either way).  The spectral form
+        // sits at the 72-register ceiling of seven CTAs per SM and keeps an
+        // early exit for its passes: with the passes made conditional on the
+        // wait outcome instead, it spilled and ran at half speed.
+        if (part_sync_and(ok, 32 * ((g.n + 3) / 4)) && warp == 0 && lane < H) {
             bulk_store(p.out + (g.brow * H + lane) * p.ld_out + (long long)g.t0 * W, smem + lane * C::SP,
                        (uint32_t)(g.n * W * 4));
             bulk_commit();
